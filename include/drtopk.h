@@ -1,0 +1,173 @@
+/*
+ * drtopk.h - C ABI of a GB300-native delegate-centric top-k library.
+ *
+ * The method is Dr. Top-k (Gaihre et al., "Dr. Top-k: Delegate-Centric
+ * Top-k on GPUs", SC'21, arXiv 2109.08219). Problem statement (Sec. 1): given
+ * a vector V of n keys, top-k returns the k largest elements of V and
+ * k-selection returns the k-th largest. The library computes both exactly:
+ *   1. delegate pass (Sec. 3.1 Rule 1, Sec. 3.3 Rule 3, Sec. 4.1): V is cut
+ *      into subranges of 2^alpha keys; each yields its beta largest keys;
+ *   2. first top-k (Sec. 3.2 Rule 2): tau = k-th largest delegate, a lower
+ *      bound on the k-th largest key of V;
+ *   3. concatenation with filtering (Sec. 3.2, 3.3): only subranges whose
+ *      delegates reach tau are read again; only keys that can still be in
+ *      the answer are kept;
+ *   4. second top-k (Sec. 4.1): an exact selection over the kept keys.
+ * alpha follows Rule 4 / Eq. 9 (const = 3, rounded down) and beta = 2
+ * (Sec. 3.3, beta tuning) unless the caller forces them.
+ *
+ * Conventions for every entry point:
+ *   - Keys are 32-bit: unsigned, signed or IEEE float, named by drtopk_dtype.
+ *     Order: unsigned / signed integer order; floats by IEEE total order
+ *     restricted to non-NaN values (-0.0 < +0.0). NaNs are accepted and
+ *     ordered by their bit pattern (positive NaNs above +inf, negative NaNs
+ *     below -inf); they are not validated.
+ *   - Ties are broken by the smallest index. The top-k output is sorted by
+ *     (key descending, index ascending); indices are int32.
+ *   - 1 <= k <= n <= 2^31 - 1. Other values return DRTOPK_ERR_K (k) or
+ *     DRTOPK_ERR_INVALID (n, pointers).
+ *   - Device pointers point to memory of the current CUDA device. Keys must
+ *     be 4-byte aligned; 16-byte alignment takes the TMA fast path.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream). Calls are asynchronous on `stream` unless stated otherwise:
+ *     results are valid once the stream has reached the call. The input
+ *     must stay alive and unmodified until then.
+ *   - The library allocates its temporary workspace with the stream-ordered
+ *     allocator (cudaMallocAsync / cudaFreeAsync on `stream`) and owns it;
+ *     the caller owns every input and output buffer.
+ *   - Calls return a drtopk_status and never abort. A CUDA error returns
+ *     DRTOPK_ERR_CUDA; argument checks happen before any CUDA call.
+ */
+#ifndef DRTOPK_H
+#define DRTOPK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DRTOPK_U32 = 0,
+  DRTOPK_I32 = 1,
+  DRTOPK_F32 = 2
+} drtopk_dtype;
+
+typedef enum {
+  DRTOPK_OK = 0,
+  DRTOPK_ERR_INVALID = 1, /* bad n, null pointer, bad alpha/beta, bad handle */
+  DRTOPK_ERR_K = 2,       /* k outside [1, n] */
+  DRTOPK_ERR_DTYPE = 3,   /* dtype not one of drtopk_dtype */
+  DRTOPK_ERR_NOMEM = 4,   /* workspace allocation failed */
+  DRTOPK_ERR_CUDA = 5,    /* a CUDA call failed */
+  DRTOPK_ERR_BUDGET = 6,  /* server: request larger than the HBM budget */
+  DRTOPK_ERR_TIMEOUT = 7, /* a bounded device-side wait gave up */
+  DRTOPK_PENDING = 8      /* server: ticket not finished yet */
+} drtopk_status;
+
+/* Human-readable name of a status. Never NULL. */
+const char* drtopk_status_str(drtopk_status s);
+
+/*
+ * Parameter choice (host only, no CUDA call). Rule 4 / Eq. 9 (Sec. 4.2):
+ * alpha = floor((log2 n - log2 k + 3) / 2), clamped to [2, 16], then lowered
+ * while fewer than 2k delegates would exist (beta * ceil(n / 2^alpha) < 2k)
+ * and alpha > 2. beta = 2 (Sec. 3.3). *workspace_bytes receives the device
+ * workspace a top-k call with these parameters allocates (may be NULL).
+ */
+drtopk_status drtopk_plan(int64_t n, int64_t k, int* alpha, int* beta,
+                          size_t* workspace_bytes);
+
+/*
+ * k-selection (Sec. 1): out_kth[0] = the k-th largest key of keys[0..n),
+ * written with the input's dtype. keys, out_kth: device pointers.
+ */
+drtopk_status drtopk_kth(const void* keys, drtopk_dtype dtype, int64_t n,
+                         int64_t k, void* out_kth, void* stream);
+
+/*
+ * top-k (Sec. 1): out_keys[0..k) (dtype of the input) and out_idx[0..k)
+ * (int32 positions in keys) receive the k largest keys, sorted by (key
+ * descending, index ascending); among equal keys the smallest indices win.
+ * keys, out_keys, out_idx: device pointers.
+ */
+drtopk_status drtopk_topk(const void* keys, drtopk_dtype dtype, int64_t n,
+                          int64_t k, void* out_keys, int32_t* out_idx,
+                          void* stream);
+
+/* Per-query statistics of the delegate-centric path (Sec. 5.2 workload
+ * statistics: delegate and concatenated vector sizes). */
+typedef struct {
+  int32_t alpha;           /* subrange size exponent used */
+  int32_t beta;            /* delegates per subrange used */
+  int64_t subranges;       /* S = ceil(n / 2^alpha) */
+  uint32_t tau;            /* threshold, order-mapped key (Rule 2) */
+  uint32_t kth_mapped;     /* k-th largest key, order-mapped */
+  int64_t greater;         /* |{x > tau}|: candidates kept by the filter */
+  int64_t ties_needed;     /* k - greater when greater < k, else 0 */
+  int64_t scanned;         /* subranges read again by the filter (Rule 3) */
+  int64_t tie_scanned;     /* subranges read again to rank ties at tau */
+  int64_t survivors;       /* candidates left after the first digit of the
+                              second top-k */
+  int64_t emitted;         /* outputs written (equals k on success) */
+  uint32_t error;          /* device error flags, 0 when none */
+  uint32_t reserved;
+} drtopk_stats;
+
+/*
+ * Extended query: alpha / beta forced when > 0 (alpha in [2, 16], beta in
+ * [1, 4], beta <= 2^alpha), else chosen as drtopk_plan does. Either out_keys
+ * and out_idx (top-k) or out_kth (k-selection) or all three may be given;
+ * when only out_kth is given the call runs k-selection. stats: HOST pointer,
+ * optional; when given, the call synchronizes `stream` and fills it.
+ */
+drtopk_status drtopk_topk_ex(const void* keys, drtopk_dtype dtype, int64_t n,
+                             int64_t k, int alpha, int beta, void* out_keys,
+                             int32_t* out_idx, void* out_kth,
+                             drtopk_stats* stats, void* stream);
+
+/*
+ * The delegate pass alone (Sec. 3.1, 3.3, 4.1), exposed as a stage. For
+ * each subrange i of 2^alpha keys (the last may be shorter) writes its beta
+ * largest keys, order-mapped, to d_keys[i*beta + j] (descending, ties by
+ * smaller index) and their int32 positions in keys to d_idx[i*beta + j].
+ * A subrange with fewer than beta keys pads with key 0 and index -1.
+ * d_keys, d_idx: device, ceil(n / 2^alpha) * beta entries.
+ */
+drtopk_status drtopk_delegates(const void* keys, drtopk_dtype dtype,
+                               int64_t n, int alpha, int beta,
+                               uint32_t* d_keys, int32_t* d_idx,
+                               void* stream);
+
+/*
+ * top-k of a HOST array: copies keys (host, pinned or pageable) to the
+ * device, runs drtopk_topk and copies the results back to host out_keys /
+ * out_idx. Synchronous: returns when the host outputs are written.
+ */
+drtopk_status drtopk_topk_host(const void* keys, drtopk_dtype dtype,
+                               int64_t n, int64_t k, void* out_keys,
+                               int32_t* out_idx, void* stream);
+
+/* Stage timing (CUDA events recorded on the launching stream around each
+ * stage while profiling is on). Stages: 0 delegate pass, 1 threshold
+ * select, 2 filter, 3 tie ranking, 4 second top-k, 5 output sort. */
+#define DRTOPK_NUM_STAGES 6
+typedef struct {
+  double ms[DRTOPK_NUM_STAGES];       /* summed device time per stage */
+  int64_t launches[DRTOPK_NUM_STAGES]; /* queries that ran the stage */
+} drtopk_profile;
+
+/* Start collecting stage times (clears previous data). Host only. */
+drtopk_status drtopk_profile_begin(void);
+/* Stop collecting; synchronizes the recorded events and fills *out. */
+drtopk_status drtopk_profile_end(drtopk_profile* out);
+
+/* Number of kernels this library has launched since it was loaded. */
+uint64_t drtopk_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DRTOPK_H */

@@ -1,0 +1,236 @@
+"""GB300-native delegate-centric top-k (Dr. Top-k, SC'21, arXiv 2109.08219).
+
+Thin Python binding of the C ABI declared in ``include/drtopk.h``: every
+function below marshals its arguments and calls the CUDA library
+``_build/libdrtopk.so`` of this package; all work runs in its kernels.
+PyTorch is used only for device memory and streams. There is no CPU
+fallback: a missing library raises ``DrTopkError``.
+
+Key dtypes: ``"u32"``, ``"i32"``, ``"f32"``. A torch.float32 tensor is f32,
+torch.int32 is i32 unless ``dtype="u32"`` is passed (torch has little uint32
+arithmetic, so u32 keys usually travel as int32 tensors holding the bits),
+torch.uint32 is u32.
+"""
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libdrtopk.so")
+
+U32, I32, F32 = 0, 1, 2
+_NAMES = {"u32": U32, "i32": I32, "f32": F32}
+
+STATUS = ["DRTOPK_OK", "DRTOPK_ERR_INVALID", "DRTOPK_ERR_K", "DRTOPK_ERR_DTYPE",
+          "DRTOPK_ERR_NOMEM", "DRTOPK_ERR_CUDA", "DRTOPK_ERR_BUDGET",
+          "DRTOPK_ERR_TIMEOUT", "DRTOPK_PENDING"]
+NUM_STAGES = 6
+STAGE_NAMES = ["delegate", "threshold", "filter", "ties", "second_select", "sort"]
+
+
+class DrTopkError(RuntimeError):
+    def __init__(self, status, where=""):
+        self.status = status
+        name = STATUS[status] if 0 <= status < len(STATUS) else str(status)
+        super().__init__("%s%s" % (name, (" in " + where) if where else ""))
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_int32), ("beta", ctypes.c_int32),
+                ("subranges", ctypes.c_int64), ("tau", ctypes.c_uint32),
+                ("kth_mapped", ctypes.c_uint32), ("greater", ctypes.c_int64),
+                ("ties_needed", ctypes.c_int64), ("scanned", ctypes.c_int64),
+                ("tie_scanned", ctypes.c_int64), ("survivors", ctypes.c_int64),
+                ("emitted", ctypes.c_int64), ("error", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * NUM_STAGES),
+                ("launches", ctypes.c_int64 * NUM_STAGES)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded C library (raises DrTopkError-like OSError when missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise OSError("drtopk CUDA library not built: %s (run __graft_entry__.build())"
+                          % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        p, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+        L.drtopk_status_str.argtypes = [i32]
+        L.drtopk_status_str.restype = ctypes.c_char_p
+        L.drtopk_plan.argtypes = [i64, i64, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                  ctypes.POINTER(ctypes.c_size_t)]
+        L.drtopk_kth.argtypes = [p, i32, i64, i64, p, p]
+        L.drtopk_topk.argtypes = [p, i32, i64, i64, p, p, p]
+        L.drtopk_topk_ex.argtypes = [p, i32, i64, i64, i32, i32, p, p, p,
+                                     ctypes.POINTER(Stats), p]
+        L.drtopk_delegates.argtypes = [p, i32, i64, i32, i32, p, p, p]
+        L.drtopk_topk_host.argtypes = [p, i32, i64, i64, p, p, p]
+        L.drtopk_profile_begin.argtypes = []
+        L.drtopk_profile_end.argtypes = [ctypes.POINTER(Profile)]
+        L.drtopk_launch_count.argtypes = []
+        L.drtopk_launch_count.restype = ctypes.c_uint64
+        for fn in ("drtopk_plan", "drtopk_kth", "drtopk_topk", "drtopk_topk_ex",
+                   "drtopk_delegates", "drtopk_topk_host", "drtopk_profile_begin",
+                   "drtopk_profile_end"):
+            getattr(L, fn).restype = i32
+        _lib = L
+    return _lib
+
+
+def _check(rc, where):
+    if rc != 0:
+        raise DrTopkError(rc, where)
+
+
+def _dtype_code(t, dtype):
+    import torch
+    if dtype is not None:
+        if dtype not in _NAMES:
+            raise ValueError("dtype must be one of u32, i32, f32")
+        code = _NAMES[dtype]
+        if t.element_size() != 4:
+            raise ValueError("keys must be 32-bit")
+        return code
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype == torch.int32:
+        return I32
+    if t.dtype == getattr(torch, "uint32", None):
+        return U32
+    raise ValueError("unsupported key dtype %s" % t.dtype)
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev(t):
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def status_str(status):
+    return lib().drtopk_status_str(status).decode()
+
+
+def drtopk_plan(n, k):
+    """Rule 4 parameter choice: (alpha, beta, workspace_bytes). Host only."""
+    a, b, w = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
+    _check(lib().drtopk_plan(n, k, ctypes.byref(a), ctypes.byref(b), ctypes.byref(w)),
+           "drtopk_plan")
+    return a.value, b.value, w.value
+
+
+def drtopk_kth(keys, k, out=None, dtype=None, stream=None):
+    """k-th largest key of a 1-D CUDA tensor; returns a 1-element tensor."""
+    import torch
+    code = _dtype_code(keys, dtype)
+    if out is None:
+        out = torch.empty(1, dtype=keys.dtype, device=keys.device)
+    _check(lib().drtopk_kth(_dev(keys), code, keys.numel(), k, _dev(out), _stream(stream)),
+           "drtopk_kth")
+    return out
+
+
+def drtopk_topk(keys, k, out_keys=None, out_idx=None, dtype=None, stream=None):
+    """Top-k of a 1-D CUDA tensor: (keys, int32 indices), sorted by (key desc,
+    index asc); ties go to the smallest index."""
+    import torch
+    code = _dtype_code(keys, dtype)
+    if out_keys is None:
+        out_keys = torch.empty(k, dtype=keys.dtype, device=keys.device)
+    if out_idx is None:
+        out_idx = torch.empty(k, dtype=torch.int32, device=keys.device)
+    _check(lib().drtopk_topk(_dev(keys), code, keys.numel(), k, _dev(out_keys), _dev(out_idx),
+                             _stream(stream)), "drtopk_topk")
+    return out_keys, out_idx
+
+
+def drtopk_topk_ex(keys, k, alpha=0, beta=0, want_topk=True, want_kth=True, dtype=None,
+                   stats=True, stream=None):
+    """Extended query with forced alpha/beta and statistics.
+
+    Returns (out_keys or None, out_idx or None, out_kth or None, stats dict or
+    None). With stats=True the call synchronizes the stream."""
+    import torch
+    code = _dtype_code(keys, dtype)
+    ok = oi = ot = None
+    if want_topk:
+        ok = torch.empty(k, dtype=keys.dtype, device=keys.device)
+        oi = torch.empty(k, dtype=torch.int32, device=keys.device)
+    if want_kth:
+        ot = torch.empty(1, dtype=keys.dtype, device=keys.device)
+    st = Stats() if stats else None
+    rc = lib().drtopk_topk_ex(_dev(keys), code, keys.numel(), k, alpha, beta,
+                              _dev(ok) if ok is not None else None,
+                              _dev(oi) if oi is not None else None,
+                              _dev(ot) if ot is not None else None,
+                              ctypes.byref(st) if st is not None else None, _stream(stream))
+    _check(rc, "drtopk_topk_ex")
+    return ok, oi, ot, (st.as_dict() if st is not None else None)
+
+
+def drtopk_delegates(keys, alpha, beta, dtype=None, stream=None):
+    """Delegate pass alone: (mapped delegate keys as int32 bits [S, beta],
+    int32 positions [S, beta]); pads are key 0 / index -1."""
+    import torch
+    code = _dtype_code(keys, dtype)
+    n = keys.numel()
+    S = (n + (1 << alpha) - 1) >> alpha
+    dk = torch.empty(S * beta, dtype=torch.int32, device=keys.device)
+    di = torch.empty(S * beta, dtype=torch.int32, device=keys.device)
+    _check(lib().drtopk_delegates(_dev(keys), code, n, alpha, beta, _dev(dk), _dev(di),
+                                  _stream(stream)), "drtopk_delegates")
+    return dk.view(S, beta), di.view(S, beta)
+
+
+def drtopk_topk_host(keys_np, k, dtype, stream=None):
+    """Top-k of a host numpy array (uint32/int32/float32 view given by dtype).
+    Returns numpy (keys, int32 indices). Synchronous."""
+    import numpy as np
+    keys_np = np.ascontiguousarray(keys_np)
+    if keys_np.itemsize != 4:
+        raise ValueError("keys must be 32-bit")
+    ok = np.empty(k, dtype=keys_np.dtype)
+    oi = np.empty(k, dtype=np.int32)
+    _check(lib().drtopk_topk_host(keys_np.ctypes.data_as(ctypes.c_void_p), _NAMES[dtype],
+                                  keys_np.size, k, ok.ctypes.data_as(ctypes.c_void_p),
+                                  oi.ctypes.data_as(ctypes.c_void_p), _stream(stream)),
+           "drtopk_topk_host")
+    return ok, oi
+
+
+def drtopk_topk_host_ptr(keys_ptr, n, k, dtype, out_keys_ptr, out_idx_ptr, stream=None):
+    """Top-k of a host buffer given by raw pointers (e.g. pinned torch tensors)."""
+    _check(lib().drtopk_topk_host(ctypes.c_void_p(keys_ptr), _NAMES[dtype], n, k,
+                                  ctypes.c_void_p(out_keys_ptr), ctypes.c_void_p(out_idx_ptr),
+                                  _stream(stream)), "drtopk_topk_host")
+
+
+def profile_begin():
+    _check(lib().drtopk_profile_begin(), "drtopk_profile_begin")
+
+
+def profile_end():
+    """Stage times since profile_begin: {stage: (ms_total, count)}."""
+    pr = Profile()
+    _check(lib().drtopk_profile_end(ctypes.byref(pr)), "drtopk_profile_end")
+    return {STAGE_NAMES[i]: (pr.ms[i], pr.launches[i]) for i in range(NUM_STAGES)}
+
+
+def launch_count():
+    return int(lib().drtopk_launch_count())

@@ -1,0 +1,427 @@
+// C ABI of the drtopk library: argument checks, parameter choice (Rule 4),
+// workspace, stage orchestration on one stream, statistics and profiling.
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+#include "launch.h"
+
+namespace drtopk {
+
+static std::atomic<uint64_t> g_launches{0};
+void note_launch(int n) { g_launches.fetch_add(static_cast<uint64_t>(n)); }
+
+namespace {
+
+// ------------------------------------------------------------- planning ---
+struct Plan {
+  int alpha;
+  int beta;
+  int64_t S;
+  int64_t g_cap;
+  bool fuse_hist;  // beta * S >= k: tau from the delegates, else tau = 0
+};
+
+int alpha_rule4(int64_t n, int64_t k) {
+  // Rule 4 / Eq. 9 with const = 3, rounded down (Sec. 4.2)
+  const double a = 0.5 * (std::log2(static_cast<double>(n)) - std::log2(static_cast<double>(k)) + 3.0);
+  return static_cast<int>(std::floor(a));
+}
+
+bool make_plan(int64_t n, int64_t k, int alpha, int beta, Plan* p) {
+  if (beta <= 0) beta = 2;  // Sec. 3.3: beta = 2 performs best
+  if (beta < 1 || beta > kMaxBeta) return false;
+  if (alpha <= 0) {
+    int a = alpha_rule4(n, k);
+    a = std::max(kMinAlpha, std::min(kMaxAlpha, a));
+    // enough delegates for a useful threshold: beta * S >= 2k
+    while (a > kMinAlpha && static_cast<int64_t>(beta) * ((n + (int64_t(1) << a) - 1) >> a) < 2 * k) --a;
+    alpha = a;
+  }
+  if (alpha < kMinAlpha || alpha > kMaxAlpha || (int64_t(1) << alpha) < beta) return false;
+  p->alpha = alpha;
+  p->beta = beta;
+  p->S = (n + (int64_t(1) << alpha) - 1) >> alpha;
+  p->fuse_hist = static_cast<int64_t>(beta) * p->S >= k;
+  if (p->fuse_hist) {
+    const int64_t bound = ((k - 1) / beta) * (int64_t(1) << alpha) + k;
+    p->g_cap = std::min<int64_t>(n, bound);
+  } else {
+    p->g_cap = n;
+  }
+  if (p->g_cap < 1) p->g_cap = 1;
+  return true;
+}
+
+constexpr size_t kAlign = 256;
+size_t al(size_t b) { return (b + kAlign - 1) & ~(kAlign - 1); }
+
+constexpr int kTieSubPerBlock = 2048;
+
+struct Layout {
+  size_t ctl, dkeys, dsegs, g, sv, w, w2, tcnt, bsum, shist, total;
+};
+
+Layout layout(const Plan& p, int64_t k, bool need_topk, bool external_dkeys) {
+  Layout L;
+  size_t o = 0;
+  L.ctl = o; o += al(sizeof(Ctl));
+  L.dkeys = o; if (!external_dkeys) o += al(static_cast<size_t>(p.S) * p.beta * 4);
+  L.dsegs = o; o += al(static_cast<size_t>(p.S) * p.beta * 2);
+  L.g = o; o += al(static_cast<size_t>(p.g_cap) * 8);
+  L.sv = o; o += al(static_cast<size_t>(p.g_cap) * 8);
+  L.w = o; if (need_topk) o += al(static_cast<size_t>(k) * 8);
+  L.w2 = o; if (need_topk && k > 4096) o += al(static_cast<size_t>(k) * 8);
+  L.tcnt = o; if (need_topk) o += al(static_cast<size_t>(p.S) * 4);
+  const int64_t nblk = (p.S + kTieSubPerBlock - 1) / kTieSubPerBlock;
+  L.bsum = o; if (need_topk) o += al(static_cast<size_t>(2 * nblk) * 4);
+  L.shist = o; if (need_topk) o += al(sort_hist_words(k) * 4);
+  L.total = o;
+  return L;
+}
+
+// --------------------------------------------------------------- device ---
+struct DevInfo {
+  int sms = 0;
+  bool pool_set = false;
+};
+std::mutex g_dev_mu;
+DevInfo g_dev[64];
+
+drtopk_status dev_info(int* sms) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return DRTOPK_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  DevInfo& d = g_dev[dev];
+  if (d.sms == 0) {
+    if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return DRTOPK_ERR_CUDA;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t thr = UINT64_MAX;  // keep freed workspace cached in the pool
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+  }
+  *sms = d.sms;
+  return DRTOPK_OK;
+}
+
+// ------------------------------------------------------------ profiling ---
+struct StageRec {
+  int stage;
+  cudaEvent_t a, b;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<StageRec> g_prof;
+
+struct StageTimer {
+  cudaStream_t s;
+  bool on;
+  cudaEvent_t a = nullptr;
+  int stage = -1;
+  explicit StageTimer(cudaStream_t st) : s(st) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    on = g_prof_on;
+  }
+  void begin(int st) {
+    if (!on) return;
+    stage = st;
+    cudaEventCreate(&a);
+    cudaEventRecord(a, s);
+  }
+  void end() {
+    if (!on || stage < 0) return;
+    cudaEvent_t b;
+    cudaEventCreate(&b);
+    cudaEventRecord(b, s);
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof.push_back(StageRec{stage, a, b});
+    stage = -1;
+  }
+};
+
+drtopk_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return DRTOPK_OK;
+  if (e == cudaErrorMemoryAllocation) return DRTOPK_ERR_NOMEM;
+  return DRTOPK_ERR_CUDA;
+}
+
+drtopk_status check_args(const void* keys, int dtype, int64_t n, int64_t k) {
+  if (dtype != DRTOPK_U32 && dtype != DRTOPK_I32 && dtype != DRTOPK_F32) return DRTOPK_ERR_DTYPE;
+  if (n < 1 || n > 0x7FFFFFFFLL) return DRTOPK_ERR_INVALID;
+  if (k < 1 || k > n) return DRTOPK_ERR_K;
+  if (!keys || (reinterpret_cast<uintptr_t>(keys) & 3u)) return DRTOPK_ERR_INVALID;
+  return DRTOPK_OK;
+}
+
+#define DRTOPK_CU(call)                          \
+  do {                                           \
+    cudaError_t e_ = (call);                     \
+    if (e_ != cudaSuccess) {                     \
+      st = cuda_status(e_);                      \
+      goto done;                                 \
+    }                                            \
+  } while (0)
+
+drtopk_status run_query(const void* keys, int dtype, int64_t n, int64_t k, int alpha, int beta,
+                        void* out_keys, int32_t* out_idx, void* out_kth, drtopk_stats* stats,
+                        cudaStream_t s) {
+  drtopk_status st = check_args(keys, dtype, n, k);
+  if (st != DRTOPK_OK) return st;
+  const bool topk = out_keys != nullptr || out_idx != nullptr;
+  if (!topk && !out_kth) return DRTOPK_ERR_INVALID;
+  if (alpha > 0 && (alpha < kMinAlpha || alpha > kMaxAlpha)) return DRTOPK_ERR_INVALID;
+  if (beta > kMaxBeta) return DRTOPK_ERR_INVALID;
+  Plan P;
+  if (!make_plan(n, k, alpha, beta, &P)) return DRTOPK_ERR_INVALID;
+  int sms = 0;
+  st = dev_info(&sms);
+  if (st != DRTOPK_OK) return st;
+
+  const Layout L = layout(P, k, topk, false);
+  char* ws = nullptr;
+  StageTimer tm(s);
+  Work w;
+  {
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ws), L.total, s);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  w.ctl = reinterpret_cast<Ctl*>(ws + L.ctl);
+  w.dkeys = reinterpret_cast<uint32_t*>(ws + L.dkeys);
+  w.dsegs = reinterpret_cast<uint16_t*>(ws + L.dsegs);
+  w.g = reinterpret_cast<uint64_t*>(ws + L.g);
+  w.sv = reinterpret_cast<uint64_t*>(ws + L.sv);
+  w.w = reinterpret_cast<uint64_t*>(ws + L.w);
+  w.w2 = reinterpret_cast<uint64_t*>(ws + L.w2);
+  w.tcnt = reinterpret_cast<uint32_t*>(ws + L.tcnt);
+  w.bsum = reinterpret_cast<uint32_t*>(ws + L.bsum);
+  w.sort_hist = reinterpret_cast<uint32_t*>(ws + L.shist);
+  w.n = n;
+  w.S = P.S;
+  w.g_cap = P.g_cap;
+  w.k = k;
+  w.alpha = P.alpha;
+  w.beta = P.beta;
+  w.dtype = dtype;
+
+  DRTOPK_CU(cudaMemsetAsync(w.ctl, 0, sizeof(Ctl), s));
+  tm.begin(0);
+  DRTOPK_CU(launch_delegates(w, keys, P.fuse_hist, sms, s));
+  note_launch();
+  tm.end();
+  if (P.fuse_hist) {
+    tm.begin(1);
+    DRTOPK_CU(launch_threshold(w, sms, s));
+    tm.end();
+  }
+  tm.begin(2);
+  DRTOPK_CU(launch_filter(w, keys, !topk, sms, s));
+  tm.end();
+  if (topk) {
+    tm.begin(3);
+    DRTOPK_CU(launch_ties(w, keys, sms, s));
+    tm.end();
+  }
+  tm.begin(4);
+  DRTOPK_CU(launch_gselect(w, !topk, sms, s));
+  if (!topk) DRTOPK_CU(launch_write_kth(w, out_kth, s));
+  tm.end();
+  if (topk) {
+    tm.begin(5);
+    DRTOPK_CU(launch_sort_output(w, out_keys, out_idx, out_kth, sms, s));
+    tm.end();
+  }
+  if (stats) {
+    Ctl c;
+    DRTOPK_CU(cudaMemcpyAsync(&c, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    DRTOPK_CU(cudaStreamSynchronize(s));
+    std::memset(stats, 0, sizeof(*stats));
+    stats->alpha = P.alpha;
+    stats->beta = P.beta;
+    stats->subranges = P.S;
+    stats->tau = c.tau;
+    stats->kth_mapped = c.kth_mapped;
+    stats->greater = c.g_count;
+    stats->ties_needed = (c.mode == kModeTies) ? c.need : 0;
+    stats->scanned = c.scanned;
+    stats->tie_scanned = c.tie_scanned;
+    stats->survivors = c.sv_count;
+    stats->emitted = c.w_count;
+    stats->error = c.error;
+    if (c.error & kErrTimeout) st = DRTOPK_ERR_TIMEOUT;
+  }
+done:
+  {
+    cudaError_t e = cudaFreeAsync(ws, s);
+    if (st == DRTOPK_OK && e != cudaSuccess) st = cuda_status(e);
+  }
+  return st;
+}
+
+}  // namespace
+}  // namespace drtopk
+
+using namespace drtopk;
+
+extern "C" {
+
+const char* drtopk_status_str(drtopk_status s) {
+  switch (s) {
+    case DRTOPK_OK: return "DRTOPK_OK";
+    case DRTOPK_ERR_INVALID: return "DRTOPK_ERR_INVALID";
+    case DRTOPK_ERR_K: return "DRTOPK_ERR_K";
+    case DRTOPK_ERR_DTYPE: return "DRTOPK_ERR_DTYPE";
+    case DRTOPK_ERR_NOMEM: return "DRTOPK_ERR_NOMEM";
+    case DRTOPK_ERR_CUDA: return "DRTOPK_ERR_CUDA";
+    case DRTOPK_ERR_BUDGET: return "DRTOPK_ERR_BUDGET";
+    case DRTOPK_ERR_TIMEOUT: return "DRTOPK_ERR_TIMEOUT";
+    case DRTOPK_PENDING: return "DRTOPK_PENDING";
+  }
+  return "DRTOPK_UNKNOWN_STATUS";
+}
+
+drtopk_status drtopk_plan(int64_t n, int64_t k, int* alpha, int* beta, size_t* workspace_bytes) {
+  if (n < 1 || n > 0x7FFFFFFFLL) return DRTOPK_ERR_INVALID;
+  if (k < 1 || k > n) return DRTOPK_ERR_K;
+  Plan P;
+  if (!make_plan(n, k, 0, 0, &P)) return DRTOPK_ERR_INVALID;
+  if (alpha) *alpha = P.alpha;
+  if (beta) *beta = P.beta;
+  if (workspace_bytes) *workspace_bytes = layout(P, k, true, false).total;
+  return DRTOPK_OK;
+}
+
+drtopk_status drtopk_kth(const void* keys, drtopk_dtype dtype, int64_t n, int64_t k,
+                         void* out_kth, void* stream) {
+  if (!out_kth) return DRTOPK_ERR_INVALID;
+  return run_query(keys, dtype, n, k, 0, 0, nullptr, nullptr, out_kth, nullptr,
+                   static_cast<cudaStream_t>(stream));
+}
+
+drtopk_status drtopk_topk(const void* keys, drtopk_dtype dtype, int64_t n, int64_t k,
+                          void* out_keys, int32_t* out_idx, void* stream) {
+  if (!out_keys || !out_idx) return DRTOPK_ERR_INVALID;
+  return run_query(keys, dtype, n, k, 0, 0, out_keys, out_idx, nullptr, nullptr,
+                   static_cast<cudaStream_t>(stream));
+}
+
+drtopk_status drtopk_topk_ex(const void* keys, drtopk_dtype dtype, int64_t n, int64_t k,
+                             int alpha, int beta, void* out_keys, int32_t* out_idx,
+                             void* out_kth, drtopk_stats* stats, void* stream) {
+  if ((out_keys == nullptr) != (out_idx == nullptr)) return DRTOPK_ERR_INVALID;
+  if (alpha < 0 || beta < 0) return DRTOPK_ERR_INVALID;
+  return run_query(keys, dtype, n, k, alpha, beta, out_keys, out_idx, out_kth, stats,
+                   static_cast<cudaStream_t>(stream));
+}
+
+drtopk_status drtopk_delegates(const void* keys, drtopk_dtype dtype, int64_t n, int alpha,
+                               int beta, uint32_t* d_keys, int32_t* d_idx, void* stream) {
+  drtopk_status st = check_args(keys, dtype, n, 1);
+  if (st != DRTOPK_OK) return st;
+  if (!d_keys || !d_idx) return DRTOPK_ERR_INVALID;
+  if (alpha < kMinAlpha || alpha > kMaxAlpha || beta < 1 || beta > kMaxBeta ||
+      (1 << alpha) < beta)
+    return DRTOPK_ERR_INVALID;
+  Plan P;
+  if (!make_plan(n, 1, alpha, beta, &P)) return DRTOPK_ERR_INVALID;
+  int sms = 0;
+  st = dev_info(&sms);
+  if (st != DRTOPK_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t bytes = al(sizeof(Ctl)) + al(static_cast<size_t>(P.S) * beta * 2);
+  char* ws = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ws), bytes, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  Work w;
+  std::memset(&w, 0, sizeof(w));
+  w.ctl = reinterpret_cast<Ctl*>(ws);
+  w.dkeys = d_keys;
+  w.dsegs = reinterpret_cast<uint16_t*>(ws + al(sizeof(Ctl)));
+  w.n = n;
+  w.S = P.S;
+  w.k = 1;
+  w.alpha = alpha;
+  w.beta = beta;
+  w.dtype = dtype;
+  e = cudaMemsetAsync(w.ctl, 0, sizeof(Ctl), s);
+  if (e == cudaSuccess) {
+    e = launch_delegates(w, keys, false, sms, s);
+    note_launch();
+  }
+  if (e == cudaSuccess) e = launch_resolve_delegates(w, keys, d_idx, s);
+  cudaError_t e2 = cudaFreeAsync(ws, s);
+  if (e == cudaSuccess) e = e2;
+  return cuda_status(e);
+}
+
+drtopk_status drtopk_topk_host(const void* keys, drtopk_dtype dtype, int64_t n, int64_t k,
+                               void* out_keys, int32_t* out_idx, void* stream) {
+  drtopk_status st = check_args(keys, dtype, n, k);
+  if (st != DRTOPK_OK) return st;
+  if (!out_keys || !out_idx) return DRTOPK_ERR_INVALID;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* d = nullptr;
+  const size_t kb = al(static_cast<size_t>(n) * 4);
+  const size_t ob = al(static_cast<size_t>(k) * 4);
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&d), kb + 2 * ob, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  e = cudaMemcpyAsync(d, keys, static_cast<size_t>(n) * 4, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    st = run_query(d, dtype, n, k, 0, 0, d + kb, reinterpret_cast<int32_t*>(d + kb + ob), nullptr,
+                   nullptr, s);
+    if (st == DRTOPK_OK) {
+      e = cudaMemcpyAsync(out_keys, d + kb, static_cast<size_t>(k) * 4, cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out_idx, d + kb + ob, static_cast<size_t>(k) * 4,
+                            cudaMemcpyDeviceToHost, s);
+    }
+  }
+  cudaError_t e2 = cudaFreeAsync(d, s);
+  cudaError_t e3 = cudaStreamSynchronize(s);
+  if (st != DRTOPK_OK) return st;
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = e3;
+  return cuda_status(e);
+}
+
+drtopk_status drtopk_profile_begin(void) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  for (auto& r : g_prof) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  g_prof.clear();
+  g_prof_on = true;
+  return DRTOPK_OK;
+}
+
+drtopk_status drtopk_profile_end(drtopk_profile* out) {
+  std::vector<StageRec> recs;
+  {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_on = false;
+    recs.swap(g_prof);
+  }
+  drtopk_status st = DRTOPK_OK;
+  if (out) std::memset(out, 0, sizeof(*out));
+  for (auto& r : recs) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess)
+      st = DRTOPK_ERR_CUDA;
+    else if (out && r.stage >= 0 && r.stage < DRTOPK_NUM_STAGES) {
+      out->ms[r.stage] += ms;
+      out->launches[r.stage] += 1;
+    }
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  return st;
+}
+
+uint64_t drtopk_launch_count(void) { return g_launches.load(); }
+
+}  // extern "C"

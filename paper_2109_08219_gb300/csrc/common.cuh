@@ -1,0 +1,259 @@
+// Shared device-side definitions of the drtopk CUDA library (sm_103a).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "drtopk.h"
+
+namespace drtopk {
+
+// ---------------------------------------------------------------- limits ---
+constexpr int kMaxBeta = 4;
+constexpr int kMinAlpha = 2;
+constexpr int kMaxAlpha = 16;
+// Bounded spin: a device-side wait gives up after this many polls and sets
+// kErrTimeout in the control block instead of hanging.
+constexpr uint32_t kSpinLimit = 1u << 24;
+
+// Device error flags (Ctl::error).
+constexpr uint32_t kErrTimeout = 1u;
+constexpr uint32_t kErrOverflowG = 2u;
+constexpr uint32_t kErrOverflowW = 4u;
+constexpr uint32_t kErrTieRank = 8u;
+
+// Query modes decided on the device after the filter.
+constexpr uint32_t kModeSelect = 0;  // |{x > tau}| >= k: select among them
+constexpr uint32_t kModeTies = 1;    // |{x > tau}| < k: k-th key is tau
+
+// ------------------------------------------------------------- key map -----
+// Order-preserving map of a raw 32-bit key to u32 (unsigned order == key
+// order). u32: identity. i32: flip the sign bit. f32: negative floats flip
+// all bits, non-negative floats set the sign bit.
+template <int DT>
+__device__ __forceinline__ uint32_t map_key(uint32_t b) {
+  if constexpr (DT == DRTOPK_U32) {
+    return b;
+  } else if constexpr (DT == DRTOPK_I32) {
+    return b ^ 0x80000000u;
+  } else {
+    return b ^ (static_cast<uint32_t>(static_cast<int32_t>(b) >> 31) | 0x80000000u);
+  }
+}
+
+__host__ __device__ __forceinline__ uint32_t unmap_key(int dt, uint32_t m) {
+  if (dt == DRTOPK_U32) return m;
+  if (dt == DRTOPK_I32) return m ^ 0x80000000u;
+  return (m & 0x80000000u) ? (m & 0x7FFFFFFFu) : ~m;
+}
+
+// Output composite: larger key first, then smaller index. Unique per element.
+__device__ __forceinline__ uint64_t make_comp(uint32_t mkey, uint32_t idx) {
+  return (static_cast<uint64_t>(mkey) << 32) | static_cast<uint32_t>(~idx);
+}
+__device__ __forceinline__ uint32_t comp_key(uint64_t c) { return static_cast<uint32_t>(c >> 32); }
+__device__ __forceinline__ uint32_t comp_idx(uint64_t c) { return ~static_cast<uint32_t>(c); }
+
+// Delegate composite used while merging per-thread lists: (key, segment)
+// with the smaller segment first among equal keys. An empty slot is 0,
+// which loses every tie against a real element (its ~seg is never 0).
+constexpr uint32_t kNoSeg = 0xFFFFu;
+__device__ __forceinline__ uint64_t make_dc(uint32_t key, uint32_t seg) {
+  return (static_cast<uint64_t>(key) << 32) | static_cast<uint32_t>(0xFFFFu - seg);
+}
+__device__ __forceinline__ uint32_t dc_key(uint64_t c) { return static_cast<uint32_t>(c >> 32); }
+__device__ __forceinline__ uint32_t dc_seg(uint64_t c) { return 0xFFFFu - static_cast<uint32_t>(c & 0xFFFFu); }
+
+// ---------------------------------------------------- radix select state ---
+// Most-significant-digit radix select with 8-bit digits (Sec. 4.1 uses
+// radix top-k with 8-bit digits for both selections). hist[p] counts the
+// digit p of the keys that still match the selected prefix; the last block
+// of each pass picks the digit that holds the k_rem-th largest key.
+template <int NPASS>
+struct SelState {
+  uint32_t hist[NPASS][256];
+  uint32_t ticket[NPASS];
+  uint32_t level;    // number of resolved digits
+  uint32_t k_rem;    // rank (1-based, from the top) inside the current bucket
+  uint32_t bucket;   // count of the current bucket
+  uint32_t done;     // set once the bucket count equals k_rem (top-k mode)
+  uint64_t prefix;   // resolved digits, most significant first, left-aligned
+};
+
+// Control block of one query, zeroed by the host before the first launch.
+struct Ctl {
+  SelState<4> dsel;  // threshold select over the delegate keys
+  SelState<8> gsel;  // second select over (key, idx) composites
+  uint32_t tau;      // threshold (mapped)
+  uint32_t tau_ready;
+  uint32_t mode;
+  uint32_t need;     // ties at tau still needed (mode == kModeTies)
+  uint32_t g_count;  // |{x > tau}| written to G
+  uint32_t sv_count; // survivors of the first digit
+  uint32_t w_count;  // outputs written to W
+  uint32_t error;
+  uint32_t scanned;
+  uint32_t tie_scanned;
+  uint32_t filter_ticket;
+  uint32_t sort_cur;  // which sort buffer holds the data
+  uint32_t kth_mapped;
+  uint32_t pad_;
+};
+
+// Device views of the workspace of one query.
+struct Work {
+  uint32_t* dkeys;    // [S * beta] delegate keys (mapped), descending
+  uint16_t* dsegs;    // [S * beta] delegate segment ids (kNoSeg = pad)
+  uint64_t* g;        // [g_cap] composites of {x > tau}
+  uint64_t* sv;       // [g_cap] survivors of the first digit
+  uint64_t* w;        // [k] winners (unsorted), later sorted
+  uint64_t* w2;       // [k] sort ping-pong buffer
+  uint32_t* tcnt;     // [S] tie counts per subrange (bit 31: lower bound)
+  uint32_t* bsum;     // [nblk] block sums for the tie scans
+  uint32_t* sort_hist;  // radix sort digit counts
+  Ctl* ctl;
+  int64_t n;
+  int64_t S;
+  int64_t g_cap;
+  int64_t k;
+  int alpha;
+  int beta;
+  int dtype;
+};
+
+// -------------------------------------------------------- small helpers ---
+__host__ __device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// ---- mbarrier + TMA bulk copy (inline PTX) --------------------------------
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait on an mbarrier phase: false when kSpinLimit polls passed.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  for (uint32_t it = 0; it < kSpinLimit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+// 1-D bulk copy global -> shared, completion counted on `bar` in bytes.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes,
+                                            uint64_t* bar, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+      : "memory");
+}
+
+// ---- warp-aggregated append ------------------------------------------------
+// Each lane contributes `cnt` items; returns the lane's first slot.
+__device__ __forceinline__ uint32_t warp_append(uint32_t* counter, uint32_t cnt) {
+  const uint32_t lane = lane_id();
+  uint32_t incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= static_cast<uint32_t>(o)) incl += v;
+  }
+  const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+  uint32_t base = 0;
+  if (lane == 31 && total) base = atomicAdd(counter, total);
+  base = __shfl_sync(0xFFFFFFFFu, base, 31);
+  return base + incl - cnt;
+}
+
+// ---- last-block-done helper --------------------------------------------------
+// Called by all threads after a block has published its partial results
+// with global atomics. Returns true in exactly one block: the last to arrive.
+__device__ __forceinline__ bool last_block(uint32_t* ticket) {
+  __shared__ uint32_t s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const uint32_t t = atomicAdd(ticket, 1u);
+    s_last = (t == gridDim.x - 1) ? 1u : 0u;
+  }
+  __syncthreads();
+  if (s_last) __threadfence();
+  return s_last != 0;
+}
+
+// Picks the digit holding the k_rem-th largest of the histogram `h` (in
+// global memory, read with L2-coherent loads) and advances the selection.
+// Executed by warp 0 of the last block only. Returns the bucket count.
+template <int NPASS>
+__device__ inline void select_digit(SelState<NPASS>* st, int pass, int total_bits,
+                                    bool allow_done) {
+  const uint32_t lane = lane_id();
+  uint32_t c[8];
+  uint32_t sum = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    c[j] = __ldcg(&st->hist[pass][lane * 8 + j]);
+    sum += c[j];
+  }
+  // suffix sums over lanes: above[l] = sum of lanes > l
+  uint32_t incl = sum;  // inclusive suffix
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t v = __shfl_down_sync(0xFFFFFFFFu, incl, o);
+    if (lane + o < 32) incl += v;
+  }
+  const uint32_t above = incl - sum;
+  const uint32_t k_rem = st->k_rem;
+  // the lane whose bins hold the k_rem-th largest: above < k_rem <= incl
+  const bool mine = (above < k_rem) && (k_rem <= incl);
+  const uint32_t who = __ffs(__ballot_sync(0xFFFFFFFFu, mine));
+  if (who != 0 && lane == who - 1) {
+    uint32_t acc = above;
+    int d = 7;
+    for (; d > 0; --d) {
+      if (acc + c[d] >= k_rem) break;
+      acc += c[d];
+    }
+    const uint32_t digit = lane * 8 + d;
+    const uint32_t nk = k_rem - acc;
+    const int shift = total_bits - 8 * (pass + 1);
+    st->prefix |= static_cast<uint64_t>(digit) << shift;
+    st->k_rem = nk;
+    st->bucket = c[d];
+    st->level = pass + 1;
+    if (allow_done && c[d] == nk) st->done = 1;
+    __threadfence();
+  }
+}
+
+}  // namespace drtopk
