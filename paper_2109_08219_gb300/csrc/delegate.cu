@@ -332,7 +332,11 @@ __global__ void __launch_bounds__(kThreads, 2) delegate_kernel(DelegParams p) {
       if (v) atomicAdd(&p.ctl->dsel.hist[0][i], v);
     }
     if (last_block(&p.ctl->dsel.ticket[0])) {
-      if (warp == 0) select_digit<4>(&p.ctl->dsel, 0, 32, false);
+      if (warp == 0) {
+        if (lane == 0) p.ctl->dsel.k_rem = p.k;
+        __syncwarp();
+        select_digit<4>(&p.ctl->dsel, 0, 32, false);
+      }
     }
   }
 }
