@@ -1,0 +1,407 @@
+#!/usr/bin/env python3
+"""Benchmark of delegate-centric top-k on GB300 (one JSON line on stdout).
+
+Workload (default): exact top-k over n = 2^30 uint32 keys, five adversarial
+distributions for delegate filtering (ascending, descending, all-equal, 16
+distinct values, Zipf(1.1) over [0, 2^32)) and k in {1024, 2^20}. One step
+= the 10 queries, inputs resident in HBM (4 GiB each, larger than L2, so no
+flush is needed). value = keys processed / second (Gkeys/s) over all ranks.
+
+Extra measurements in the same line:
+  roofline      delegate pass (the kernel that streams all n keys):
+                algorithmic bytes 4n per launch / mean CUDA-event duration on
+                the launching stream, against MEASURED_PEAKS.json hbm_gbs;
+  e2e           same metric through drtopk_topk_host (host keys in pinned
+                memory, H2D copy and D2H of the results inside the timing);
+  cpu_baseline  the CPU oracle (single thread) on a bounded sample;
+  clocks        nvidia-smi samples taken during the timed region;
+  breakdown     per (distribution, k): ms, candidates kept, stage times.
+
+--impl reference times the CPU oracle instead (rank 0 only).
+Multi-GPU (torchrun): every rank runs the same workload on its own GPU
+(independent replicas, weak scaling); value sums all ranks over the max time.
+"""
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+DISTS = ["ascending", "descending", "all_equal", "distinct16", "zipf"]
+KS = [1024, 1 << 20]
+SEED = 3
+PAPER_UD_MS = 6.4  # Dr. Top-k radix, |V| = 2^30 UD, k = 1024, V100S (Sec. 5.1)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="drtopk", choices=["drtopk", "reference"])
+    ap.add_argument("--log2n", type=int, default=30)
+    ap.add_argument("--dists", default=",".join(DISTS))
+    ap.add_argument("--ks", default=",".join(str(k) for k in KS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip breakdown/context runs")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------- clocks ----
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.samples = []
+        self.proc = None
+        self.index = index
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.time(), line.strip()))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        rows = [s for (t, s) in self.samples if t0 - 0.15 <= t <= t1 + 0.15]
+        if not rows and self.samples:
+            # the timed region is shorter than the sampling period: nearest sample
+            mid = 0.5 * (t0 + t1)
+            rows = [min(self.samples, key=lambda ts: abs(ts[0] - mid))[1]]
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            f = [x.strip() for x in r.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------- distributed ----
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl")
+        else:
+            dist.init_process_group("gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda") if torch.cuda.is_available() else torch.device("cpu")
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------ oracle leg ---
+def oracle_sample(dists, ks, sample_log2, reps=1, data=None):
+    """Single-thread CPU oracle over the first 2^sample_log2 keys of each query
+    (the generators are element-wise in the index, so a prefix of the full
+    input is the same array at the smaller size)."""
+    import numpy as np
+    import oracle
+    from paper_2109_08219_gb300 import inputs
+    m = 1 << sample_log2
+    if data is None:
+        data = {d: inputs.DISTRIBUTIONS[d](m, SEED).numpy().view(np.uint32) for d in dists}
+    oracle.topk(data[dists[0]][:1024], oracle.U32, 1)  # load the library
+    keys = 0
+    t = 0.0
+    for _ in range(reps):
+        for d in dists:
+            for k in ks:
+                kk = min(k, m)
+                t0 = time.perf_counter()
+                oracle.topk(data[d], oracle.U32, kk)
+                t += time.perf_counter() - t0
+                keys += m
+    return keys, t
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    dists = args.dists.split(",")
+    ks = [int(x) for x in args.ks.split(",")]
+    import numpy as np
+    from paper_2109_08219_gb300 import inputs
+    sample_log2 = min(21, args.log2n)
+    m = 1 << sample_log2
+    data = {d: inputs.DISTRIBUTIONS[d](m, SEED).numpy().view(np.uint32) for d in dists}
+    for _ in range(args.warmup):
+        oracle_sample(dists, ks, sample_log2, data=data)
+    keys, t = oracle_sample(dists, ks, sample_log2, reps=args.steps, data=data)
+    gk = keys / t / 1e9
+    sample = ("first 2^%d keys of each of the %d (distribution, k) queries, %d steps"
+              % (sample_log2, len(dists) * len(ks), args.steps))
+    out = {
+        "impl": "reference",
+        "metric": "top-k throughput (n=2^%d u32, adversarial distributions)" % args.log2n,
+        "value": gk, "unit": "Gkeys/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": workload_config(args, dists, ks),
+        "cpu_baseline": {"value": gk, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": gk, "unit": "Gkeys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+def workload_config(args, dists, ks):
+    return {"workload": "top-k, n=2^%d uint32 keys, distributions %s, k in %s, 1 query per "
+                        "(distribution, k) per step" % (args.log2n, "/".join(dists),
+                                                       "/".join(str(k) for k in ks)),
+            "n": 1 << args.log2n, "k": ks, "distributions": dists, "seed": SEED,
+            "queries_per_step": len(dists) * len(ks),
+            "l2": "inputs larger than L2 (%d MiB each); no flush" % ((4 << args.log2n) >> 20)}
+
+
+# ----------------------------------------------------------------- main ----
+def main():
+    args = parse()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import numpy as np
+    import torch
+    import paper_2109_08219_gb300 as drtopk
+    from paper_2109_08219_gb300 import build as libbuild
+    from paper_2109_08219_gb300 import inputs
+
+    libbuild.build()
+    dev = torch.device("cuda", local if world > 1 else torch.cuda.current_device())
+    torch.cuda.set_device(dev)
+    dists = args.dists.split(",")
+    ks = [int(x) for x in args.ks.split(",")]
+    n = 1 << args.log2n
+    xs = {d: inputs.DISTRIBUTIONS[d](n, SEED, device=dev) for d in dists}
+    outs = {k: (torch.empty(k, dtype=torch.int32, device=dev),
+                torch.empty(k, dtype=torch.int32, device=dev)) for k in ks}
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for d in dists:
+            for k in ks:
+                drtopk.drtopk_topk(xs[d], k, out_keys=outs[k][0], out_idx=outs[k][1],
+                                   dtype="u32", stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    clk = ClockSampler(dev.index if dev.index is not None else 0) if rank == 0 else None
+    if clk is not None:
+        time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    launches0 = drtopk.launch_count()
+    drtopk.profile_begin()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    tw0 = time.time()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    tw1 = time.time()
+    prof = drtopk.profile_end()
+    launches = drtopk.launch_count() - launches0
+    barrier(world)
+    ms = ev0.elapsed_time(ev1)
+    ms_max = max_over_ranks(ms, world)
+    if clk is not None:
+        time.sleep(0.2)
+        clk.stop()
+    queries = len(dists) * len(ks)
+    keys_all = float(n) * queries * args.steps * world
+    value = keys_all / (ms_max * 1e-3) / 1e9
+
+    if rank != 0:
+        return
+
+    # roofline of the delegate pass
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if peak else "fallback"
+    if not peak:
+        peak = 6800.0
+    dms, dl = prof["delegate"]
+    achieved = (4.0 * n) / ((dms / max(dl, 1)) * 1e-3) / 1e9 if dl else None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "kernel": "delegate_kernel (TMA-streamed delegate pass)",
+                "algorithmic_bytes_per_launch": 4 * n, "launches": dl,
+                "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs, copy burst)" % peak_src,
+                "frac_vs_nominal_8TBps": (achieved / 8000.0) if achieved else None,
+                "end_to_end_frac_of_peak": (4.0 * n * queries * args.steps / (ms * 1e-3) / 1e9) / peak}
+    stage_ms = {k: (v[0] / max(v[1], 1)) for k, v in prof.items()}
+
+    out = {
+        "metric": "top-k throughput (n=2^%d u32, adversarial distributions)" % args.log2n,
+        "value": value, "unit": "Gkeys/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": workload_config(args, dists, ks),
+        "roofline": roofline,
+        "gpu_launches": launches,
+        "stage_ms_per_query": stage_ms,
+    }
+    if clk is not None:
+        out["clocks"] = clk.summary(tw0, tw1)
+
+    # breakdown per query + candidate statistics + context UD line
+    if not args.no_extra:
+        bd = []
+        for d in dists:
+            for k in ks:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                reps = 5
+                e0.record(stream)
+                for _ in range(reps):
+                    drtopk.drtopk_topk(xs[d], k, out_keys=outs[k][0], out_idx=outs[k][1],
+                                       dtype="u32", stream=stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                qms = e0.elapsed_time(e1) / reps
+                _, _, _, st = drtopk.drtopk_topk_ex(xs[d], k, want_kth=False, dtype="u32")
+                bd.append({"dist": d, "k": k, "ms": qms, "gkeys_s": n / qms / 1e6,
+                           "alpha": st["alpha"], "beta": st["beta"],
+                           "candidate_fraction": (st["greater"] + st["ties_needed"]) / n,
+                           "workload_fraction": (st["beta"] * st["subranges"] + st["greater"]
+                                                 + st["ties_needed"]) / n,
+                           "greater": st["greater"], "ties_needed": st["ties_needed"],
+                           "scanned_subranges": st["scanned"],
+                           "tie_scanned_subranges": st["tie_scanned"]})
+        out["breakdown"] = bd
+        # context: the paper's headline setting (UD, k = 1024) on this GPU
+        ud = inputs.uniform_u32(n, 1, device=dev)
+        o1 = (torch.empty(1024, dtype=torch.int32, device=dev),
+              torch.empty(1024, dtype=torch.int32, device=dev))
+        for _ in range(3):
+            drtopk.drtopk_topk(ud, 1024, out_keys=o1[0], out_idx=o1[1], dtype="u32")
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(20):
+            drtopk.drtopk_topk(ud, 1024, out_keys=o1[0], out_idx=o1[1], dtype="u32")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ums = e0.elapsed_time(e1) / 20
+        out["context_uniform_k1024"] = {
+            "ms": ums, "gkeys_s": n / ums / 1e6, "hbm_frac_of_measured": (4.0 * n / ums / 1e6) / peak,
+            "paper_ms_v100s": PAPER_UD_MS if args.log2n == 30 else None,
+            "note": "paper number is V100S (1134 GB/s), context only"}
+        del ud
+
+    if not args.no_cpu and world == 1:
+        sample_log2 = min(26, args.log2n)
+        m = 1 << sample_log2
+        data = {d: xs[d][:m].cpu().numpy().view(np.uint32) for d in dists}
+        keys, t = oracle_sample(dists, ks, sample_log2, data=data)
+        out["cpu_baseline"] = {"value": keys / t / 1e9, "unit": "Gkeys/s", "cores": 1,
+                               "kind": "oracle",
+                               "sample": "first 2^%d keys of each of the %d (distribution, k) "
+                                         "queries, once (std::nth_element + sort, 1 thread)"
+                                         % (sample_log2, queries)}
+
+    # end to end through the host entry point
+    if not args.no_e2e:
+        hosts = {}
+        for d in dists:
+            h = torch.empty(n, dtype=torch.int32, pin_memory=True)
+            h.copy_(xs[d])
+            hosts[d] = h
+        hk = {k: (torch.empty(k, dtype=torch.int32, pin_memory=True),
+                  torch.empty(k, dtype=torch.int32, pin_memory=True)) for k in ks}
+        # free the device copies: the host path stages its own
+        del xs
+        torch.cuda.empty_cache()
+
+        def estep():
+            for d in dists:
+                for k in ks:
+                    drtopk.drtopk_topk_host_ptr(hosts[d].data_ptr(), n, k, "u32",
+                                                hk[k][0].data_ptr(), hk[k][1].data_ptr())
+        estep()
+        esteps = max(2, min(args.steps, 5))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(esteps):
+            estep()
+        torch.cuda.synchronize()
+        et = time.perf_counter() - t0
+        out["e2e"] = {"value": float(n) * queries * esteps / et / 1e9, "unit": "Gkeys/s",
+                      "h2d_bytes_per_step": 4 * n * queries,
+                      "d2h_bytes_per_step": 8 * sum(ks) * len(dists),
+                      "steps": esteps, "api": "drtopk_topk_host (pinned host keys)"}
+
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()
