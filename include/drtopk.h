@@ -141,6 +141,31 @@ drtopk_status drtopk_delegates(const void* keys, drtopk_dtype dtype,
                                void* stream);
 
 /*
+ * k-selection without any allocation (the paper has no counterpart; this
+ * entry point exists for callers that may not allocate device memory while
+ * serving queries, e.g. pipelines that forbid allocation after start-up or
+ * processes whose device memory is wholly owned by another allocator).
+ * Same arguments and result as drtopk_kth, but the workspace is a fixed
+ * 64 MiB array inside this library (a file-scope __device__ array): every
+ * GPU that loads the library holds it until the process exits, and no
+ * cudaMalloc, cudaMallocAsync or cudaFree is called.
+ *   - Limit: the query's workspace (delegate keys and segments, the
+ *     candidates above the threshold and their survivors) must fit in
+ *     64 MiB; otherwise the call returns DRTOPK_ERR_NOMEM and launches
+ *     nothing. For n = 2^30 this admits k up to about 4096.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture on the device.
+ *   - All calls on a device share the array, which keeps the previous call's
+ *     contents (the call clears what must start at zero). Calls that overlap
+ *     on the GPU (different streams or threads without ordering between
+ *     them) race on the array and give wrong results: order them.
+ */
+drtopk_status drtopk_kth_noalloc(const void* keys, drtopk_dtype dtype,
+                                 int64_t n, int64_t k, void* out_kth,
+                                 void* stream);
+
+/*
  * top-k of a HOST array: copies keys (host, pinned or pageable) to the
  * device, runs drtopk_topk and copies the results back to host out_keys /
  * out_idx. Synchronous: returns when the host outputs are written.

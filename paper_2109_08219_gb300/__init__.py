@@ -75,6 +75,8 @@ def lib():
                                      ctypes.POINTER(Stats), p]
         L.drtopk_delegates.argtypes = [p, i32, i64, i32, i32, p, p, p]
         L.drtopk_topk_host.argtypes = [p, i32, i64, i64, p, p, p]
+        L.drtopk_kth_noalloc.argtypes = [p, i32, i64, i64, p, p]
+        L.drtopk_kth_noalloc.restype = i32
         L.drtopk_profile_begin.argtypes = []
         L.drtopk_profile_end.argtypes = [ctypes.POINTER(Profile)]
         L.drtopk_launch_count.argtypes = []
@@ -143,6 +145,21 @@ def drtopk_kth(keys, k, out=None, dtype=None, stream=None):
         out = torch.empty(1, dtype=keys.dtype, device=keys.device)
     _check(lib().drtopk_kth(_dev(keys), code, keys.numel(), k, _dev(out), _stream(stream)),
            "drtopk_kth")
+    return out
+
+
+def drtopk_kth_noalloc(keys, k, out=None, dtype=None, stream=None):
+    """k-th largest key using the library's fixed 64 MiB device scratch: no
+    device allocation happens in the call. For callers that may not allocate
+    while serving queries. Raises DrTopkError(DRTOPK_ERR_NOMEM) when the
+    query needs more scratch than the array holds. Calls that overlap on the
+    GPU share the array and race: keep them ordered on one stream."""
+    import torch
+    code = _dtype_code(keys, dtype)
+    if out is None:
+        out = torch.empty(1, dtype=keys.dtype, device=keys.device)
+    _check(lib().drtopk_kth_noalloc(_dev(keys), code, keys.numel(), k, _dev(out),
+                                    _stream(stream)), "drtopk_kth_noalloc")
     return out
 
 
