@@ -59,26 +59,27 @@ bool make_plan(int64_t n, int64_t k, int alpha, int beta, Plan* p) {
 constexpr size_t kAlign = 256;
 size_t al(size_t b) { return (b + kAlign - 1) & ~(kAlign - 1); }
 
-constexpr int kTieSubPerBlock = 2048;
-
 struct Layout {
-  size_t ctl, dkeys, dsegs, g, sv, w, w2, tcnt, bsum, shist, total;
+  size_t ctl, dkeys, dsegs, ds, scanq, g, sv, w, w2, tcnt, bsum, tieq, sstat, total;
 };
 
 Layout layout(const Plan& p, int64_t k, bool need_topk, bool external_dkeys) {
   Layout L;
+  const size_t D = static_cast<size_t>(p.S) * p.beta;
   size_t o = 0;
   L.ctl = o; o += al(sizeof(Ctl));
-  L.dkeys = o; if (!external_dkeys) o += al(static_cast<size_t>(p.S) * p.beta * 4);
-  L.dsegs = o; o += al(static_cast<size_t>(p.S) * p.beta * 2);
+  L.dkeys = o; if (!external_dkeys) o += al(D * 4);
+  L.dsegs = o; o += al(D * 2);
+  L.ds = o; if (p.fuse_hist) o += al(D * 4);
+  L.scanq = o; o += al(static_cast<size_t>(p.S) * 4);
   L.g = o; o += al(static_cast<size_t>(p.g_cap) * 8);
   L.sv = o; o += al(static_cast<size_t>(p.g_cap) * 8);
   L.w = o; if (need_topk) o += al(static_cast<size_t>(k) * 8);
   L.w2 = o; if (need_topk && k > 4096) o += al(static_cast<size_t>(k) * 8);
   L.tcnt = o; if (need_topk) o += al(static_cast<size_t>(p.S) * 4);
-  const int64_t nblk = (p.S + kTieSubPerBlock - 1) / kTieSubPerBlock;
-  L.bsum = o; if (need_topk) o += al(static_cast<size_t>(2 * nblk) * 4);
-  L.shist = o; if (need_topk) o += al(sort_hist_words(k) * 4);
+  L.bsum = o; if (need_topk) o += al(static_cast<size_t>(2 * tie_blocks(p.S)) * 4);
+  L.tieq = o; if (need_topk) o += al(static_cast<size_t>(2 * p.S) * 4);
+  L.sstat = o; if (need_topk) o += al(sort_status_words(k) * 8);
   L.total = o;
   return L;
 }
@@ -193,13 +194,16 @@ drtopk_status run_query(const void* keys, int dtype, int64_t n, int64_t k, int a
   w.ctl = reinterpret_cast<Ctl*>(ws + L.ctl);
   w.dkeys = reinterpret_cast<uint32_t*>(ws + L.dkeys);
   w.dsegs = reinterpret_cast<uint16_t*>(ws + L.dsegs);
+  w.ds = reinterpret_cast<uint32_t*>(ws + L.ds);
+  w.scanq = reinterpret_cast<uint32_t*>(ws + L.scanq);
   w.g = reinterpret_cast<uint64_t*>(ws + L.g);
   w.sv = reinterpret_cast<uint64_t*>(ws + L.sv);
   w.w = reinterpret_cast<uint64_t*>(ws + L.w);
   w.w2 = reinterpret_cast<uint64_t*>(ws + L.w2);
   w.tcnt = reinterpret_cast<uint32_t*>(ws + L.tcnt);
   w.bsum = reinterpret_cast<uint32_t*>(ws + L.bsum);
-  w.sort_hist = reinterpret_cast<uint32_t*>(ws + L.shist);
+  w.tieq = reinterpret_cast<uint32_t*>(ws + L.tieq);
+  w.sort_status = reinterpret_cast<uint64_t*>(ws + L.sstat);
   w.n = n;
   w.S = P.S;
   w.g_cap = P.g_cap;

@@ -89,28 +89,39 @@ struct Ctl {
   uint32_t mode;
   uint32_t need;     // ties at tau still needed (mode == kModeTies)
   uint32_t g_count;  // |{x > tau}| written to G
-  uint32_t sv_count; // survivors of the first digit
+  uint32_t sv_count; // survivors of the first digit of the second select
   uint32_t w_count;  // outputs written to W
   uint32_t error;
   uint32_t scanned;
   uint32_t tie_scanned;
   uint32_t filter_ticket;
-  uint32_t sort_cur;  // which sort buffer holds the data
   uint32_t kth_mapped;
-  uint32_t pad_;
+  uint32_t ds_count;       // delegate keys surviving the first threshold digit
+  uint32_t scanq_count;    // subranges queued for the filter scan
+  uint32_t tieq1_count;    // subranges queued for exact tie counts
+  uint32_t tieq2_count;    // subranges queued for tie emission
+  uint32_t stage_count[10];  // survivors entering each second-select stage
+  uint32_t sort_ticket;
+  uint32_t sort_tiles[8];    // dynamic tile ids of the output radix sort
+  uint32_t sort_hist[8][256];  // digit counts of the output composites
+  uint32_t sort_skip[8];
+  uint32_t pad_[3];
 };
 
 // Device views of the workspace of one query.
 struct Work {
   uint32_t* dkeys;    // [S * beta] delegate keys (mapped), descending
   uint16_t* dsegs;    // [S * beta] delegate segment ids (kNoSeg = pad)
+  uint32_t* ds;       // [S * beta] delegate keys surviving the first digit
+  uint32_t* scanq;    // [S] subranges queued for the filter scan
   uint64_t* g;        // [g_cap] composites of {x > tau}
-  uint64_t* sv;       // [g_cap] survivors of the first digit
+  uint64_t* sv;       // [g_cap] second-select ping-pong buffer
   uint64_t* w;        // [k] winners (unsorted), later sorted
   uint64_t* w2;       // [k] sort ping-pong buffer
   uint32_t* tcnt;     // [S] tie counts per subrange (bit 31: lower bound)
-  uint32_t* bsum;     // [nblk] block sums for the tie scans
-  uint32_t* sort_hist;  // radix sort digit counts
+  uint32_t* bsum;     // [4 * nblk] block sums for the tie scans
+  uint32_t* tieq;     // [2 * S] tie queues (subrange ids; emission prefixes)
+  uint64_t* sort_status;  // [8 * tiles * 256] look-back words of the sort
   Ctl* ctl;
   int64_t n;
   int64_t S;
@@ -194,6 +205,58 @@ __device__ __forceinline__ uint32_t warp_append(uint32_t* counter, uint32_t cnt)
   base = __shfl_sync(0xFFFFFFFFu, base, 31);
   return base + incl - cnt;
 }
+
+// ---- block-aggregated append -------------------------------------------------
+// Every thread of the block calls this with its item count; one atomicAdd per
+// block reserves the block's range. Returns the thread's first slot.
+template <int NT>
+__device__ __forceinline__ uint32_t block_append(uint32_t* counter, uint32_t cnt) {
+  __shared__ uint32_t s_w[NT / 32];
+  __shared__ uint32_t s_base;
+  const uint32_t lane = lane_id();
+  const int warp = threadIdx.x >> 5;
+  uint32_t incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= static_cast<uint32_t>(o)) incl += v;
+  }
+  if (lane == 31) s_w[warp] = incl;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int w = 0; w < NT / 32; ++w) {
+      const uint32_t t = s_w[w];
+      s_w[w] = run;
+      run += t;
+    }
+    s_base = run ? atomicAdd(counter, run) : 0u;
+  }
+  __syncthreads();
+  const uint32_t r = s_base + s_w[warp] + incl - cnt;
+  __syncthreads();
+  return r;
+}
+
+// Thread-local run-length aggregation of shared-histogram increments: equal
+// consecutive bins (skewed or tied data) cost one shared atomic per run.
+struct RunHist {
+  uint32_t bin = 0xFFFFFFFFu;
+  uint32_t cnt = 0;
+  __device__ __forceinline__ void add(uint32_t* sh, uint32_t b) {
+    if (b != bin) {
+      if (cnt) atomicAdd(&sh[bin], cnt);
+      bin = b;
+      cnt = 1;
+    } else {
+      ++cnt;
+    }
+  }
+  __device__ __forceinline__ void flush(uint32_t* sh) {
+    if (cnt) atomicAdd(&sh[bin], cnt);
+    cnt = 0;
+  }
+};
 
 // ---- last-block-done helper --------------------------------------------------
 // Called by all threads after a block has published its partial results

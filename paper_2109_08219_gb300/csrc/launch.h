@@ -37,7 +37,10 @@ cudaError_t launch_write_kth(const Work& w, void* out_kth, cudaStream_t s);
 // Sorts W[0..k) descending and writes out_keys (dtype) / out_idx (sort.cu).
 cudaError_t launch_sort_output(const Work& w, void* out_keys, int32_t* out_idx,
                                void* out_kth, int sms, cudaStream_t s);
-size_t sort_hist_words(int64_t k);
+size_t sort_status_words(int64_t k);
+
+// Number of 2048-subrange blocks of the tie scans (select.cu).
+int64_t tie_blocks(int64_t S);
 
 // Resolves exact delegate positions for drtopk_delegates (select.cu).
 cudaError_t launch_resolve_delegates(const Work& w, const void* keys, int32_t* d_idx,

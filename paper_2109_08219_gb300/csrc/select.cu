@@ -17,6 +17,11 @@
 // per-subrange tie counts taken in index order, reading a subrange again
 // only when its count is not already known from its delegates and an
 // earlier prefix could still be short.
+//
+// GB300 organisation: every variable-size output is appended with one
+// atomic per block (block_append); uneven work (scanned subranges, tie
+// counts) goes through global queues that all warps of the grid drain; each
+// radix pass keeps only the survivors of the previous digit.
 #include "common.cuh"
 #include "launch.h"
 
@@ -29,6 +34,7 @@ constexpr uint32_t kScanned = 0x40000000u;  // tie count came from a scan
 constexpr uint32_t kCountMask = 0x3FFFFFFFu;
 constexpr int kTieSubPerThread = 8;
 constexpr int kTieSubPerBlock = kThreads * kTieSubPerThread;
+constexpr int kScanKPT = 32;  // virtual keys per thread per filter-scan step
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
   uint32_t m;
@@ -36,13 +42,8 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   return m;
 }
 
-// Shared-memory histogram add, aggregated over lanes with the same bin.
-__device__ __forceinline__ void hist_add(uint32_t* sh, uint32_t bin, bool active) {
-  const uint32_t am = __ballot_sync(0xFFFFFFFFu, active);
-  if (active) {
-    const uint32_t peers = __match_any_sync(am, bin);
-    if ((lanemask_lt() & peers) == 0) atomicAdd(&sh[bin], __popc(peers));
-  }
+__device__ __forceinline__ void zero_hist(uint32_t* sh) {
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) sh[i] = 0;
 }
 
 __device__ __forceinline__ void flush_hist(const uint32_t* sh, uint32_t* g) {
@@ -86,36 +87,87 @@ __device__ __forceinline__ int occ_rank(const uint32_t* dk, const uint16_t* ds, 
   return r;
 }
 
+int grid_for(int64_t work, int per_block, int sms, int per_sm) {
+  int64_t g = (work + per_block - 1) / per_block;
+  const int64_t cap = static_cast<int64_t>(sms) * per_sm;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return static_cast<int>(g);
+}
+
 // ------------------------------------------------------------ threshold ---
-__global__ void __launch_bounds__(kThreads) thr_pass_kernel(const uint32_t* dkeys, int64_t count,
-                                                            Ctl* ctl, int pass) {
+// Digit 1 pass: keep the delegate keys whose first digit is the selected
+// one (compacted into ds) and histogram their second digit.
+__global__ void __launch_bounds__(kThreads) thr_compact_kernel(const uint32_t* dkeys,
+                                                               int64_t count, uint32_t* ds,
+                                                               Ctl* ctl) {
   __shared__ uint32_t sh[256];
-  for (int i = threadIdx.x; i < 256; i += kThreads) sh[i] = 0;
+  zero_hist(sh);
   __syncthreads();
   SelState<4>* st = &ctl->dsel;
+  const uint32_t d0 = static_cast<uint32_t>(__ldcg(&st->prefix)) >> 24;
+  RunHist rh;
+  const int64_t step = int64_t(gridDim.x) * kThreads * 16;
+  for (int64_t base = int64_t(blockIdx.x) * kThreads * 16; base < count; base += step) {
+    uint32_t v[16];
+    uint32_t c = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t i0 = base + (int64_t(q) * kThreads + threadIdx.x) * 4;
+      if (i0 + 3 < count) {
+        const uint4 x = __ldcg(reinterpret_cast<const uint4*>(dkeys + i0));
+        v[q * 4 + 0] = x.x; v[q * 4 + 1] = x.y; v[q * 4 + 2] = x.z; v[q * 4 + 3] = x.w;
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) v[q * 4 + e] = (i0 + e < count) ? dkeys[i0 + e] : 0u;
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const bool ok = (i0 + e < count) && ((v[q * 4 + e] >> 24) == d0);
+        c += ok;
+      }
+    }
+    uint32_t slot = block_append<kThreads>(&ctl->ds_count, c);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t i0 = base + (int64_t(q) * kThreads + threadIdx.x) * 4;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const uint32_t x = v[q * 4 + e];
+        if ((i0 + e < count) && ((x >> 24) == d0)) {
+          ds[slot++] = x;
+          rh.add(sh, (x >> 16) & 255u);
+        }
+      }
+    }
+  }
+  rh.flush(sh);
+  __syncthreads();
+  flush_hist(sh, st->hist[1]);
+  if (last_block(&st->ticket[1])) {
+    if (threadIdx.x < 32) select_digit<4>(st, 1, 32, false);
+  }
+}
+
+// Digit 2 and 3 passes over the compacted survivors.
+__global__ void __launch_bounds__(kThreads) thr_pass_kernel(const uint32_t* ds, Ctl* ctl,
+                                                            int pass) {
+  __shared__ uint32_t sh[256];
+  zero_hist(sh);
+  __syncthreads();
+  SelState<4>* st = &ctl->dsel;
+  const int64_t count = __ldcg(&ctl->ds_count);
   const uint32_t prefix = static_cast<uint32_t>(__ldcg(&st->prefix));
   const uint32_t mask = 0xFFFFFFFFu << (32 - 8 * pass);
   const uint32_t want = prefix & mask;
   const int sh_d = 24 - 8 * pass;
-  const int64_t warps_total = int64_t(gridDim.x) * (kThreads / 32);
-  const int64_t gw = int64_t(blockIdx.x) * (kThreads / 32) + (threadIdx.x >> 5);
-  const uint32_t lane = lane_id();
-  for (int64_t base = gw * 128; base < count; base += warps_total * 128) {
-    const int64_t i0 = base + lane * 4;
-    uint32_t v[4];
-    if (i0 + 3 < count) {
-      const uint4 q = *reinterpret_cast<const uint4*>(dkeys + i0);
-      v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
-    } else {
-#pragma unroll
-      for (int e = 0; e < 4; ++e) v[e] = (i0 + e < count) ? dkeys[i0 + e] : 0;
-    }
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const bool act = (i0 + e < count) && ((v[e] & mask) == want);
-      hist_add(sh, (v[e] >> sh_d) & 255u, act);
-    }
+  RunHist rh;
+  for (int64_t i = int64_t(blockIdx.x) * kThreads + threadIdx.x; i < count;
+       i += int64_t(gridDim.x) * kThreads) {
+    const uint32_t x = ds[i];
+    if ((x & mask) == want) rh.add(sh, (x >> sh_d) & 255u);
   }
+  rh.flush(sh);
   __syncthreads();
   flush_hist(sh, st->hist[pass]);
   if (last_block(&st->ticket[pass])) {
@@ -137,53 +189,44 @@ struct FilterParams {
   int alpha;
   const uint32_t* dkeys;
   const uint16_t* dsegs;
+  uint32_t* scanq;
   uint64_t* g;
   Ctl* ctl;
   int kth_only;
 };
 
-template <int DT>
-__device__ __forceinline__ void emit_g(const FilterParams& p, uint32_t* sh, const uint64_t* items,
-                                       int cnt) {
-  const uint32_t slot = warp_append(&p.ctl->g_count, cnt);
-  for (int e = 0; e < cnt; ++e) {
-    const uint64_t s = uint64_t(slot) + e;
-    if (s < static_cast<uint64_t>(p.g_cap)) p.g[s] = items[e];
-    else atomicOr(&p.ctl->error, kErrOverflowG);
-  }
-}
-
+// One thread per subrange: skip it (m^0 <= tau), queue it for a scan
+// (m^{beta-1} > tau: Rule 3 says every element may qualify) or emit its
+// delegates > tau (Rule 3: they are all of its elements > tau).
 template <int DT, int B>
-__global__ void __launch_bounds__(kThreads) filter_kernel(FilterParams p) {
+__global__ void __launch_bounds__(kThreads) filter_classify_kernel(FilterParams p) {
   __shared__ uint32_t sh[256];
-  for (int i = threadIdx.x; i < 256; i += kThreads) sh[i] = 0;
+  zero_hist(sh);
   __syncthreads();
   const uint32_t tau = __ldcg(&p.ctl->tau);
-  const uint32_t lane = lane_id();
-  const int64_t warps_total = int64_t(gridDim.x) * (kThreads / 32);
-  const int64_t gw = int64_t(blockIdx.x) * (kThreads / 32) + (threadIdx.x >> 5);
   const int alpha = p.alpha;
-
-  for (int64_t base = gw * 32; base < p.S; base += warps_total * 32) {
-    const int64_t i = base + lane;
+  uint32_t nscan = 0;
+  for (int64_t base = int64_t(blockIdx.x) * kThreads; base < p.S;
+       base += int64_t(gridDim.x) * kThreads) {
+    const int64_t i = base + threadIdx.x;
     uint32_t dk[B];
     uint16_t ds[B];
     int cls = 0;  // 0 none, 1 delegates only, 2 scan
-    int64_t len = 0;
     if (i < p.S) {
 #pragma unroll
       for (int j = 0; j < B; ++j) {
         dk[j] = p.dkeys[i * B + j];
         ds[j] = p.dsegs[i * B + j];
       }
-      len = sub_len(i, alpha, p.n);
-      if (dk[0] > tau) cls = (dk[B - 1] > tau && len > B) ? 2 : 1;
+      if (dk[0] > tau) cls = (dk[B - 1] > tau && sub_len(i, alpha, p.n) > B) ? 2 : 1;
     }
-    // delegates-only subranges: their delegates > tau are all of {x > tau}
+    const uint32_t qs = block_append<kThreads>(&p.ctl->scanq_count, cls == 2);
+    if (cls == 2) {
+      p.scanq[qs] = static_cast<uint32_t>(i);
+      ++nscan;
+    }
     uint64_t items[B];
-#pragma unroll
-    for (int j = 0; j < B; ++j) items[j] = 0;
-    int cnt = 0;
+    uint32_t cnt = 0;
     if (cls == 1) {
 #pragma unroll
       for (int j = 0; j < B; ++j) {
@@ -195,39 +238,63 @@ __global__ void __launch_bounds__(kThreads) filter_kernel(FilterParams p) {
         }
       }
     }
-    for (int e = 0; e < B; ++e) hist_add(sh, static_cast<uint32_t>(items[e < cnt ? e : 0] >> 56), e < cnt);
-    emit_g<DT>(p, sh, items, cnt);
+    const uint32_t slot = block_append<kThreads>(&p.ctl->g_count, cnt);
+    for (uint32_t e = 0; e < cnt; ++e) {
+      const uint64_t s = uint64_t(slot) + e;
+      if (s < static_cast<uint64_t>(p.g_cap)) p.g[s] = items[e];
+      else atomicOr(&p.ctl->error, kErrOverflowG);
+      atomicAdd(&sh[static_cast<uint32_t>(items[e] >> 56)], 1u);
+    }
+  }
+  __syncthreads();
+  flush_hist(sh, p.ctl->gsel.hist[0]);
+  if (nscan) atomicAdd(&p.ctl->scanned, nscan);
+}
 
-    // scanned subranges: the whole warp reads each one
-    uint32_t scan_mask = __ballot_sync(0xFFFFFFFFu, cls == 2);
-    if (lane == 0 && scan_mask) atomicAdd(&p.ctl->scanned, __popc(scan_mask));
-    while (scan_mask) {
-      const int src = __ffs(scan_mask) - 1;
-      scan_mask &= scan_mask - 1;
-      const int64_t si = base + src;
-      const int64_t lo = si << alpha;
-      const int64_t slen = sub_len(si, alpha, p.n);
-      for (int64_t off = 0; off < slen; off += 128) {
-        uint64_t it[4];
-        int c2 = 0;
+// All queued subranges read as one virtual array of nq * 2^alpha keys,
+// 8192 per block step, appended with one atomic per block step. The last
+// block decides the query mode.
+template <int DT>
+__global__ void __launch_bounds__(kThreads) filter_scan_kernel(FilterParams p) {
+  __shared__ uint32_t sh[256];
+  zero_hist(sh);
+  __syncthreads();
+  const uint32_t tau = __ldcg(&p.ctl->tau);
+  const int alpha = p.alpha;
+  const int64_t nq = __ldcg(&p.ctl->scanq_count);
+  const int64_t total = nq << alpha;
+  const int64_t mask = (int64_t(1) << alpha) - 1;
+  RunHist rh;
+  const int64_t step = int64_t(gridDim.x) * kThreads * kScanKPT;
+  for (int64_t base = int64_t(blockIdx.x) * kThreads * kScanKPT; base < total; base += step) {
+    uint32_t x[kScanKPT];
+    uint32_t hit = 0;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int64_t t = off + u * 32 + lane;
-          if (t < slen) {
-            const uint32_t x = map_key<DT>(__ldg(p.keys + lo + t));
-            if (x > tau) it[c2++] = make_comp(x, static_cast<uint32_t>(lo + t));
-          }
-        }
-        for (int e = 0; e < 4; ++e) hist_add(sh, static_cast<uint32_t>(it[e < c2 ? e : 0] >> 56), e < c2);
-        const uint32_t slot = warp_append(&p.ctl->g_count, c2);
-        for (int e = 0; e < c2; ++e) {
-          const uint64_t s = uint64_t(slot) + e;
-          if (s < static_cast<uint64_t>(p.g_cap)) p.g[s] = it[e];
-          else atomicOr(&p.ctl->error, kErrOverflowG);
+    for (int u = 0; u < kScanKPT; ++u) {
+      const int64_t v = base + threadIdx.x + int64_t(u) * kThreads;
+      x[u] = 0;
+      if (v < total) {
+        const int64_t gi = (int64_t(__ldg(p.scanq + (v >> alpha))) << alpha) + (v & mask);
+        if (gi < p.n) {
+          x[u] = map_key<DT>(__ldg(p.keys + gi));
+          if (x[u] > tau) hit |= 1u << u;
         }
       }
     }
+    uint32_t slot = block_append<kThreads>(&p.ctl->g_count, __popc(hit));
+#pragma unroll
+    for (int u = 0; u < kScanKPT; ++u) {
+      if (hit & (1u << u)) {
+        const int64_t v = base + threadIdx.x + int64_t(u) * kThreads;
+        const int64_t gi = (int64_t(__ldg(p.scanq + (v >> alpha))) << alpha) + (v & mask);
+        if (slot < p.g_cap) p.g[slot] = make_comp(x[u], static_cast<uint32_t>(gi));
+        else atomicOr(&p.ctl->error, kErrOverflowG);
+        ++slot;
+        rh.add(sh, x[u] >> 24);
+      }
+    }
   }
+  rh.flush(sh);
   __syncthreads();
   flush_hist(sh, p.ctl->gsel.hist[0]);
   if (last_block(&p.ctl->filter_ticket)) {
@@ -253,6 +320,11 @@ __global__ void __launch_bounds__(kThreads) filter_kernel(FilterParams p) {
 }
 
 // --------------------------------------------------------- second select ---
+// Stage s (1..8) reads the composites that match the digits selected so far
+// (stage 1: all of G) and decides digit level s-1: larger digit -> winner
+// (written to W), equal -> survivor for stage s+1 (or winner when the
+// bucket is exactly what is still needed), smaller -> dropped. The last
+// block selects the next digit from the survivors' histogram.
 struct GSelParams {
   uint64_t* g;
   uint64_t* sv;
@@ -262,103 +334,66 @@ struct GSelParams {
   int kth_only;
 };
 
-__global__ void __launch_bounds__(kThreads) gpart_kernel(GSelParams p) {
+__global__ void __launch_bounds__(kThreads) gstage_kernel(GSelParams p, int s) {
   Ctl* ctl = p.ctl;
   if (__ldcg(&ctl->mode) != kModeSelect) return;
+  const int level = s - 1;
+  const int64_t count = (s == 1) ? imin64(__ldcg(&ctl->g_count), p.g_cap)
+                                 : static_cast<int64_t>(__ldcg(&ctl->stage_count[s]));
+  if (count == 0) return;  // uniform over the grid: nothing survived
   __shared__ uint32_t sh[256];
-  for (int i = threadIdx.x; i < 256; i += kThreads) sh[i] = 0;
+  zero_hist(sh);
   __syncthreads();
-  const uint32_t gcount =
-      static_cast<uint32_t>(imin64(__ldcg(&ctl->g_count), p.g_cap));  // overflow is flagged
-  const uint32_t d0 = static_cast<uint32_t>(__ldcg(&ctl->gsel.prefix) >> 56);
-  const bool done0 = __ldcg(&ctl->gsel.done) != 0;
-  const uint32_t lane = lane_id();
-  const int64_t warps_total = int64_t(gridDim.x) * (kThreads / 32);
-  const int64_t gw = int64_t(blockIdx.x) * (kThreads / 32) + (threadIdx.x >> 5);
-  for (int64_t base = gw * 32; base < gcount; base += warps_total * 32) {
-    const int64_t i = base + lane;
-    uint64_t c = 0;
-    int kind = 0;  // 1 winner, 2 survivor
-    if (i < gcount) {
-      c = p.g[i];
-      const uint32_t dg = static_cast<uint32_t>(c >> 56);
-      if (dg > d0 || (dg == d0 && done0)) kind = 1;
-      else if (dg == d0) kind = 2;
-    }
-    if (!p.kth_only) {
-      const uint32_t slot = warp_append(&ctl->w_count, kind == 1);
-      if (kind == 1) {
-        if (slot < p.k) p.w[slot] = c;
-        else atomicOr(&ctl->error, kErrOverflowW);
+  const uint64_t* src = (s & 1) ? p.g : p.sv;
+  uint64_t* dst = (s & 1) ? p.sv : p.g;
+  const uint64_t prefix = __ldcg(&ctl->gsel.prefix);
+  const uint32_t d = static_cast<uint32_t>(prefix >> (56 - 8 * level)) & 255u;
+  const bool done = __ldcg(&ctl->gsel.done) != 0;
+  const bool last = (level == 7);
+  const int nsh = 48 - 8 * level;  // next digit shift
+  RunHist rh;
+  constexpr int IPT = 8;
+  const int64_t stepn = int64_t(gridDim.x) * kThreads * IPT;
+  for (int64_t base = int64_t(blockIdx.x) * kThreads * IPT; base < count; base += stepn) {
+    uint64_t c[IPT];
+    uint32_t win = 0, sur = 0;
+#pragma unroll
+    for (int u = 0; u < IPT; ++u) {
+      const int64_t i = base + threadIdx.x + int64_t(u) * kThreads;
+      c[u] = 0;
+      if (i < count) {
+        c[u] = src[i];
+        const uint32_t dg = static_cast<uint32_t>(c[u] >> (56 - 8 * level)) & 255u;
+        if (dg > d || (dg == d && (done || last))) win |= 1u << u;
+        else if (dg == d) sur |= 1u << u;
       }
     }
-    const uint32_t s2 = warp_append(&ctl->sv_count, kind == 2);
-    if (kind == 2) p.sv[s2] = c;
-    hist_add(sh, static_cast<uint32_t>(c >> 48) & 255u, kind == 2);
-  }
-  __syncthreads();
-  flush_hist(sh, ctl->gsel.hist[1]);
-  if (last_block(&ctl->gsel.ticket[1])) {
-    if (threadIdx.x < 32 && !done0) select_digit<8>(&ctl->gsel, 1, 64, !p.kth_only);
-  }
-}
-
-__global__ void __launch_bounds__(kThreads) gpass_kernel(GSelParams p, int pass) {
-  Ctl* ctl = p.ctl;
-  if (__ldcg(&ctl->mode) != kModeSelect) return;
-  if (__ldcg(&ctl->gsel.done) != 0) return;
-  __shared__ uint32_t sh[256];
-  for (int i = threadIdx.x; i < 256; i += kThreads) sh[i] = 0;
-  __syncthreads();
-  const uint32_t cnt = __ldcg(&ctl->sv_count);
-  const uint64_t prefix = __ldcg(&ctl->gsel.prefix);
-  const uint64_t mask = ~uint64_t(0) << (64 - 8 * pass);
-  const uint64_t want = prefix & mask;
-  const int sh_d = 56 - 8 * pass;
-  const uint32_t lane = lane_id();
-  const int64_t warps_total = int64_t(gridDim.x) * (kThreads / 32);
-  const int64_t gw = int64_t(blockIdx.x) * (kThreads / 32) + (threadIdx.x >> 5);
-  for (int64_t base = gw * 32; base < cnt; base += warps_total * 32) {
-    const int64_t i = base + lane;
-    uint64_t c = 0;
-    bool act = false;
-    if (i < cnt) {
-      c = p.sv[i];
-      act = (c & mask) == want;
+    if (!p.kth_only) {
+      uint32_t ws = block_append<kThreads>(&ctl->w_count, __popc(win));
+#pragma unroll
+      for (int u = 0; u < IPT; ++u) {
+        if (win & (1u << u)) {
+          if (ws < p.k) p.w[ws] = c[u];
+          else atomicOr(&ctl->error, kErrOverflowW);
+          ++ws;
+        }
+      }
     }
-    hist_add(sh, static_cast<uint32_t>(c >> sh_d) & 255u, act);
+    uint32_t ss = block_append<kThreads>(&ctl->stage_count[s + 1], __popc(sur));
+#pragma unroll
+    for (int u = 0; u < IPT; ++u) {
+      if (sur & (1u << u)) {
+        dst[ss++] = c[u];
+        if (nsh >= 0) rh.add(sh, static_cast<uint32_t>(c[u] >> nsh) & 255u);
+      }
+    }
   }
+  if (last || done) return;  // no further digit to select (uniform)
+  rh.flush(sh);
   __syncthreads();
-  flush_hist(sh, ctl->gsel.hist[pass]);
-  if (last_block(&ctl->gsel.ticket[pass])) {
-    if (threadIdx.x < 32) select_digit<8>(&ctl->gsel, pass, 64, !p.kth_only);
-  }
-}
-
-__global__ void __launch_bounds__(kThreads) gemit_kernel(GSelParams p) {
-  Ctl* ctl = p.ctl;
-  if (__ldcg(&ctl->mode) != kModeSelect) return;
-  const uint32_t level = __ldcg(&ctl->gsel.level);
-  const bool done = __ldcg(&ctl->gsel.done) != 0;
-  if (level <= 1 && done) return;  // the partition already wrote every winner
-  const uint64_t T = __ldcg(&ctl->gsel.prefix);
-  const uint32_t cnt = __ldcg(&ctl->sv_count);
-  const uint32_t lane = lane_id();
-  const int64_t warps_total = int64_t(gridDim.x) * (kThreads / 32);
-  const int64_t gw = int64_t(blockIdx.x) * (kThreads / 32) + (threadIdx.x >> 5);
-  for (int64_t base = gw * 32; base < cnt; base += warps_total * 32) {
-    const int64_t i = base + lane;
-    uint64_t c = 0;
-    bool win = false;
-    if (i < cnt) {
-      c = p.sv[i];
-      win = c >= T;
-    }
-    const uint32_t slot = warp_append(&ctl->w_count, win);
-    if (win) {
-      if (slot < p.k) p.w[slot] = c;
-      else atomicOr(&ctl->error, kErrOverflowW);
-    }
+  flush_hist(sh, ctl->gsel.hist[level + 1]);
+  if (last_block(&ctl->gsel.ticket[level + 1])) {
+    if (threadIdx.x < 32) select_digit<8>(&ctl->gsel, level + 1, 64, !p.kth_only);
   }
 }
 
@@ -370,9 +405,12 @@ struct TieParams {
   const uint32_t* dkeys;
   const uint16_t* dsegs;
   uint32_t* tcnt;
-  uint32_t* bsum1;
-  uint32_t* bsum2;
+  uint32_t* bsum1;   // block sums of the lower bounds, scanned in place
+  uint32_t* bsum2;   // block sums after exact counts, scanned in place
   int64_t nblk;
+  uint32_t* q1;      // subranges needing an exact tie count
+  uint32_t* q2;      // subranges emitting ties
+  uint32_t* q2pre;   // their tie prefixes
   const uint64_t* g;
   uint64_t* w;
   Ctl* ctl;
@@ -435,7 +473,10 @@ __global__ void __launch_bounds__(kThreads) tie_lb_kernel(TieParams p) {
   }
   uint32_t tot;
   block_excl_scan(sum, &tot);
-  if (threadIdx.x == 0) p.bsum1[blockIdx.x] = tot;
+  if (threadIdx.x == 0) {
+    p.bsum1[blockIdx.x] = tot;
+    p.bsum2[blockIdx.x] = tot;
+  }
 }
 
 // Exclusive scan of nblk block sums in place, one block of 1024 threads.
@@ -465,9 +506,9 @@ __global__ void __launch_bounds__(1024) scan_blocks_kernel(uint32_t* a, int64_t 
 
 // Per-thread exclusive prefixes of the 8 tie counts it owns, offset by the
 // block's scanned sum: pre[e] = number of ties (as counted) before subrange e.
-__device__ __forceinline__ uint32_t tie_prefixes(const TieParams& p, const uint32_t* bscan,
-                                                 uint32_t (&t)[kTieSubPerThread],
-                                                 uint32_t (&pre)[kTieSubPerThread]) {
+__device__ __forceinline__ void tie_prefixes(const TieParams& p, const uint32_t* bscan,
+                                             uint32_t (&t)[kTieSubPerThread],
+                                             uint32_t (&pre)[kTieSubPerThread]) {
   const int64_t i0 = int64_t(blockIdx.x) * kTieSubPerBlock + threadIdx.x * kTieSubPerThread;
   uint32_t sum = 0;
 #pragma unroll
@@ -477,94 +518,105 @@ __device__ __forceinline__ uint32_t tie_prefixes(const TieParams& p, const uint3
     pre[e] = sum;
     sum += t[e] & kCountMask;
   }
-  uint32_t total;
-  const uint32_t off = block_excl_scan(sum, &total) + bscan[blockIdx.x];
+  const uint32_t off = block_excl_scan(sum, nullptr) + bscan[blockIdx.x];
 #pragma unroll
   for (int e = 0; e < kTieSubPerThread; ++e) pre[e] += off;
-  return total;
 }
 
+// Queue the subranges whose tie count is only a lower bound and whose
+// prefix is still below `need`: only they can hold a needed tie we cannot
+// place yet.
+__global__ void __launch_bounds__(kThreads) tie_enqueue_kernel(TieParams p) {
+  Ctl* ctl = p.ctl;
+  if (__ldcg(&ctl->mode) != kModeTies) return;
+  const uint32_t need = __ldcg(&ctl->need);
+  uint32_t t[kTieSubPerThread], pre[kTieSubPerThread];
+  tie_prefixes(p, p.bsum1, t, pre);
+  const int64_t i0 = int64_t(blockIdx.x) * kTieSubPerBlock + threadIdx.x * kTieSubPerThread;
+  uint32_t c = 0;
+#pragma unroll
+  for (int e = 0; e < kTieSubPerThread; ++e) c += ((t[e] & kInexact) && pre[e] < need);
+  uint32_t slot = block_append<kThreads>(&ctl->tieq1_count, c);
+#pragma unroll
+  for (int e = 0; e < kTieSubPerThread; ++e)
+    if ((t[e] & kInexact) && pre[e] < need) p.q1[slot++] = static_cast<uint32_t>(i0 + e);
+}
+
+// Exact tie counts of the queued subranges, one warp per subrange over the
+// whole grid; the block sums used for the second scan are corrected in place.
 template <int DT>
-__global__ void __launch_bounds__(kThreads) tie_exact_kernel(TieParams p) {
+__global__ void __launch_bounds__(kThreads) tie_count_kernel(TieParams p) {
   Ctl* ctl = p.ctl;
   if (__ldcg(&ctl->mode) != kModeTies) return;
   const uint32_t tau = __ldcg(&ctl->tau);
-  const uint32_t need = __ldcg(&ctl->need);
-  __shared__ uint32_t q_sub[kTieSubPerBlock];
-  __shared__ uint32_t q_n;
-  __shared__ uint32_t delta;
-  if (threadIdx.x == 0) {
-    q_n = 0;
-    delta = 0;
-  }
-  __syncthreads();
-  uint32_t t[kTieSubPerThread], pre[kTieSubPerThread];
-  const uint32_t old_total = tie_prefixes(p, p.bsum1, t, pre);
-#pragma unroll
-  for (int e = 0; e < kTieSubPerThread; ++e) {
-    if ((t[e] & kInexact) && pre[e] < need) {
-      const uint32_t s = atomicAdd(&q_n, 1u);
-      q_sub[s] = static_cast<uint32_t>(threadIdx.x * kTieSubPerThread + e);
-    }
-  }
-  __syncthreads();
-  const uint32_t nq = q_n;
+  const int64_t nq = __ldcg(&ctl->tieq1_count);
   const uint32_t lane = lane_id();
-  const int warp = threadIdx.x >> 5;
-  for (uint32_t q = warp; q < nq; q += kThreads / 32) {
-    const int64_t i = int64_t(blockIdx.x) * kTieSubPerBlock + q_sub[q];
+  const int64_t warps = int64_t(gridDim.x) * (kThreads / 32);
+  uint32_t done = 0;
+  for (int64_t q = int64_t(blockIdx.x) * (kThreads / 32) + (threadIdx.x >> 5); q < nq;
+       q += warps) {
+    const int64_t i = p.q1[q];
     const int64_t lo = i << p.alpha;
     const int64_t len = sub_len(i, p.alpha, p.n);
     uint32_t c = 0;
-    for (int64_t off = lane; off < len; off += 32) c += (map_key<DT>(__ldg(p.keys + lo + off)) == tau);
+    for (int64_t off = lane; off < len; off += 32)
+      c += (map_key<DT>(__ldg(p.keys + lo + off)) == tau);
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
     if (lane == 0) {
       const uint32_t old = p.tcnt[i] & kCountMask;
       p.tcnt[i] = c | kScanned;
-      atomicAdd(&delta, c - old);
-      atomicAdd(&ctl->tie_scanned, 1u);
+      atomicAdd(&p.bsum2[i / kTieSubPerBlock], c - old);
+      ++done;
     }
   }
-  __syncthreads();
-  if (threadIdx.x == 0) p.bsum2[blockIdx.x] = old_total + delta;
+  if (done) atomicAdd(&ctl->tie_scanned, done);
 }
 
+// Queue the subranges that hold needed ties (exact prefix below `need`) and
+// copy G, which is part of the answer, in front of the ties in W.
+__global__ void __launch_bounds__(kThreads) tie_emit_enqueue_kernel(TieParams p) {
+  Ctl* ctl = p.ctl;
+  if (__ldcg(&ctl->mode) != kModeTies) return;
+  const uint32_t need = __ldcg(&ctl->need);
+  const uint32_t g = __ldcg(&ctl->g_count);  // < k in this mode
+  for (int64_t j = int64_t(blockIdx.x) * kThreads + threadIdx.x; j < g;
+       j += int64_t(gridDim.x) * kThreads)
+    p.w[j] = p.g[j];
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&ctl->w_count, g);
+  uint32_t t[kTieSubPerThread], pre[kTieSubPerThread];
+  tie_prefixes(p, p.bsum2, t, pre);
+  const int64_t i0 = int64_t(blockIdx.x) * kTieSubPerBlock + threadIdx.x * kTieSubPerThread;
+  uint32_t c = 0;
+#pragma unroll
+  for (int e = 0; e < kTieSubPerThread; ++e) c += ((t[e] & kCountMask) > 0 && pre[e] < need);
+  uint32_t slot = block_append<kThreads>(&ctl->tieq2_count, c);
+#pragma unroll
+  for (int e = 0; e < kTieSubPerThread; ++e) {
+    if ((t[e] & kCountMask) > 0 && pre[e] < need) {
+      p.q2[slot] = static_cast<uint32_t>(i0 + e);
+      p.q2pre[slot] = pre[e];
+      ++slot;
+    }
+  }
+}
+
+// Emit the ties of the queued subranges in index order, one warp each.
 template <int DT, int B>
 __global__ void __launch_bounds__(kThreads) tie_emit_kernel(TieParams p) {
   Ctl* ctl = p.ctl;
   if (__ldcg(&ctl->mode) != kModeTies) return;
   const uint32_t tau = __ldcg(&ctl->tau);
   const uint32_t need = __ldcg(&ctl->need);
-  const uint32_t g = __ldcg(&ctl->g_count);  // < k in this mode
-  // G is part of the answer: copy it in front of the ties
-  for (int64_t j = int64_t(blockIdx.x) * kThreads + threadIdx.x; j < g;
-       j += int64_t(gridDim.x) * kThreads)
-    p.w[j] = p.g[j];
-  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&ctl->w_count, g);
-
-  __shared__ uint32_t q_sub[kTieSubPerBlock];
-  __shared__ uint32_t q_pre[kTieSubPerBlock];
-  __shared__ uint32_t q_n;
-  if (threadIdx.x == 0) q_n = 0;
-  __syncthreads();
-  uint32_t t[kTieSubPerThread], pre[kTieSubPerThread];
-  tie_prefixes(p, p.bsum2, t, pre);
-#pragma unroll
-  for (int e = 0; e < kTieSubPerThread; ++e) {
-    if ((t[e] & kCountMask) > 0 && pre[e] < need) {
-      const uint32_t s = atomicAdd(&q_n, 1u);
-      q_sub[s] = static_cast<uint32_t>(threadIdx.x * kTieSubPerThread + e);
-      q_pre[s] = pre[e];
-    }
-  }
-  __syncthreads();
-  const uint32_t nq = q_n;
+  const uint32_t g = __ldcg(&ctl->g_count);
+  const int64_t nq = __ldcg(&ctl->tieq2_count);
   const uint32_t lane = lane_id();
-  const int warp = threadIdx.x >> 5;
-  for (uint32_t q = warp; q < nq; q += kThreads / 32) {
-    const int64_t i = int64_t(blockIdx.x) * kTieSubPerBlock + q_sub[q];
-    const uint32_t base = q_pre[q];
+  const int64_t warps = int64_t(gridDim.x) * (kThreads / 32);
+  uint32_t emitted_total = 0;
+  for (int64_t q = int64_t(blockIdx.x) * (kThreads / 32) + (threadIdx.x >> 5); q < nq;
+       q += warps) {
+    const int64_t i = p.q2[q];
+    const uint32_t base = p.q2pre[q];
     const uint32_t tt = p.tcnt[i];
     uint32_t emitted = 0;
     if (tt & kScanned) {
@@ -606,10 +658,11 @@ __global__ void __launch_bounds__(kThreads) tie_emit_kernel(TieParams p) {
         }
       }
     }
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) emitted += __shfl_xor_sync(0xFFFFFFFFu, emitted, o);
-    if (lane == 0 && emitted) atomicAdd(&ctl->w_count, emitted);
+    emitted_total += emitted;
   }
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) emitted_total += __shfl_xor_sync(0xFFFFFFFFu, emitted_total, o);
+  if (lane == 0 && emitted_total) atomicAdd(&ctl->w_count, emitted_total);
 }
 
 // ----------------------------------------------------------- k-th output ---
@@ -645,29 +698,25 @@ __global__ void resolve_kernel(const uint32_t* keys, int64_t n, int64_t S, int a
   }
 }
 
-int grid_for(int64_t work, int per_block, int sms, int per_sm) {
-  int64_t g = (work + per_block - 1) / per_block;
-  const int64_t cap = static_cast<int64_t>(sms) * per_sm;
-  if (g > cap) g = cap;
-  if (g < 1) g = 1;
-  return static_cast<int>(g);
-}
-
 }  // namespace
+
+int64_t tie_blocks(int64_t S) { return (S + kTieSubPerBlock - 1) / kTieSubPerBlock; }
 
 cudaError_t launch_threshold(const Work& w, int sms, cudaStream_t s) {
   const int64_t count = w.S * w.beta;
-  const int grid = grid_for(count, kThreads * 16, sms, 4);
-  for (int pass = 1; pass <= 3; ++pass) {
-    thr_pass_kernel<<<grid, kThreads, 0, s>>>(w.dkeys, count, w.ctl, pass);
-    note_launch();
-  }
+  const int g1 = grid_for(count, kThreads * 16, sms, 4);
+  thr_compact_kernel<<<g1, kThreads, 0, s>>>(w.dkeys, count, w.ds, w.ctl);
+  const int g2 = grid_for(count, kThreads * 8, sms, 4);
+  thr_pass_kernel<<<g2, kThreads, 0, s>>>(w.ds, w.ctl, 2);
+  thr_pass_kernel<<<g2, kThreads, 0, s>>>(w.ds, w.ctl, 3);
+  note_launch(3);
   return cudaGetLastError();
 }
 
 template <int DT, int B>
-static void filter_t(const FilterParams& p, int grid, cudaStream_t s) {
-  filter_kernel<DT, B><<<grid, kThreads, 0, s>>>(p);
+static void filter_t(const FilterParams& p, int g1, int g2, cudaStream_t s) {
+  filter_classify_kernel<DT, B><<<g1, kThreads, 0, s>>>(p);
+  filter_scan_kernel<DT><<<g2, kThreads, 0, s>>>(p);
 }
 
 cudaError_t launch_filter(const Work& w, const void* keys, bool kth_only, int sms,
@@ -681,16 +730,19 @@ cudaError_t launch_filter(const Work& w, const void* keys, bool kth_only, int sm
   p.alpha = w.alpha;
   p.dkeys = w.dkeys;
   p.dsegs = w.dsegs;
+  p.scanq = w.scanq;
   p.g = w.g;
   p.ctl = w.ctl;
   p.kth_only = kth_only ? 1 : 0;
-  const int grid = grid_for(w.S, kThreads * 4, sms, 8);
-#define DRTOPK_FILTER_CASE(DTV)                           \
-  switch (w.beta) {                                       \
-    case 1: filter_t<DTV, 1>(p, grid, s); break;          \
-    case 2: filter_t<DTV, 2>(p, grid, s); break;          \
-    case 3: filter_t<DTV, 3>(p, grid, s); break;          \
-    default: filter_t<DTV, 4>(p, grid, s); break;         \
+  const int g1 = grid_for(w.S, kThreads, sms, 8);
+  // scanned keys are bounded by the G capacity (or n when tau = 0)
+  const int g2 = grid_for(w.g_cap, kThreads * kScanKPT, sms, 8);
+#define DRTOPK_FILTER_CASE(DTV)                              \
+  switch (w.beta) {                                          \
+    case 1: filter_t<DTV, 1>(p, g1, g2, s); break;           \
+    case 2: filter_t<DTV, 2>(p, g1, g2, s); break;           \
+    case 3: filter_t<DTV, 3>(p, g1, g2, s); break;           \
+    default: filter_t<DTV, 4>(p, g1, g2, s); break;          \
   }
   switch (w.dtype) {
     case DRTOPK_U32: DRTOPK_FILTER_CASE(DRTOPK_U32); break;
@@ -698,12 +750,11 @@ cudaError_t launch_filter(const Work& w, const void* keys, bool kth_only, int sm
     default: DRTOPK_FILTER_CASE(DRTOPK_F32); break;
   }
 #undef DRTOPK_FILTER_CASE
-  note_launch();
+  note_launch(2);
   return cudaGetLastError();
 }
 
 cudaError_t launch_ties(const Work& w, const void* keys, int sms, cudaStream_t s) {
-  (void)sms;
   TieParams p;
   p.keys = static_cast<const uint32_t*>(keys);
   p.n = w.n;
@@ -713,13 +764,17 @@ cudaError_t launch_ties(const Work& w, const void* keys, int sms, cudaStream_t s
   p.dkeys = w.dkeys;
   p.dsegs = w.dsegs;
   p.tcnt = w.tcnt;
-  p.nblk = (w.S + kTieSubPerBlock - 1) / kTieSubPerBlock;
+  p.nblk = tie_blocks(w.S);
   p.bsum1 = w.bsum;
   p.bsum2 = w.bsum + p.nblk;
+  p.q1 = w.tieq;
+  p.q2 = w.tieq + w.S;
+  p.q2pre = w.scanq;  // the filter's queue is no longer needed
   p.g = w.g;
   p.w = w.w;
   p.ctl = w.ctl;
   const int grid = static_cast<int>(p.nblk);
+  const int gq = grid_for(w.S, kThreads / 32, sms, 8);
 #define DRTOPK_TIE_CASE(DTV)                                                        \
   switch (w.beta) {                                                                 \
     case 1: tie_lb_kernel<1><<<grid, kThreads, 0, s>>>(p); break;                   \
@@ -728,13 +783,15 @@ cudaError_t launch_ties(const Work& w, const void* keys, int sms, cudaStream_t s
     default: tie_lb_kernel<4><<<grid, kThreads, 0, s>>>(p); break;                  \
   }                                                                                 \
   scan_blocks_kernel<<<1, 1024, 0, s>>>(p.bsum1, p.nblk, p.ctl);                    \
-  tie_exact_kernel<DTV><<<grid, kThreads, 0, s>>>(p);                               \
+  tie_enqueue_kernel<<<grid, kThreads, 0, s>>>(p);                                  \
+  tie_count_kernel<DTV><<<gq, kThreads, 0, s>>>(p);                                 \
   scan_blocks_kernel<<<1, 1024, 0, s>>>(p.bsum2, p.nblk, p.ctl);                    \
+  tie_emit_enqueue_kernel<<<grid, kThreads, 0, s>>>(p);                             \
   switch (w.beta) {                                                                 \
-    case 1: tie_emit_kernel<DTV, 1><<<grid, kThreads, 0, s>>>(p); break;            \
-    case 2: tie_emit_kernel<DTV, 2><<<grid, kThreads, 0, s>>>(p); break;            \
-    case 3: tie_emit_kernel<DTV, 3><<<grid, kThreads, 0, s>>>(p); break;            \
-    default: tie_emit_kernel<DTV, 4><<<grid, kThreads, 0, s>>>(p); break;           \
+    case 1: tie_emit_kernel<DTV, 1><<<gq, kThreads, 0, s>>>(p); break;              \
+    case 2: tie_emit_kernel<DTV, 2><<<gq, kThreads, 0, s>>>(p); break;              \
+    case 3: tie_emit_kernel<DTV, 3><<<gq, kThreads, 0, s>>>(p); break;              \
+    default: tie_emit_kernel<DTV, 4><<<gq, kThreads, 0, s>>>(p); break;             \
   }
   switch (w.dtype) {
     case DRTOPK_U32: DRTOPK_TIE_CASE(DRTOPK_U32); break;
@@ -742,7 +799,7 @@ cudaError_t launch_ties(const Work& w, const void* keys, int sms, cudaStream_t s
     default: DRTOPK_TIE_CASE(DRTOPK_F32); break;
   }
 #undef DRTOPK_TIE_CASE
-  note_launch(5);
+  note_launch(7);
   return cudaGetLastError();
 }
 
@@ -756,15 +813,11 @@ cudaError_t launch_gselect(const Work& w, bool kth_only, int sms, cudaStream_t s
   p.ctl = w.ctl;
   p.kth_only = kth_only ? 1 : 0;
   const int grid = grid_for(w.g_cap, kThreads * 8, sms, 8);
-  gpart_kernel<<<grid, kThreads, 0, s>>>(p);
-  const int last = kth_only ? 3 : 7;
-  for (int pass = 2; pass <= last; ++pass) gpass_kernel<<<grid, kThreads, 0, s>>>(p, pass);
-  int launched = 1 + (last - 1);
-  if (!kth_only) {
-    gemit_kernel<<<grid, kThreads, 0, s>>>(p);
-    ++launched;
-  }
-  note_launch(launched);
+  // k-selection needs the 4 key digits (stages 1-3 decide digits 0-2 and
+  // select digit 3); top-k resolves all 8 digits of the composite.
+  const int last = kth_only ? 3 : 8;
+  for (int st = 1; st <= last; ++st) gstage_kernel<<<grid, kThreads, 0, s>>>(p, st);
+  note_launch(last);
   return cudaGetLastError();
 }
 

@@ -3,9 +3,13 @@
 // output order of top-k; the paper leaves it unstated), and written as the
 // input dtype's key bits plus int32 indices.
 //   * k <= 4096: one CTA bitonic-sorts W in shared memory;
-//   * larger k: a stable LSD radix sort with 8-bit digits over the
-//     complemented composites (ascending), 3 kernels per digit; a digit that
-//     is the same for all k entries is skipped on the device.
+//   * larger k: a stable LSD radix sort of the complemented composites
+//     (ascending) with 8-bit digits. One kernel histograms all 8 digits at
+//     once; each digit pass is then a single kernel: tiles of 4096 are taken
+//     in order from an atomic counter, ranked stably in shared memory, and
+//     their global offsets come from a decoupled look-back over the earlier
+//     tiles' per-digit counts (bounded waits). A digit equal for all k
+//     entries is skipped.
 #include "common.cuh"
 #include "launch.h"
 
@@ -16,11 +20,23 @@ constexpr int kSmallSort = 4096;
 constexpr int kSortThreads = 256;
 constexpr int kItems = 16;
 constexpr int kTile = kSortThreads * kItems;  // 4096
+constexpr uint64_t kFlagAgg = uint64_t(1) << 32;
+constexpr uint64_t kFlagIncl = uint64_t(2) << 32;
+constexpr uint32_t kLookbackSpin = 1u << 22;
 
 __device__ __forceinline__ uint32_t lanemask_lt_s() {
   uint32_t m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
   return m;
+}
+
+__device__ __forceinline__ void st_relaxed(uint64_t* p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t ld_relaxed(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
 }
 
 __device__ __forceinline__ void write_out(uint64_t c, int64_t j, int64_t k, int dtype,
@@ -66,9 +82,9 @@ __global__ void __launch_bounds__(1024) small_sort_kernel(const uint64_t* w, int
 
 struct SortParams {
   uint64_t* buf[2];
-  uint32_t* hist;  // [256][nblk] digit-major counts, then [2] flags per pass
+  uint64_t* status;  // [8][ntiles][256] look-back words (flag << 32 | count)
   int64_t k;
-  int64_t nblk;
+  int64_t ntiles;
   Ctl* ctl;
 };
 
@@ -77,91 +93,78 @@ __device__ __forceinline__ uint32_t sdigit(uint64_t c, int pass) {
   return static_cast<uint32_t>((~c) >> (8 * pass)) & 255u;
 }
 
-__global__ void __launch_bounds__(kSortThreads) sort_hist_kernel(SortParams p, int pass) {
-  __shared__ uint32_t sh[256];
-  for (int i = threadIdx.x; i < 256; i += kSortThreads) sh[i] = 0;
+__global__ void __launch_bounds__(kSortThreads) sort_hist_all_kernel(SortParams p) {
+  __shared__ uint32_t sh[8][256];
+  for (int i = threadIdx.x; i < 8 * 256; i += kSortThreads) (&sh[0][0])[i] = 0;
   __syncthreads();
-  const uint64_t* src = p.buf[__ldcg(&p.ctl->sort_cur) & 1];
-  const int64_t t0 = int64_t(blockIdx.x) * kTile;
-  for (int r = 0; r < kItems; ++r) {
-    const int64_t i = t0 + r * kSortThreads + threadIdx.x;
-    if (i < p.k) atomicAdd(&sh[sdigit(src[i], pass)], 1u);
+  const uint64_t* src = p.buf[0];
+  for (int64_t i = int64_t(blockIdx.x) * kSortThreads + threadIdx.x; i < p.k;
+       i += int64_t(gridDim.x) * kSortThreads) {
+    const uint64_t c = src[i];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) atomicAdd(&sh[q][sdigit(c, q)], 1u);
   }
   __syncthreads();
-  for (int d = threadIdx.x; d < 256; d += kSortThreads) p.hist[int64_t(d) * p.nblk + blockIdx.x] = sh[d];
-}
-
-// Exclusive scan over the digit-major counts; flags[pass] = 1 when one digit
-// holds every entry (the pass is skipped).
-__global__ void __launch_bounds__(1024) sort_scan_kernel(SortParams p, int pass) {
-  __shared__ uint32_t part[1024];
-  __shared__ uint32_t s_skip;
-  const int64_t total = 256 * p.nblk;
-  const int64_t per = (total + 1023) / 1024;
-  const int64_t lo = threadIdx.x * per;
-  const int64_t hi = imin64(total, lo + per);
-  uint32_t s = 0;
-  for (int64_t i = lo; i < hi; ++i) s += p.hist[i];
-  part[threadIdx.x] = s;
-  if (threadIdx.x == 0) s_skip = 0;
-  __syncthreads();
-  // a digit holds everything iff its nblk counts sum to k
-  if (threadIdx.x < 256) {
-    uint64_t ds = 0;
-    for (int64_t b = 0; b < p.nblk; ++b) ds += p.hist[int64_t(threadIdx.x) * p.nblk + b];
-    if (ds == static_cast<uint64_t>(p.k)) s_skip = 1;
+  for (int i = threadIdx.x; i < 8 * 256; i += kSortThreads) {
+    const uint32_t v = (&sh[0][0])[i];
+    if (v) atomicAdd(&(&p.ctl->sort_hist[0][0])[i], v);
   }
-  for (int o = 1; o < 1024; o <<= 1) {
-    const uint32_t v = threadIdx.x >= static_cast<unsigned>(o) ? part[threadIdx.x - o] : 0u;
-    __syncthreads();
-    part[threadIdx.x] += v;
-    __syncthreads();
-  }
-  uint32_t run = part[threadIdx.x] - s;
-  for (int64_t i = lo; i < hi; ++i) {
-    const uint32_t v = p.hist[i];
-    p.hist[i] = run;
-    run += v;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const uint32_t cur = p.ctl->sort_cur & 1;
-    p.hist[total + 2 * pass] = s_skip;
-    p.hist[total + 2 * pass + 1] = cur;  // source buffer of this pass
-    if (!s_skip) p.ctl->sort_cur = cur ^ 1u;
+  if (last_block(&p.ctl->sort_ticket)) {
+    if (threadIdx.x < 8) {
+      // exclusive offsets per digit; a digit that holds all k entries is skipped
+      uint32_t* h = p.ctl->sort_hist[threadIdx.x];
+      uint32_t run = 0, skip = 0;
+      for (int d = 0; d < 256; ++d) {
+        const uint32_t v = __ldcg(&h[d]);
+        if (v == static_cast<uint32_t>(p.k)) skip = 1;
+        h[d] = run;
+        run += v;
+      }
+      p.ctl->sort_skip[threadIdx.x] = skip;
+    }
   }
 }
 
-__global__ void __launch_bounds__(kSortThreads) sort_scatter_kernel(SortParams p, int pass) {
-  const int64_t total = 256 * p.nblk;
-  if (__ldcg(&p.hist[total + 2 * pass]) != 0) return;
-  const uint32_t cur = __ldcg(&p.hist[total + 2 * pass + 1]);
-  const uint64_t* src = p.buf[cur];
-  uint64_t* dst = p.buf[cur ^ 1u];
+__global__ void __launch_bounds__(kSortThreads) sort_pass_kernel(SortParams p, int pass) {
+  Ctl* ctl = p.ctl;
+  if (__ldcg(&ctl->sort_skip[pass])) return;
+  uint32_t par = 0;
+  for (int q = 0; q < pass; ++q) par ^= (__ldcg(&ctl->sort_skip[q]) == 0);
+  const uint64_t* src = p.buf[par];
+  uint64_t* dst = p.buf[par ^ 1u];
+
+  __shared__ uint32_t s_tile;
   __shared__ uint32_t base[256];
   __shared__ uint32_t wcnt[kSortThreads / 32][256];
+  __shared__ uint32_t s_off[256];
+  if (threadIdx.x == 0) s_tile = atomicAdd(&ctl->sort_tiles[pass], 1u);
+  for (int d = threadIdx.x; d < 256; d += kSortThreads) base[d] = 0;
+  __syncthreads();
+  const int64_t tile = s_tile;
   const int warp = threadIdx.x >> 5;
-  const uint32_t lane = threadIdx.x & 31u;
-  for (int d = threadIdx.x; d < 256; d += kSortThreads) base[d] = p.hist[int64_t(d) * p.nblk + blockIdx.x];
-  const int64_t t0 = int64_t(blockIdx.x) * kTile;
+  const int64_t t0 = tile * kTile;
+
+  uint64_t c[kItems];
+  uint32_t rank[kItems];
+  // stable ranking inside the tile: element order = (round, warp, lane)
+#pragma unroll
   for (int r = 0; r < kItems; ++r) {
     for (int q = threadIdx.x; q < (kSortThreads / 32) * 256; q += kSortThreads)
       (&wcnt[0][0])[q] = 0;
     __syncthreads();
     const int64_t i = t0 + r * kSortThreads + threadIdx.x;
     const bool act = i < p.k;
-    uint64_t c = 0;
-    uint32_t d = 0, rank = 0;
+    uint32_t d = 0, rk = 0;
     const uint32_t am = __ballot_sync(0xFFFFFFFFu, act);
+    c[r] = 0;
     if (act) {
-      c = src[i];
-      d = sdigit(c, pass);
+      c[r] = src[i];
+      d = sdigit(c[r], pass);
       const uint32_t peers = __match_any_sync(am, d);
-      rank = __popc(peers & lanemask_lt_s());
-      if (rank == 0) wcnt[warp][d] = __popc(peers);
+      rk = __popc(peers & lanemask_lt_s());
+      if (rk == 0) wcnt[warp][d] = __popc(peers);
     }
     __syncthreads();
-    // per digit: offsets of the warps in order, then advance the base
     for (int dd = threadIdx.x; dd < 256; dd += kSortThreads) {
       uint32_t run = base[dd];
       for (int q = 0; q < kSortThreads / 32; ++q) {
@@ -172,14 +175,54 @@ __global__ void __launch_bounds__(kSortThreads) sort_scatter_kernel(SortParams p
       base[dd] = run;
     }
     __syncthreads();
-    if (act) dst[wcnt[warp][d] + rank] = c;
-    __syncthreads();
+    rank[r] = act ? wcnt[warp][d] + rk : 0u;
+    __syncthreads();  // wcnt is cleared again by the next round
+  }
+
+  // decoupled look-back: thread d publishes this tile's count of digit d and
+  // adds the earlier tiles' counts
+  {
+    const int d = threadIdx.x;  // 256 threads = 256 digits
+    uint64_t* st = p.status + (int64_t(pass) * p.ntiles) * 256;
+    const uint32_t cnt = base[d];
+    uint32_t excl = 0;
+    if (tile == 0) {
+      st_relaxed(&st[d], kFlagIncl | cnt);
+    } else {
+      st_relaxed(&st[tile * 256 + d], kFlagAgg | cnt);
+      int64_t t = tile - 1;
+      uint32_t spins = 0;
+      while (t >= 0) {
+        const uint64_t v = ld_relaxed(&st[t * 256 + d]);
+        const uint64_t f = v & ~uint64_t(0xFFFFFFFFu);
+        if (f == 0) {
+          if (++spins > kLookbackSpin) {
+            atomicOr(&ctl->error, kErrTimeout);
+            break;
+          }
+          continue;
+        }
+        excl += static_cast<uint32_t>(v);
+        if (f == kFlagIncl) break;
+        --t;
+      }
+      st_relaxed(&st[tile * 256 + d], kFlagIncl | (excl + cnt));
+    }
+    s_off[d] = __ldcg(&ctl->sort_hist[pass][d]) + excl;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kItems; ++r) {
+    const int64_t i = t0 + r * kSortThreads + threadIdx.x;
+    if (i < p.k) dst[s_off[sdigit(c[r], pass)] + rank[r]] = c[r];
   }
 }
 
 __global__ void finalize_kernel(SortParams p, int dtype, uint32_t* out_keys, int32_t* out_idx,
                                 uint32_t* out_kth) {
-  const uint64_t* src = p.buf[__ldcg(&p.ctl->sort_cur) & 1];
+  uint32_t par = 0;
+  for (int q = 0; q < 8; ++q) par ^= (__ldcg(&p.ctl->sort_skip[q]) == 0);
+  const uint64_t* src = p.buf[par];
   for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < p.k;
        j += int64_t(gridDim.x) * blockDim.x)
     write_out(src[j], j, p.k, dtype, out_keys, out_idx, out_kth, p.ctl);
@@ -187,10 +230,10 @@ __global__ void finalize_kernel(SortParams p, int dtype, uint32_t* out_keys, int
 
 }  // namespace
 
-size_t sort_hist_words(int64_t k) {
+size_t sort_status_words(int64_t k) {
   if (k <= kSmallSort) return 0;
-  const int64_t nblk = (k + kTile - 1) / kTile;
-  return static_cast<size_t>(256 * nblk + 16);
+  const int64_t nt = (k + kTile - 1) / kTile;
+  return static_cast<size_t>(8 * nt * 256);
 }
 
 cudaError_t launch_sort_output(const Work& w, void* out_keys, int32_t* out_idx, void* out_kth,
@@ -205,20 +248,20 @@ cudaError_t launch_sort_output(const Work& w, void* out_keys, int32_t* out_idx, 
   SortParams p;
   p.buf[0] = w.w;
   p.buf[1] = w.w2;
-  p.hist = w.sort_hist;
+  p.status = w.sort_status;
   p.k = w.k;
-  p.nblk = (w.k + kTile - 1) / kTile;
+  p.ntiles = (w.k + kTile - 1) / kTile;
   p.ctl = w.ctl;
-  const int nb = static_cast<int>(p.nblk);
-  for (int pass = 0; pass < 8; ++pass) {
-    sort_hist_kernel<<<nb, kSortThreads, 0, s>>>(p, pass);
-    sort_scan_kernel<<<1, 1024, 0, s>>>(p, pass);
-    sort_scatter_kernel<<<nb, kSortThreads, 0, s>>>(p, pass);
-  }
-  int g = static_cast<int>(std::min<int64_t>((w.k + 255) / 256, int64_t(sms) * 8));
+  cudaError_t e = cudaMemsetAsync(p.status, 0, sort_status_words(w.k) * 8, s);
+  if (e != cudaSuccess) return e;
+  const int gh = static_cast<int>(std::min<int64_t>(p.ntiles, int64_t(sms) * 4));
+  sort_hist_all_kernel<<<gh, kSortThreads, 0, s>>>(p);
+  for (int pass = 0; pass < 8; ++pass)
+    sort_pass_kernel<<<static_cast<unsigned>(p.ntiles), kSortThreads, 0, s>>>(p, pass);
+  const int g = static_cast<int>(std::min<int64_t>((w.k + 255) / 256, int64_t(sms) * 8));
   finalize_kernel<<<g, 256, 0, s>>>(p, w.dtype, static_cast<uint32_t*>(out_keys), out_idx,
                                     static_cast<uint32_t*>(out_kth));
-  note_launch(25);
+  note_launch(10);
   return cudaGetLastError();
 }
 
