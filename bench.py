@@ -39,6 +39,10 @@ DISTS = ["ascending", "descending", "all_equal", "distinct16", "zipf"]
 KS = [1024, 1 << 20]
 SEED = 3
 PAPER_UD_MS = 6.4  # Dr. Top-k radix, |V| = 2^30 UD, k = 1024, V100S (Sec. 5.1)
+# DRAM bytes (read + write) per key of one delegate-pass launch, from the ncu
+# capture in profiles/delegate_kernel_zipf_u32_2p27_k1024.md (scaled by keys).
+# Must be re-measured (or set to None) whenever the delegate kernel changes.
+DELEG_DRAM_BYTES_PER_KEY = (536.93e6 + 4.21e6) / (1 << 27)
 
 
 def parse():
@@ -291,8 +295,11 @@ def main():
         peak = 6800.0
     dms, dl = prof["delegate"]
     achieved = (4.0 * n) / ((dms / max(dl, 1)) * 1e-3) / 1e9 if dl else None
+    traffic = DELEG_DRAM_BYTES_PER_KEY * n if DELEG_DRAM_BYTES_PER_KEY else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum at n=2^27, "
+                                  "scaled by keys to one launch",
                 "kernel": "delegate_kernel (TMA-streamed delegate pass)",
                 "algorithmic_bytes_per_launch": 4 * n, "launches": dl,
                 "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs, copy burst)" % peak_src,

@@ -101,11 +101,12 @@ struct Ctl {
   uint32_t tieq1_count;    // subranges queued for exact tie counts
   uint32_t tieq2_count;    // subranges queued for tie emission
   uint32_t stage_count[10];  // survivors entering each second-select stage
+  uint32_t ds_inplace;       // threshold passes 2-3 read the delegate keys in place
   uint32_t sort_ticket;
   uint32_t sort_tiles[8];    // dynamic tile ids of the output radix sort
   uint32_t sort_hist[8][256];  // digit counts of the output composites
   uint32_t sort_skip[8];
-  uint32_t pad_[3];
+  uint32_t pad_[2];
 };
 
 // Device views of the workspace of one query.
@@ -238,6 +239,120 @@ __device__ __forceinline__ uint32_t block_append(uint32_t* counter, uint32_t cnt
   return r;
 }
 
+// Warp-contiguous reservation for one or two output arrays. Each warp
+// passes its totals (same value in every lane); one atomic per counter per
+// block reserves the block's range; every warp gets a contiguous sub-range
+// so that its lanes can write coalesced rounds (ballot + popc ranks).
+template <int NT>
+__device__ __forceinline__ void block_reserve2(uint32_t* ctr0, uint32_t t0, uint32_t* ctr1,
+                                               uint32_t t1, uint32_t& b0, uint32_t& b1) {
+  __shared__ uint32_t s[2][NT / 32];
+  __shared__ uint32_t s_base[2];
+  const uint32_t lane = lane_id();
+  const int warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    s[0][warp] = t0;
+    s[1][warp] = t1;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    const int c = threadIdx.x;
+    uint32_t run = 0;
+    for (int w = 0; w < NT / 32; ++w) {
+      const uint32_t t = s[c][w];
+      s[c][w] = run;
+      run += t;
+    }
+    uint32_t* ctr = c ? ctr1 : ctr0;
+    s_base[c] = (run && ctr) ? atomicAdd(ctr, run) : 0u;
+  }
+  __syncthreads();
+  b0 = s_base[0] + s[0][warp];
+  b1 = s_base[1] + s[1][warp];
+  __syncthreads();
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt32() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Block-wide exclusive scan of one value per thread (NT threads); *total
+// (optional) receives the block sum.
+template <int NT>
+__device__ __forceinline__ uint32_t block_scan_excl(uint32_t v, uint32_t* total) {
+  __shared__ uint32_t wsum[NT / 32];
+  const uint32_t lane = lane_id();
+  const int warp = threadIdx.x >> 5;
+  uint32_t incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= static_cast<uint32_t>(o)) incl += t;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  uint32_t wpre = 0, tot = 0;
+#pragma unroll
+  for (int q = 0; q < NT / 32; ++q) {
+    if (q < warp) wpre += wsum[q];
+    tot += wsum[q];
+  }
+  __syncthreads();
+  if (total) *total = tot;
+  return wpre + incl - v;
+}
+
+// Shared-memory staging of a variable-size output: items are gathered in a
+// block buffer of CAP entries and copied to the global array with one
+// atomicAdd per flush (coalesced). All threads of the block call these.
+template <typename T, int NT>
+__device__ __forceinline__ void stage_flush(T* buf, uint32_t* s_fill, uint32_t* gctr, T* gdst,
+                                            uint64_t gcap, uint32_t* err, uint32_t ebit) {
+  __shared__ uint32_t s_base;
+  __syncthreads();
+  const uint32_t f = *s_fill;
+  if (threadIdx.x == 0) s_base = f ? atomicAdd(gctr, f) : 0u;
+  __syncthreads();
+  const uint64_t b = s_base;
+  for (uint32_t j = threadIdx.x; j < f; j += NT) {
+    if (b + j < gcap) gdst[b + j] = buf[j];
+    else atomicOr(err, ebit);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *s_fill = 0;
+  __syncthreads();
+}
+
+// Reserves cnt staged slots for the calling thread (flushing first when the
+// buffer cannot take this round); returns the first slot in buf. The caller
+// writes buf[slot .. slot + cnt) before the next stage call.
+template <typename T, int NT, int CAP>
+__device__ __forceinline__ uint32_t stage_reserve(T* buf, uint32_t* s_fill, uint32_t cnt,
+                                                  uint32_t* gctr, T* gdst, uint64_t gcap,
+                                                  uint32_t* err, uint32_t ebit) {
+  uint32_t total;
+  const uint32_t excl = block_scan_excl<NT>(cnt, &total);
+  if (*s_fill + total > CAP) stage_flush<T, NT>(buf, s_fill, gctr, gdst, gcap, err, ebit);
+  const uint32_t slot = *s_fill + excl;
+  __syncthreads();
+  if (threadIdx.x == 0) *s_fill += total;
+  return slot;
+}
+
+// Lanes of `am` whose 8-bit value d equals the calling lane's (radix-rank
+// peer mask from 8 ballots; cheaper than a generic match on this GPU).
+__device__ __forceinline__ uint32_t peers8(uint32_t am, uint32_t d) {
+  uint32_t peers = am;
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    const uint32_t bal = __ballot_sync(am, (d >> b) & 1u);
+    peers &= ((d >> b) & 1u) ? bal : ~bal;
+  }
+  return peers;
+}
+
 // Thread-local run-length aggregation of shared-histogram increments: equal
 // consecutive bins (skewed or tied data) cost one shared atomic per run.
 struct RunHist {
@@ -272,6 +387,29 @@ __device__ __forceinline__ bool last_block(uint32_t* ticket) {
   __syncthreads();
   if (s_last) __threadfence();
   return s_last != 0;
+}
+
+// Same for a grid of which only the first `nact` blocks take part.
+__device__ __forceinline__ bool last_block_of(uint32_t* ticket, uint32_t nact) {
+  __shared__ uint32_t s_last2;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const uint32_t t = atomicAdd(ticket, 1u);
+    s_last2 = (t == nact - 1) ? 1u : 0u;
+  }
+  __syncthreads();
+  if (s_last2) __threadfence();
+  return s_last2 != 0;
+}
+
+// Number of blocks that have work when `count` items are processed
+// `per_step` at a time by a grid-stride loop (at least 1).
+__device__ __forceinline__ uint32_t active_blocks(int64_t count, int64_t per_step) {
+  int64_t a = (count + per_step - 1) / per_step;
+  if (a > static_cast<int64_t>(gridDim.x)) a = gridDim.x;
+  if (a < 1) a = 1;
+  return static_cast<uint32_t>(a);
 }
 
 // Picks the digit holding the k_rem-th largest of the histogram `h` (in

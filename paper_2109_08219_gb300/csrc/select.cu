@@ -34,7 +34,7 @@ constexpr uint32_t kScanned = 0x40000000u;  // tie count came from a scan
 constexpr uint32_t kCountMask = 0x3FFFFFFFu;
 constexpr int kTieSubPerThread = 8;
 constexpr int kTieSubPerBlock = kThreads * kTieSubPerThread;
-constexpr int kScanKPT = 32;  // virtual keys per thread per filter-scan step
+constexpr int kScanKPT = 16;  // virtual keys per thread per filter-scan step
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
   uint32_t m;
@@ -66,6 +66,30 @@ __device__ int64_t resolve_pos(const uint32_t* keys, int64_t n, int alpha, int64
   const int64_t gran = alpha < 5 ? (int64_t(1) << alpha) : 32;
   const int64_t lo = (i << alpha) + seg * gran;
   const int64_t hi = imin64(imin64(n, lo + gran), (i + 1) << alpha);
+  if (hi - lo == gran && (reinterpret_cast<uintptr_t>(keys + lo) & 15u) == 0) {
+    // whole segment, 16-byte aligned: issue every load at once
+    const uint4* v4 = reinterpret_cast<const uint4*>(keys + lo);
+    const int words = static_cast<int>(gran >> 2);
+    uint4 v[8];
+#pragma unroll
+    for (int w = 0; w < 8; ++w)
+      if (w < words) v[w] = __ldg(v4 + w);
+    int cnt = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+      if (w < words) {
+        const uint32_t e[4] = {v[w].x, v[w].y, v[w].z, v[w].w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (map_key<DT>(e[q]) == K) {
+            if (cnt == r) return lo + 4 * w + q;
+            ++cnt;
+          }
+        }
+      }
+    }
+    return -1;
+  }
   int cnt = 0;
   for (int64_t t = lo; t < hi; ++t) {
     if (map_key<DT>(__ldg(keys + t)) == K) {
@@ -96,51 +120,75 @@ int grid_for(int64_t work, int per_block, int sms, int per_sm) {
 }
 
 // ------------------------------------------------------------ threshold ---
+// Loads 16 consecutive-in-blocks keys per thread: word q (0..3) of thread t
+// in block step `base` covers keys base + (q * NT + t) * 4 .. + 3.
+template <int NT>
+__device__ __forceinline__ void load16(const uint32_t* a, int64_t count, int64_t base,
+                                       uint32_t (&v)[16]) {
+  // full words load unconditionally (clamped to the last full word); the
+  // ragged tail (count not a multiple of 4) is patched with scalar loads
+  const int64_t last_full = (count >> 2) - 1;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int64_t w = (base >> 2) + int64_t(q) * NT + threadIdx.x;
+    const int64_t wc = w < last_full ? w : (last_full < 0 ? 0 : last_full);
+    uint4 x = make_uint4(0, 0, 0, 0);
+    if (last_full >= 0) x = __ldcg(reinterpret_cast<const uint4*>(a) + wc);
+    v[q * 4 + 0] = x.x; v[q * 4 + 1] = x.y; v[q * 4 + 2] = x.z; v[q * 4 + 3] = x.w;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int64_t w = (base >> 2) + int64_t(q) * NT + threadIdx.x;
+    if (w > last_full) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) v[q * 4 + e] = (w * 4 + e < count) ? a[w * 4 + e] : 0u;
+    }
+  }
+}
+
+constexpr int kThrStageCap = kThreads * 16;
+
 // Digit 1 pass: keep the delegate keys whose first digit is the selected
-// one (compacted into ds) and histogram their second digit.
+// one (compacted into ds) and histogram their second digit. When the first
+// digit's bucket is large (ties, few distinct values) nothing is copied and
+// the later passes read the delegate keys in place.
 __global__ void __launch_bounds__(kThreads) thr_compact_kernel(const uint32_t* dkeys,
                                                                int64_t count, uint32_t* ds,
                                                                Ctl* ctl) {
   __shared__ uint32_t sh[256];
+  __shared__ uint32_t sbuf[kThrStageCap];
+  __shared__ uint32_t s_fill;
   zero_hist(sh);
+  if (threadIdx.x == 0) s_fill = 0;
   __syncthreads();
   SelState<4>* st = &ctl->dsel;
   const uint32_t d0 = static_cast<uint32_t>(__ldcg(&st->prefix)) >> 24;
+  const bool inplace = uint64_t(__ldcg(&st->bucket)) * 8 > static_cast<uint64_t>(count);
+  if (inplace && blockIdx.x == 0 && threadIdx.x == 0) ctl->ds_inplace = 1;
   RunHist rh;
   const int64_t step = int64_t(gridDim.x) * kThreads * 16;
   for (int64_t base = int64_t(blockIdx.x) * kThreads * 16; base < count; base += step) {
     uint32_t v[16];
-    uint32_t c = 0;
+    load16<kThreads>(dkeys, count, base, v);
+    uint32_t hit = 0;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int64_t i0 = base + (int64_t(q) * kThreads + threadIdx.x) * 4;
-      if (i0 + 3 < count) {
-        const uint4 x = __ldcg(reinterpret_cast<const uint4*>(dkeys + i0));
-        v[q * 4 + 0] = x.x; v[q * 4 + 1] = x.y; v[q * 4 + 2] = x.z; v[q * 4 + 3] = x.w;
-      } else {
-#pragma unroll
-        for (int e = 0; e < 4; ++e) v[q * 4 + e] = (i0 + e < count) ? dkeys[i0 + e] : 0u;
-      }
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const bool ok = (i0 + e < count) && ((v[q * 4 + e] >> 24) == d0);
-        c += ok;
+    for (int e = 0; e < 16; ++e) {
+      const int64_t i = base + (int64_t(e >> 2) * kThreads + threadIdx.x) * 4 + (e & 3);
+      if (i < count && (v[e] >> 24) == d0) {
+        hit |= 1u << e;
+        rh.add(sh, (v[e] >> 16) & 255u);
       }
     }
-    uint32_t slot = block_append<kThreads>(&ctl->ds_count, c);
+    if (!inplace) {
+      uint32_t slot = stage_reserve<uint32_t, kThreads, kThrStageCap>(
+          sbuf, &s_fill, __popc(hit), &ctl->ds_count, ds, ~uint64_t(0), &ctl->error, 0u);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int64_t i0 = base + (int64_t(q) * kThreads + threadIdx.x) * 4;
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const uint32_t x = v[q * 4 + e];
-        if ((i0 + e < count) && ((x >> 24) == d0)) {
-          ds[slot++] = x;
-          rh.add(sh, (x >> 16) & 255u);
-        }
-      }
+      for (int e = 0; e < 16; ++e)
+        if (hit & (1u << e)) sbuf[slot++] = v[e];
     }
   }
+  if (!inplace) stage_flush<uint32_t, kThreads>(sbuf, &s_fill, &ctl->ds_count, ds, ~uint64_t(0),
+                                                &ctl->error, 0u);
   rh.flush(sh);
   __syncthreads();
   flush_hist(sh, st->hist[1]);
@@ -149,28 +197,39 @@ __global__ void __launch_bounds__(kThreads) thr_compact_kernel(const uint32_t* d
   }
 }
 
-// Digit 2 and 3 passes over the compacted survivors.
-__global__ void __launch_bounds__(kThreads) thr_pass_kernel(const uint32_t* ds, Ctl* ctl,
+// Digit 2 and 3 passes over the compacted survivors (or the delegate keys).
+__global__ void __launch_bounds__(kThreads) thr_pass_kernel(const uint32_t* dsv,
+                                                            const uint32_t* dkeys,
+                                                            int64_t dcount, Ctl* ctl,
                                                             int pass) {
   __shared__ uint32_t sh[256];
   zero_hist(sh);
   __syncthreads();
   SelState<4>* st = &ctl->dsel;
-  const int64_t count = __ldcg(&ctl->ds_count);
+  const bool inplace = __ldcg(&ctl->ds_inplace) != 0;
+  const uint32_t* ds = inplace ? dkeys : dsv;
+  const int64_t count = inplace ? dcount : static_cast<int64_t>(__ldcg(&ctl->ds_count));
   const uint32_t prefix = static_cast<uint32_t>(__ldcg(&st->prefix));
   const uint32_t mask = 0xFFFFFFFFu << (32 - 8 * pass);
   const uint32_t want = prefix & mask;
   const int sh_d = 24 - 8 * pass;
+  const uint32_t nact = active_blocks(count, int64_t(kThreads) * 16);
+  if (blockIdx.x >= nact) return;
   RunHist rh;
-  for (int64_t i = int64_t(blockIdx.x) * kThreads + threadIdx.x; i < count;
-       i += int64_t(gridDim.x) * kThreads) {
-    const uint32_t x = ds[i];
-    if ((x & mask) == want) rh.add(sh, (x >> sh_d) & 255u);
+  const int64_t step = int64_t(nact) * kThreads * 16;
+  for (int64_t base = int64_t(blockIdx.x) * kThreads * 16; base < count; base += step) {
+    uint32_t v[16];
+    load16<kThreads>(ds, count, base, v);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      const int64_t i = base + (int64_t(e >> 2) * kThreads + threadIdx.x) * 4 + (e & 3);
+      if (i < count && (v[e] & mask) == want) rh.add(sh, (v[e] >> sh_d) & 255u);
+    }
   }
   rh.flush(sh);
   __syncthreads();
   flush_hist(sh, st->hist[pass]);
-  if (last_block(&st->ticket[pass])) {
+  if (last_block_of(&st->ticket[pass], nact)) {
     if (threadIdx.x < 32) {
       select_digit<4>(st, pass, 32, false);
       if (pass == 3 && threadIdx.x == 0) {
@@ -195,58 +254,82 @@ struct FilterParams {
   int kth_only;
 };
 
-// One thread per subrange: skip it (m^0 <= tau), queue it for a scan
-// (m^{beta-1} > tau: Rule 3 says every element may qualify) or emit its
-// delegates > tau (Rule 3: they are all of its elements > tau).
+// Each thread classifies 4 subranges per step: skip (m^0 <= tau), queue
+// for a scan (m^{beta-1} > tau: Rule 3 says every element may qualify) or
+// emit its delegates > tau (Rule 3: they are all of its elements > tau).
+// Queue entries and emitted candidates are staged in shared memory.
+constexpr int kClsSub = 4;
+constexpr int kClsGCap = kThreads * kClsSub * 4;
+constexpr int kClsQCap = kThreads * kClsSub * 2;
+
 template <int DT, int B>
 __global__ void __launch_bounds__(kThreads) filter_classify_kernel(FilterParams p) {
   __shared__ uint32_t sh[256];
+  __shared__ uint64_t gbuf[kClsGCap];
+  __shared__ uint32_t qbuf[kClsQCap];
+  __shared__ uint32_t g_fill, q_fill;
   zero_hist(sh);
+  if (threadIdx.x == 0) {
+    g_fill = 0;
+    q_fill = 0;
+  }
   __syncthreads();
   const uint32_t tau = __ldcg(&p.ctl->tau);
   const int alpha = p.alpha;
   uint32_t nscan = 0;
-  for (int64_t base = int64_t(blockIdx.x) * kThreads; base < p.S;
-       base += int64_t(gridDim.x) * kThreads) {
-    const int64_t i = base + threadIdx.x;
-    uint32_t dk[B];
-    uint16_t ds[B];
-    int cls = 0;  // 0 none, 1 delegates only, 2 scan
-    if (i < p.S) {
+  const int64_t per_step = int64_t(kThreads) * kClsSub;
+  for (int64_t base = int64_t(blockIdx.x) * per_step; base < p.S;
+       base += int64_t(gridDim.x) * per_step) {
+    uint32_t dk[kClsSub][B];
+    uint16_t ds[kClsSub][B];
+#pragma unroll
+    for (int u = 0; u < kClsSub; ++u) {
+      const int64_t i = base + int64_t(u) * kThreads + threadIdx.x;
 #pragma unroll
       for (int j = 0; j < B; ++j) {
-        dk[j] = p.dkeys[i * B + j];
-        ds[j] = p.dsegs[i * B + j];
+        dk[u][j] = (i < p.S) ? p.dkeys[i * B + j] : 0u;
+        ds[u][j] = (i < p.S) ? p.dsegs[i * B + j] : static_cast<uint16_t>(kNoSeg);
       }
-      if (dk[0] > tau) cls = (dk[B - 1] > tau && sub_len(i, alpha, p.n) > B) ? 2 : 1;
     }
-    const uint32_t qs = block_append<kThreads>(&p.ctl->scanq_count, cls == 2);
-    if (cls == 2) {
-      p.scanq[qs] = static_cast<uint32_t>(i);
-      ++nscan;
-    }
-    uint64_t items[B];
-    uint32_t cnt = 0;
-    if (cls == 1) {
+    uint32_t scanm = 0, nitems = 0;
+    uint64_t items[kClsSub * B];
 #pragma unroll
-      for (int j = 0; j < B; ++j) {
-        if (dk[j] > tau) {
-          const int r = occ_rank<B>(dk, ds, j);
-          const int64_t pos = resolve_pos<DT>(p.keys, p.n, alpha, i, ds[j], dk[j], r);
-          if (pos < 0) atomicOr(&p.ctl->error, kErrTieRank);
-          items[cnt++] = make_comp(dk[j], static_cast<uint32_t>(pos));
+    for (int u = 0; u < kClsSub; ++u) {
+      const int64_t i = base + int64_t(u) * kThreads + threadIdx.x;
+      if (i < p.S && dk[u][0] > tau) {
+        if (dk[u][B - 1] > tau && sub_len(i, alpha, p.n) > B) {
+          scanm |= 1u << u;
+        } else {
+#pragma unroll
+          for (int j = 0; j < B; ++j) {
+            if (dk[u][j] > tau) {
+              const int r = occ_rank<B>(dk[u], ds[u], j);
+              const int64_t pos = resolve_pos<DT>(p.keys, p.n, alpha, i, ds[u][j], dk[u][j], r);
+              if (pos < 0) atomicOr(&p.ctl->error, kErrTieRank);
+              items[nitems++] = make_comp(dk[u][j], static_cast<uint32_t>(pos));
+            }
+          }
         }
       }
     }
-    const uint32_t slot = block_append<kThreads>(&p.ctl->g_count, cnt);
-    for (uint32_t e = 0; e < cnt; ++e) {
-      const uint64_t s = uint64_t(slot) + e;
-      if (s < static_cast<uint64_t>(p.g_cap)) p.g[s] = items[e];
-      else atomicOr(&p.ctl->error, kErrOverflowG);
+    uint32_t qs = stage_reserve<uint32_t, kThreads, kClsQCap>(
+        qbuf, &q_fill, __popc(scanm), &p.ctl->scanq_count, p.scanq, ~uint64_t(0), &p.ctl->error, 0u);
+#pragma unroll
+    for (int u = 0; u < kClsSub; ++u)
+      if (scanm & (1u << u)) qbuf[qs++] = static_cast<uint32_t>(base + int64_t(u) * kThreads + threadIdx.x);
+    nscan += __popc(scanm);
+    uint32_t gs = stage_reserve<uint64_t, kThreads, kClsGCap>(
+        gbuf, &g_fill, nitems, &p.ctl->g_count, p.g, static_cast<uint64_t>(p.g_cap), &p.ctl->error,
+        kErrOverflowG);
+    for (uint32_t e = 0; e < nitems; ++e) {
+      gbuf[gs + e] = items[e];
       atomicAdd(&sh[static_cast<uint32_t>(items[e] >> 56)], 1u);
     }
   }
-  __syncthreads();
+  stage_flush<uint32_t, kThreads>(qbuf, &q_fill, &p.ctl->scanq_count, p.scanq, ~uint64_t(0),
+                                  &p.ctl->error, 0u);
+  stage_flush<uint64_t, kThreads>(gbuf, &g_fill, &p.ctl->g_count, p.g,
+                                  static_cast<uint64_t>(p.g_cap), &p.ctl->error, kErrOverflowG);
   flush_hist(sh, p.ctl->gsel.hist[0]);
   if (nscan) atomicAdd(&p.ctl->scanned, nscan);
 }
@@ -264,40 +347,53 @@ __global__ void __launch_bounds__(kThreads) filter_scan_kernel(FilterParams p) {
   const int64_t nq = __ldcg(&p.ctl->scanq_count);
   const int64_t total = nq << alpha;
   const int64_t mask = (int64_t(1) << alpha) - 1;
+  const uint32_t nact = active_blocks(total, int64_t(kThreads) * kScanKPT);
+  if (blockIdx.x >= nact) return;
   RunHist rh;
-  const int64_t step = int64_t(gridDim.x) * kThreads * kScanKPT;
+  const int64_t step = int64_t(nact) * kThreads * kScanKPT;
   for (int64_t base = int64_t(blockIdx.x) * kThreads * kScanKPT; base < total; base += step) {
     uint32_t x[kScanKPT];
+    uint32_t sq[kScanKPT];
     uint32_t hit = 0;
+    // phase 1: queue entries (independent loads, all in flight)
+#pragma unroll
+    for (int u = 0; u < kScanKPT; ++u) {
+      const int64_t v = imin64(base + threadIdx.x + int64_t(u) * kThreads, total - 1);
+      sq[u] = __ldg(p.scanq + (v >> alpha));
+    }
+    // phase 2: keys (clamped addresses, unconditional loads)
 #pragma unroll
     for (int u = 0; u < kScanKPT; ++u) {
       const int64_t v = base + threadIdx.x + int64_t(u) * kThreads;
-      x[u] = 0;
-      if (v < total) {
-        const int64_t gi = (int64_t(__ldg(p.scanq + (v >> alpha))) << alpha) + (v & mask);
-        if (gi < p.n) {
-          x[u] = map_key<DT>(__ldg(p.keys + gi));
-          if (x[u] > tau) hit |= 1u << u;
-        }
-      }
+      const int64_t gi = (int64_t(sq[u]) << alpha) + (v & mask);
+      const bool ok = v < total && gi < p.n;
+      x[u] = map_key<DT>(__ldg(p.keys + (ok ? gi : 0)));
+      if (ok && x[u] > tau) hit |= 1u << u;
     }
-    uint32_t slot = block_append<kThreads>(&p.ctl->g_count, __popc(hit));
+    const uint32_t wt = __reduce_add_sync(0xFFFFFFFFu, __popc(hit));
+    uint32_t wb, unused;
+    block_reserve2<kThreads>(&p.ctl->g_count, wt, nullptr, 0, wb, unused);
+    const uint32_t lt = lanemask_lt();
+    uint32_t run = 0;
 #pragma unroll
     for (int u = 0; u < kScanKPT; ++u) {
-      if (hit & (1u << u)) {
+      const bool h = (hit >> u) & 1u;
+      const uint32_t bal = __ballot_sync(0xFFFFFFFFu, h);
+      if (h) {
         const int64_t v = base + threadIdx.x + int64_t(u) * kThreads;
-        const int64_t gi = (int64_t(__ldg(p.scanq + (v >> alpha))) << alpha) + (v & mask);
+        const int64_t gi = (int64_t(sq[u]) << alpha) + (v & mask);
+        const uint32_t slot = wb + run + __popc(bal & lt);
         if (slot < p.g_cap) p.g[slot] = make_comp(x[u], static_cast<uint32_t>(gi));
         else atomicOr(&p.ctl->error, kErrOverflowG);
-        ++slot;
         rh.add(sh, x[u] >> 24);
       }
+      run += __popc(bal);
     }
   }
   rh.flush(sh);
   __syncthreads();
   flush_hist(sh, p.ctl->gsel.hist[0]);
-  if (last_block(&p.ctl->filter_ticket)) {
+  if (last_block_of(&p.ctl->filter_ticket, nact)) {
     if (threadIdx.x < 32) {
       Ctl* ctl = p.ctl;
       const uint32_t g = __ldcg(&ctl->g_count);
@@ -334,6 +430,9 @@ struct GSelParams {
   int kth_only;
 };
 
+constexpr int kGIpt = 16;
+constexpr int kGCap = kThreads * kGIpt;  // one step's worth per buffer
+
 __global__ void __launch_bounds__(kThreads) gstage_kernel(GSelParams p, int s) {
   Ctl* ctl = p.ctl;
   if (__ldcg(&ctl->mode) != kModeSelect) return;
@@ -341,8 +440,18 @@ __global__ void __launch_bounds__(kThreads) gstage_kernel(GSelParams p, int s) {
   const int64_t count = (s == 1) ? imin64(__ldcg(&ctl->g_count), p.g_cap)
                                  : static_cast<int64_t>(__ldcg(&ctl->stage_count[s]));
   if (count == 0) return;  // uniform over the grid: nothing survived
+  const uint32_t nact = active_blocks(count, int64_t(kThreads) * kGIpt);
+  if (blockIdx.x >= nact) return;
   __shared__ uint32_t sh[256];
+  extern __shared__ __align__(16) uint64_t gsm[];
+  uint64_t* wbuf = gsm;           // winners staged
+  uint64_t* sbuf = gsm + kGCap;   // survivors staged
+  __shared__ uint32_t w_fill, s_fill;
   zero_hist(sh);
+  if (threadIdx.x == 0) {
+    w_fill = 0;
+    s_fill = 0;
+  }
   __syncthreads();
   const uint64_t* src = (s & 1) ? p.g : p.sv;
   uint64_t* dst = (s & 1) ? p.sv : p.g;
@@ -352,47 +461,59 @@ __global__ void __launch_bounds__(kThreads) gstage_kernel(GSelParams p, int s) {
   const bool last = (level == 7);
   const int nsh = 48 - 8 * level;  // next digit shift
   RunHist rh;
-  constexpr int IPT = 8;
-  const int64_t stepn = int64_t(gridDim.x) * kThreads * IPT;
-  for (int64_t base = int64_t(blockIdx.x) * kThreads * IPT; base < count; base += stepn) {
-    uint64_t c[IPT];
+  const int64_t stepn = int64_t(nact) * kThreads * kGIpt;
+  for (int64_t base = int64_t(blockIdx.x) * kThreads * kGIpt; base < count; base += stepn) {
+    uint64_t c[kGIpt];
     uint32_t win = 0, sur = 0;
 #pragma unroll
-    for (int u = 0; u < IPT; ++u) {
+    for (int u = 0; u < kGIpt; ++u) {
       const int64_t i = base + threadIdx.x + int64_t(u) * kThreads;
-      c[u] = 0;
+      c[u] = __ldcg(src + imin64(i, count - 1));
+    }
+#pragma unroll
+    for (int u = 0; u < kGIpt; ++u) {
+      const int64_t i = base + threadIdx.x + int64_t(u) * kThreads;
+      const uint32_t dg = static_cast<uint32_t>(c[u] >> (56 - 8 * level)) & 255u;
       if (i < count) {
-        c[u] = src[i];
-        const uint32_t dg = static_cast<uint32_t>(c[u] >> (56 - 8 * level)) & 255u;
         if (dg > d || (dg == d && (done || last))) win |= 1u << u;
         else if (dg == d) sur |= 1u << u;
       }
     }
-    if (!p.kth_only) {
-      uint32_t ws = block_append<kThreads>(&ctl->w_count, __popc(win));
-#pragma unroll
-      for (int u = 0; u < IPT; ++u) {
-        if (win & (1u << u)) {
-          if (ws < p.k) p.w[ws] = c[u];
-          else atomicOr(&ctl->error, kErrOverflowW);
-          ++ws;
-        }
-      }
+    if (p.kth_only) win = 0;  // k-selection keeps no winners
+    // one block scan reserves both staged outputs (16-bit fields)
+    uint32_t tot;
+    const uint32_t ex = block_scan_excl<kThreads>(__popc(win) | (__popc(sur) << 16), &tot);
+    if (w_fill + (tot & 0xFFFFu) > kGCap)
+      stage_flush<uint64_t, kThreads>(wbuf, &w_fill, &ctl->w_count, p.w, static_cast<uint64_t>(p.k),
+                                      &ctl->error, kErrOverflowW);
+    if (s_fill + (tot >> 16) > kGCap)
+      stage_flush<uint64_t, kThreads>(sbuf, &s_fill, &ctl->stage_count[s + 1], dst,
+                                      static_cast<uint64_t>(p.g_cap), &ctl->error, kErrOverflowG);
+    uint32_t ws = w_fill + (ex & 0xFFFFu);
+    uint32_t ss = s_fill + (ex >> 16);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      w_fill += tot & 0xFFFFu;
+      s_fill += tot >> 16;
     }
-    uint32_t ss = block_append<kThreads>(&ctl->stage_count[s + 1], __popc(sur));
 #pragma unroll
-    for (int u = 0; u < IPT; ++u) {
+    for (int u = 0; u < kGIpt; ++u) {
+      if (win & (1u << u)) wbuf[ws++] = c[u];
       if (sur & (1u << u)) {
-        dst[ss++] = c[u];
+        sbuf[ss++] = c[u];
         if (nsh >= 0) rh.add(sh, static_cast<uint32_t>(c[u] >> nsh) & 255u);
       }
     }
   }
+  stage_flush<uint64_t, kThreads>(wbuf, &w_fill, &ctl->w_count, p.w, static_cast<uint64_t>(p.k),
+                                  &ctl->error, kErrOverflowW);
+  stage_flush<uint64_t, kThreads>(sbuf, &s_fill, &ctl->stage_count[s + 1], dst,
+                                  static_cast<uint64_t>(p.g_cap), &ctl->error, kErrOverflowG);
   if (last || done) return;  // no further digit to select (uniform)
   rh.flush(sh);
   __syncthreads();
   flush_hist(sh, ctl->gsel.hist[level + 1]);
-  if (last_block(&ctl->gsel.ticket[level + 1])) {
+  if (last_block_of(&ctl->gsel.ticket[level + 1], nact)) {
     if (threadIdx.x < 32) select_digit<8>(&ctl->gsel, level + 1, 64, !p.kth_only);
   }
 }
@@ -444,18 +565,26 @@ __global__ void __launch_bounds__(kThreads) tie_lb_kernel(TieParams p) {
   Ctl* ctl = p.ctl;
   if (__ldcg(&ctl->mode) != kModeTies) return;
   const uint32_t tau = __ldcg(&ctl->tau);
-  const int64_t i0 = int64_t(blockIdx.x) * kTieSubPerBlock + threadIdx.x * kTieSubPerThread;
+  for (int64_t b = blockIdx.x; b < p.nblk; b += gridDim.x) {
+  const int64_t i0 = b * kTieSubPerBlock + threadIdx.x * kTieSubPerThread;
   uint32_t sum = 0;
+  uint32_t dka[kTieSubPerThread][B];
+  uint16_t dsa[kTieSubPerThread][B];
+#pragma unroll
+  for (int e = 0; e < kTieSubPerThread; ++e) {
+    const int64_t i = i0 + e;
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+      dka[e][j] = (i < p.S) ? p.dkeys[i * B + j] : 0u;
+      dsa[e][j] = (i < p.S) ? p.dsegs[i * B + j] : static_cast<uint16_t>(kNoSeg);
+    }
+  }
+#pragma unroll
   for (int e = 0; e < kTieSubPerThread; ++e) {
     const int64_t i = i0 + e;
     if (i >= p.S) break;
-    uint32_t dk[B];
-    uint16_t ds[B];
-#pragma unroll
-    for (int j = 0; j < B; ++j) {
-      dk[j] = p.dkeys[i * B + j];
-      ds[j] = p.dsegs[i * B + j];
-    }
+    const uint32_t* dk = dka[e];
+    const uint16_t* ds = dsa[e];
     const int64_t len = sub_len(i, p.alpha, p.n);
     uint32_t t;
     if (dk[0] < tau) {
@@ -474,8 +603,9 @@ __global__ void __launch_bounds__(kThreads) tie_lb_kernel(TieParams p) {
   uint32_t tot;
   block_excl_scan(sum, &tot);
   if (threadIdx.x == 0) {
-    p.bsum1[blockIdx.x] = tot;
-    p.bsum2[blockIdx.x] = tot;
+    p.bsum1[b] = tot;
+    p.bsum2[b] = tot;
+  }
   }
 }
 
@@ -506,10 +636,10 @@ __global__ void __launch_bounds__(1024) scan_blocks_kernel(uint32_t* a, int64_t 
 
 // Per-thread exclusive prefixes of the 8 tie counts it owns, offset by the
 // block's scanned sum: pre[e] = number of ties (as counted) before subrange e.
-__device__ __forceinline__ void tie_prefixes(const TieParams& p, const uint32_t* bscan,
+__device__ __forceinline__ void tie_prefixes(const TieParams& p, const uint32_t* bscan, int64_t b,
                                              uint32_t (&t)[kTieSubPerThread],
                                              uint32_t (&pre)[kTieSubPerThread]) {
-  const int64_t i0 = int64_t(blockIdx.x) * kTieSubPerBlock + threadIdx.x * kTieSubPerThread;
+  const int64_t i0 = b * kTieSubPerBlock + threadIdx.x * kTieSubPerThread;
   uint32_t sum = 0;
 #pragma unroll
   for (int e = 0; e < kTieSubPerThread; ++e) {
@@ -518,7 +648,7 @@ __device__ __forceinline__ void tie_prefixes(const TieParams& p, const uint32_t*
     pre[e] = sum;
     sum += t[e] & kCountMask;
   }
-  const uint32_t off = block_excl_scan(sum, nullptr) + bscan[blockIdx.x];
+  const uint32_t off = block_excl_scan(sum, nullptr) + bscan[b];
 #pragma unroll
   for (int e = 0; e < kTieSubPerThread; ++e) pre[e] += off;
 }
@@ -530,20 +660,42 @@ __global__ void __launch_bounds__(kThreads) tie_enqueue_kernel(TieParams p) {
   Ctl* ctl = p.ctl;
   if (__ldcg(&ctl->mode) != kModeTies) return;
   const uint32_t need = __ldcg(&ctl->need);
-  uint32_t t[kTieSubPerThread], pre[kTieSubPerThread];
-  tie_prefixes(p, p.bsum1, t, pre);
-  const int64_t i0 = int64_t(blockIdx.x) * kTieSubPerBlock + threadIdx.x * kTieSubPerThread;
-  uint32_t c = 0;
+  for (int64_t b = blockIdx.x; b < p.nblk; b += gridDim.x) {
+    uint32_t t[kTieSubPerThread], pre[kTieSubPerThread];
+    tie_prefixes(p, p.bsum1, b, t, pre);
+    const int64_t i0 = b * kTieSubPerBlock + threadIdx.x * kTieSubPerThread;
+    uint32_t c = 0;
 #pragma unroll
-  for (int e = 0; e < kTieSubPerThread; ++e) c += ((t[e] & kInexact) && pre[e] < need);
-  uint32_t slot = block_append<kThreads>(&ctl->tieq1_count, c);
+    for (int e = 0; e < kTieSubPerThread; ++e) c += ((t[e] & kInexact) && pre[e] < need);
+    uint32_t slot = block_append<kThreads>(&ctl->tieq1_count, c);
 #pragma unroll
-  for (int e = 0; e < kTieSubPerThread; ++e)
-    if ((t[e] & kInexact) && pre[e] < need) p.q1[slot++] = static_cast<uint32_t>(i0 + e);
+    for (int e = 0; e < kTieSubPerThread; ++e)
+      if ((t[e] & kInexact) && pre[e] < need) p.q1[slot++] = static_cast<uint32_t>(i0 + e);
+  }
 }
 
 // Exact tie counts of the queued subranges, one warp per subrange over the
 // whole grid; the block sums used for the second scan are corrected in place.
+// Ties equal to tau among keys [lo, lo + len), read by one thread (len <= 64).
+template <int DT>
+__device__ __forceinline__ uint32_t count_eq_thread(const uint32_t* keys, int64_t lo, int64_t len,
+                                                    uint32_t tau) {
+  uint32_t c = 0;
+  if ((len & 3) == 0 && (reinterpret_cast<uintptr_t>(keys + lo) & 15u) == 0) {
+    const uint4* v4 = reinterpret_cast<const uint4*>(keys + lo);
+    for (int64_t w = 0; w < (len >> 2); ++w) {
+      const uint4 v = __ldg(v4 + w);
+      c += (map_key<DT>(v.x) == tau) + (map_key<DT>(v.y) == tau) + (map_key<DT>(v.z) == tau) +
+           (map_key<DT>(v.w) == tau);
+    }
+  } else {
+    for (int64_t t = 0; t < len; ++t) c += (map_key<DT>(__ldg(keys + lo + t)) == tau);
+  }
+  return c;
+}
+
+constexpr int kTieThreadAlpha = 6;  // subranges of <= 64 keys: one thread each
+
 template <int DT>
 __global__ void __launch_bounds__(kThreads) tie_count_kernel(TieParams p) {
   Ctl* ctl = p.ctl;
@@ -553,6 +705,32 @@ __global__ void __launch_bounds__(kThreads) tie_count_kernel(TieParams p) {
   const uint32_t lane = lane_id();
   const int64_t warps = int64_t(gridDim.x) * (kThreads / 32);
   uint32_t done = 0;
+  if (p.alpha <= kTieThreadAlpha) {
+    const int64_t nthr = int64_t(gridDim.x) * kThreads;
+    for (int64_t q0 = int64_t(blockIdx.x) * kThreads; q0 < nq; q0 += nthr) {
+      const int64_t q = q0 + threadIdx.x;
+      uint32_t delta = 0;
+      int64_t blk = -1;
+      if (q < nq) {
+        const int64_t i = p.q1[q];
+        const uint32_t c = count_eq_thread<DT>(p.keys, i << p.alpha, sub_len(i, p.alpha, p.n), tau);
+        delta = c - (p.tcnt[i] & kCountMask);
+        p.tcnt[i] = c | kScanned;
+        blk = i / kTieSubPerBlock;
+        ++done;
+      }
+      // consecutive queue entries mostly share a block sum: add once per group
+      const uint32_t am = __ballot_sync(0xFFFFFFFFu, q < nq);
+      if (q < nq) {
+        const uint32_t peers = __match_any_sync(am, static_cast<unsigned long long>(blk));
+        const uint32_t tot = __reduce_add_sync(peers, delta);
+        if ((peers & lanemask_lt()) == 0) atomicAdd(&p.bsum2[blk], tot);
+      }
+    }
+    done = __reduce_add_sync(0xFFFFFFFFu, done);
+    if (lane == 0 && done) atomicAdd(&ctl->tie_scanned, done);
+    return;
+  }
   for (int64_t q = int64_t(blockIdx.x) * (kThreads / 32) + (threadIdx.x >> 5); q < nq;
        q += warps) {
     const int64_t i = p.q1[q];
@@ -584,19 +762,21 @@ __global__ void __launch_bounds__(kThreads) tie_emit_enqueue_kernel(TieParams p)
        j += int64_t(gridDim.x) * kThreads)
     p.w[j] = p.g[j];
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&ctl->w_count, g);
-  uint32_t t[kTieSubPerThread], pre[kTieSubPerThread];
-  tie_prefixes(p, p.bsum2, t, pre);
-  const int64_t i0 = int64_t(blockIdx.x) * kTieSubPerBlock + threadIdx.x * kTieSubPerThread;
-  uint32_t c = 0;
+  for (int64_t b = blockIdx.x; b < p.nblk; b += gridDim.x) {
+    uint32_t t[kTieSubPerThread], pre[kTieSubPerThread];
+    tie_prefixes(p, p.bsum2, b, t, pre);
+    const int64_t i0 = b * kTieSubPerBlock + threadIdx.x * kTieSubPerThread;
+    uint32_t c = 0;
 #pragma unroll
-  for (int e = 0; e < kTieSubPerThread; ++e) c += ((t[e] & kCountMask) > 0 && pre[e] < need);
-  uint32_t slot = block_append<kThreads>(&ctl->tieq2_count, c);
+    for (int e = 0; e < kTieSubPerThread; ++e) c += ((t[e] & kCountMask) > 0 && pre[e] < need);
+    uint32_t slot = block_append<kThreads>(&ctl->tieq2_count, c);
 #pragma unroll
-  for (int e = 0; e < kTieSubPerThread; ++e) {
-    if ((t[e] & kCountMask) > 0 && pre[e] < need) {
-      p.q2[slot] = static_cast<uint32_t>(i0 + e);
-      p.q2pre[slot] = pre[e];
-      ++slot;
+    for (int e = 0; e < kTieSubPerThread; ++e) {
+      if ((t[e] & kCountMask) > 0 && pre[e] < need) {
+        p.q2[slot] = static_cast<uint32_t>(i0 + e);
+        p.q2pre[slot] = pre[e];
+        ++slot;
+      }
     }
   }
 }
@@ -613,8 +793,52 @@ __global__ void __launch_bounds__(kThreads) tie_emit_kernel(TieParams p) {
   const uint32_t lane = lane_id();
   const int64_t warps = int64_t(gridDim.x) * (kThreads / 32);
   uint32_t emitted_total = 0;
-  for (int64_t q = int64_t(blockIdx.x) * (kThreads / 32) + (threadIdx.x >> 5); q < nq;
-       q += warps) {
+  if (p.alpha <= kTieThreadAlpha) {
+    // one thread per subrange, reading it in index order
+    for (int64_t q = int64_t(blockIdx.x) * kThreads + threadIdx.x; q < nq;
+         q += int64_t(gridDim.x) * kThreads) {
+      const int64_t i = p.q2[q];
+      uint32_t r = p.q2pre[q];
+      if (p.tcnt[i] & kScanned) {
+        const int64_t lo = i << p.alpha;
+        const int64_t len = sub_len(i, p.alpha, p.n);
+        for (int64_t t0 = 0; t0 < len && r < need; t0 += 16) {
+          uint32_t v[16];
+#pragma unroll
+          for (int e = 0; e < 16; ++e) v[e] = (t0 + e < len) ? __ldg(p.keys + lo + t0 + e) : 0u;
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            if (t0 + e < len && r < need && map_key<DT>(v[e]) == tau) {
+              p.w[g + r] = make_comp(tau, static_cast<uint32_t>(lo + t0 + e));
+              ++r;
+              ++emitted_total;
+            }
+          }
+        }
+      } else {
+        uint32_t dk[B];
+        uint16_t ds[B];
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+          dk[j] = p.dkeys[i * B + j];
+          ds[j] = p.dsegs[i * B + j];
+        }
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+          if (dk[j] == tau && ds[j] != kNoSeg && r < need) {
+            const int o = occ_rank<B>(dk, ds, j);
+            const int64_t pos = resolve_pos<DT>(p.keys, p.n, p.alpha, i, ds[j], tau, o);
+            if (pos < 0) atomicOr(&ctl->error, kErrTieRank);
+            p.w[g + r] = make_comp(tau, static_cast<uint32_t>(pos));
+            ++r;
+            ++emitted_total;
+          }
+        }
+      }
+    }
+  }
+  for (int64_t q = int64_t(blockIdx.x) * (kThreads / 32) + (threadIdx.x >> 5);
+       p.alpha > kTieThreadAlpha && q < nq; q += warps) {
     const int64_t i = p.q2[q];
     const uint32_t base = p.q2pre[q];
     const uint32_t tt = p.tcnt[i];
@@ -707,8 +931,8 @@ cudaError_t launch_threshold(const Work& w, int sms, cudaStream_t s) {
   const int g1 = grid_for(count, kThreads * 16, sms, 4);
   thr_compact_kernel<<<g1, kThreads, 0, s>>>(w.dkeys, count, w.ds, w.ctl);
   const int g2 = grid_for(count, kThreads * 8, sms, 4);
-  thr_pass_kernel<<<g2, kThreads, 0, s>>>(w.ds, w.ctl, 2);
-  thr_pass_kernel<<<g2, kThreads, 0, s>>>(w.ds, w.ctl, 3);
+  thr_pass_kernel<<<g2, kThreads, 0, s>>>(w.ds, w.dkeys, count, w.ctl, 2);
+  thr_pass_kernel<<<g2, kThreads, 0, s>>>(w.ds, w.dkeys, count, w.ctl, 3);
   note_launch(3);
   return cudaGetLastError();
 }
@@ -773,8 +997,8 @@ cudaError_t launch_ties(const Work& w, const void* keys, int sms, cudaStream_t s
   p.g = w.g;
   p.w = w.w;
   p.ctl = w.ctl;
-  const int grid = static_cast<int>(p.nblk);
-  const int gq = grid_for(w.S, kThreads / 32, sms, 8);
+  const int grid = static_cast<int>(std::min<int64_t>(p.nblk, int64_t(sms) * 4));
+  const int gq = grid_for(w.S, kThreads / 32, sms, 4);
 #define DRTOPK_TIE_CASE(DTV)                                                        \
   switch (w.beta) {                                                                 \
     case 1: tie_lb_kernel<1><<<grid, kThreads, 0, s>>>(p); break;                   \
@@ -812,11 +1036,14 @@ cudaError_t launch_gselect(const Work& w, bool kth_only, int sms, cudaStream_t s
   p.k = w.k;
   p.ctl = w.ctl;
   p.kth_only = kth_only ? 1 : 0;
-  const int grid = grid_for(w.g_cap, kThreads * 8, sms, 8);
+  const int grid = grid_for(w.g_cap, kThreads * kGIpt, sms, 2);
+  const size_t dsm = size_t(2) * kGCap * sizeof(uint64_t);
+  cudaFuncSetAttribute(gstage_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       static_cast<int>(dsm));
   // k-selection needs the 4 key digits (stages 1-3 decide digits 0-2 and
   // select digit 3); top-k resolves all 8 digits of the composite.
   const int last = kth_only ? 3 : 8;
-  for (int st = 1; st <= last; ++st) gstage_kernel<<<grid, kThreads, 0, s>>>(p, st);
+  for (int st = 1; st <= last; ++st) gstage_kernel<<<grid, kThreads, dsm, s>>>(p, st);
   note_launch(last);
   return cudaGetLastError();
 }

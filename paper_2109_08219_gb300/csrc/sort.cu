@@ -17,9 +17,10 @@ namespace drtopk {
 namespace {
 
 constexpr int kSmallSort = 4096;
-constexpr int kSortThreads = 256;
+constexpr int kSortThreads = 512;
 constexpr int kItems = 16;
-constexpr int kTile = kSortThreads * kItems;  // 4096
+constexpr int kTile = kSortThreads * kItems;  // 16384
+constexpr int kHistThreads = 256;
 constexpr uint64_t kFlagAgg = uint64_t(1) << 32;
 constexpr uint64_t kFlagIncl = uint64_t(2) << 32;
 constexpr uint32_t kLookbackSpin = 1u << 22;
@@ -93,135 +94,197 @@ __device__ __forceinline__ uint32_t sdigit(uint64_t c, int pass) {
   return static_cast<uint32_t>((~c) >> (8 * pass)) & 255u;
 }
 
-__global__ void __launch_bounds__(kSortThreads) sort_hist_all_kernel(SortParams p) {
+__global__ void __launch_bounds__(kHistThreads) sort_hist_all_kernel(SortParams p) {
   __shared__ uint32_t sh[8][256];
-  for (int i = threadIdx.x; i < 8 * 256; i += kSortThreads) (&sh[0][0])[i] = 0;
+  for (int i = threadIdx.x; i < 8 * 256; i += kHistThreads) (&sh[0][0])[i] = 0;
   __syncthreads();
   const uint64_t* src = p.buf[0];
-  for (int64_t i = int64_t(blockIdx.x) * kSortThreads + threadIdx.x; i < p.k;
-       i += int64_t(gridDim.x) * kSortThreads) {
-    const uint64_t c = src[i];
+  const uint32_t lane = lane_id();
+  for (int64_t b = int64_t(blockIdx.x) * kHistThreads; b < p.k;
+       b += int64_t(gridDim.x) * kHistThreads) {
+    const int64_t i = b + threadIdx.x;
+    const bool act = i < p.k;
+    const uint32_t am = __ballot_sync(0xFFFFFFFFu, act);
+    if (act) {
+      const uint64_t c = src[i];
+      const int leader = __ffs(am) - 1;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) atomicAdd(&sh[q][sdigit(c, q)], 1u);
+      for (int q = 0; q < 8; ++q) {
+        const uint32_t d = sdigit(c, q);
+        // a digit equal across the warp (common: high key bytes) adds once
+        if (__all_sync(am, d == __shfl_sync(am, d, leader))) {
+          if (static_cast<int>(lane) == leader) atomicAdd(&sh[q][d], __popc(am));
+        } else {
+          atomicAdd(&sh[q][d], 1u);
+        }
+      }
+    }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < 8 * 256; i += kSortThreads) {
+  for (int i = threadIdx.x; i < 8 * 256; i += kHistThreads) {
     const uint32_t v = (&sh[0][0])[i];
     if (v) atomicAdd(&(&p.ctl->sort_hist[0][0])[i], v);
   }
   if (last_block(&p.ctl->sort_ticket)) {
-    if (threadIdx.x < 8) {
-      // exclusive offsets per digit; a digit that holds all k entries is skipped
-      uint32_t* h = p.ctl->sort_hist[threadIdx.x];
-      uint32_t run = 0, skip = 0;
-      for (int d = 0; d < 256; ++d) {
-        const uint32_t v = __ldcg(&h[d]);
-        if (v == static_cast<uint32_t>(p.k)) skip = 1;
-        h[d] = run;
-        run += v;
-      }
-      p.ctl->sort_skip[threadIdx.x] = skip;
+    // exclusive offsets per digit, all 8 digit histograms at once (thread d
+    // owns bin d of every digit); a digit that holds all k entries is skipped
+    __syncthreads();
+    uint32_t v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = __ldcg(&p.ctl->sort_hist[q][threadIdx.x]);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const uint32_t e = block_scan_excl<kHistThreads>(v[q], nullptr);
+      p.ctl->sort_hist[q][threadIdx.x] = e;
+      const int full = __syncthreads_or(v[q] == static_cast<uint32_t>(p.k));
+      if (threadIdx.x == 0) p.ctl->sort_skip[q] = full ? 1u : 0u;
     }
   }
 }
 
-__global__ void __launch_bounds__(kSortThreads) sort_pass_kernel(SortParams p, int pass) {
+__global__ void __launch_bounds__(kSortThreads, 1) sort_pass_kernel(SortParams p, int pass) {
   Ctl* ctl = p.ctl;
-  if (__ldcg(&ctl->sort_skip[pass])) return;
+  uint32_t skip[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) skip[q] = __ldcg(&ctl->sort_skip[q]);
+  if (skip[pass]) return;
   uint32_t par = 0;
-  for (int q = 0; q < pass; ++q) par ^= (__ldcg(&ctl->sort_skip[q]) == 0);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) par ^= (q < pass && skip[q] == 0) ? 1u : 0u;
   const uint64_t* src = p.buf[par];
   uint64_t* dst = p.buf[par ^ 1u];
 
+  constexpr int kWarpsS = kSortThreads / 32;
+  constexpr int kPerWarp = kTile / kWarpsS;  // consecutive tile positions per warp
   __shared__ uint32_t s_tile;
-  __shared__ uint32_t base[256];
-  __shared__ uint32_t wcnt[kSortThreads / 32][256];
+  __shared__ uint32_t wcnt[kWarpsS][256];
   __shared__ uint32_t s_off[256];
+  __shared__ uint32_t s_start[256];
+  extern __shared__ __align__(16) uint64_t s_el[];  // kTile entries, then kTile u16 ranks
+  uint16_t* s_rank = reinterpret_cast<uint16_t*>(s_el + kTile);
   if (threadIdx.x == 0) s_tile = atomicAdd(&ctl->sort_tiles[pass], 1u);
-  for (int d = threadIdx.x; d < 256; d += kSortThreads) base[d] = 0;
+  for (int q = threadIdx.x; q < kWarpsS * 256; q += kSortThreads) (&wcnt[0][0])[q] = 0;
   __syncthreads();
   const int64_t tile = s_tile;
   const int warp = threadIdx.x >> 5;
-  const int64_t t0 = tile * kTile;
+  const uint32_t lane = lane_id();
+  const int64_t w0 = tile * kTile + int64_t(warp) * kPerWarp;
 
+  // stable ranking: warp w owns kPerWarp consecutive tile positions, 32 per
+  // round; warp-private digit counters, no block barrier per round. The
+  // rank inside (warp, digit) is kept in shared memory.
   uint64_t c[kItems];
-  uint32_t rank[kItems];
-  // stable ranking inside the tile: element order = (round, warp, lane)
+  const uint32_t lt = lanemask_lt32();
 #pragma unroll
   for (int r = 0; r < kItems; ++r) {
-    for (int q = threadIdx.x; q < (kSortThreads / 32) * 256; q += kSortThreads)
-      (&wcnt[0][0])[q] = 0;
-    __syncthreads();
-    const int64_t i = t0 + r * kSortThreads + threadIdx.x;
-    const bool act = i < p.k;
-    uint32_t d = 0, rk = 0;
-    const uint32_t am = __ballot_sync(0xFFFFFFFFu, act);
-    c[r] = 0;
-    if (act) {
-      c[r] = src[i];
-      d = sdigit(c[r], pass);
-      const uint32_t peers = __match_any_sync(am, d);
-      rk = __popc(peers & lanemask_lt_s());
-      if (rk == 0) wcnt[warp][d] = __popc(peers);
-    }
-    __syncthreads();
-    for (int dd = threadIdx.x; dd < 256; dd += kSortThreads) {
-      uint32_t run = base[dd];
-      for (int q = 0; q < kSortThreads / 32; ++q) {
-        const uint32_t v = wcnt[q][dd];
-        wcnt[q][dd] = run;
-        run += v;
-      }
-      base[dd] = run;
-    }
-    __syncthreads();
-    rank[r] = act ? wcnt[warp][d] + rk : 0u;
-    __syncthreads();  // wcnt is cleared again by the next round
+    const int64_t i = w0 + r * 32 + lane;
+    c[r] = (i < p.k) ? src[i] : 0ull;
   }
+#pragma unroll
+  for (int r = 0; r < kItems; ++r) {
+    const int64_t i = w0 + r * 32 + lane;
+    const bool act = i < p.k;
+    const uint32_t am = __ballot_sync(0xFFFFFFFFu, act);
+    if (act) {
+      const uint32_t d = sdigit(c[r], pass);
+      const uint32_t peers = peers8(am, d);
+      const uint32_t before = wcnt[warp][d];
+      s_rank[warp * kPerWarp + r * 32 + lane] = static_cast<uint16_t>(before + __popc(peers & lt));
+      __syncwarp(am);
+      if ((peers & lt) == 0) wcnt[warp][d] = before + __popc(peers);
+    }
+    __syncwarp();
+  }
+  __syncthreads();
 
-  // decoupled look-back: thread d publishes this tile's count of digit d and
-  // adds the earlier tiles' counts
-  {
-    const int d = threadIdx.x;  // 256 threads = 256 digits
+  // per digit: exclusive offsets of the warps inside the tile, then the
+  // decoupled look-back over the earlier tiles (thread d handles digit d)
+  if (threadIdx.x < 256) {
+    const int d = threadIdx.x;
+    uint32_t cnt = 0;
+    for (int q = 0; q < kWarpsS; ++q) {
+      const uint32_t v = wcnt[q][d];
+      wcnt[q][d] = cnt;
+      cnt += v;
+    }
     uint64_t* st = p.status + (int64_t(pass) * p.ntiles) * 256;
-    const uint32_t cnt = base[d];
     uint32_t excl = 0;
     if (tile == 0) {
       st_relaxed(&st[d], kFlagIncl | cnt);
     } else {
       st_relaxed(&st[tile * 256 + d], kFlagAgg | cnt);
+      // windowed look-back: read kWin predecessors per round trip, add
+      // their counts back to the nearest inclusive prefix
+      constexpr int kWin = 8;
       int64_t t = tile - 1;
       uint32_t spins = 0;
-      while (t >= 0) {
-        const uint64_t v = ld_relaxed(&st[t * 256 + d]);
-        const uint64_t f = v & ~uint64_t(0xFFFFFFFFu);
-        if (f == 0) {
-          if (++spins > kLookbackSpin) {
-            atomicOr(&ctl->error, kErrTimeout);
-            break;
+      bool found = false;
+      while (t >= 0 && !found) {
+        uint64_t v[kWin];
+#pragma unroll
+        for (int j = 0; j < kWin; ++j)
+          v[j] = (t - j >= 0) ? ld_relaxed(&st[(t - j) * 256 + d]) : kFlagIncl;
+        int used = 0;
+        bool stall = false;
+#pragma unroll
+        for (int j = 0; j < kWin; ++j) {
+          if (!stall && !found) {
+            const uint64_t f = v[j] & ~uint64_t(0xFFFFFFFFu);
+            if (f == 0) {
+              stall = true;
+            } else {
+              excl += static_cast<uint32_t>(v[j]);
+              ++used;
+              if (f == kFlagIncl) found = true;
+            }
           }
-          continue;
         }
-        excl += static_cast<uint32_t>(v);
-        if (f == kFlagIncl) break;
-        --t;
+        t -= used;
+        if (stall && ++spins > kLookbackSpin) {
+          atomicOr(&ctl->error, kErrTimeout);
+          break;
+        }
       }
       st_relaxed(&st[tile * 256 + d], kFlagIncl | (excl + cnt));
     }
     s_off[d] = __ldcg(&ctl->sort_hist[pass][d]) + excl;
+    s_start[d] = cnt;
   }
   __syncthreads();
+  // tile-local start of each digit run (exclusive scan of the 256 counts)
+  {
+    const uint32_t v = threadIdx.x < 256 ? s_start[threadIdx.x] : 0u;
+    const uint32_t e = block_scan_excl<kSortThreads>(v, nullptr);
+    if (threadIdx.x < 256) s_start[threadIdx.x] = e;
+  }
+  __syncthreads();
+  // reorder the tile by digit in shared memory, then write each digit's run
+  // to consecutive global positions (coalesced)
 #pragma unroll
   for (int r = 0; r < kItems; ++r) {
-    const int64_t i = t0 + r * kSortThreads + threadIdx.x;
-    if (i < p.k) dst[s_off[sdigit(c[r], pass)] + rank[r]] = c[r];
+    const int64_t i = w0 + r * 32 + lane;
+    if (i < p.k) {
+      const uint32_t d = sdigit(c[r], pass);
+      s_el[s_start[d] + wcnt[warp][d] + s_rank[warp * kPerWarp + r * 32 + lane]] = c[r];
+    }
+  }
+  __syncthreads();
+  const int64_t tcount = imin64(kTile, p.k - tile * kTile);
+  for (int j = threadIdx.x; j < tcount; j += kSortThreads) {
+    const uint64_t e = s_el[j];
+    const uint32_t d = sdigit(e, pass);
+    dst[s_off[d] + (j - s_start[d])] = e;
   }
 }
 
 __global__ void finalize_kernel(SortParams p, int dtype, uint32_t* out_keys, int32_t* out_idx,
                                 uint32_t* out_kth) {
+  uint32_t skip[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) skip[q] = __ldcg(&p.ctl->sort_skip[q]);
   uint32_t par = 0;
-  for (int q = 0; q < 8; ++q) par ^= (__ldcg(&p.ctl->sort_skip[q]) == 0);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) par ^= (skip[q] == 0) ? 1u : 0u;
   const uint64_t* src = p.buf[par];
   for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < p.k;
        j += int64_t(gridDim.x) * blockDim.x)
@@ -254,10 +317,14 @@ cudaError_t launch_sort_output(const Work& w, void* out_keys, int32_t* out_idx, 
   p.ctl = w.ctl;
   cudaError_t e = cudaMemsetAsync(p.status, 0, sort_status_words(w.k) * 8, s);
   if (e != cudaSuccess) return e;
-  const int gh = static_cast<int>(std::min<int64_t>(p.ntiles, int64_t(sms) * 4));
-  sort_hist_all_kernel<<<gh, kSortThreads, 0, s>>>(p);
+  const int gh = static_cast<int>(std::min<int64_t>((w.k + kHistThreads * 16 - 1) / (kHistThreads * 16),
+                                                     int64_t(sms) * 2));
+  sort_hist_all_kernel<<<gh, kHistThreads, 0, s>>>(p);
+  const size_t dsm = static_cast<size_t>(kTile) * (8 + 2);
+  cudaFuncSetAttribute(sort_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       static_cast<int>(dsm));
   for (int pass = 0; pass < 8; ++pass)
-    sort_pass_kernel<<<static_cast<unsigned>(p.ntiles), kSortThreads, 0, s>>>(p, pass);
+    sort_pass_kernel<<<static_cast<unsigned>(p.ntiles), kSortThreads, dsm, s>>>(p, pass);
   const int g = static_cast<int>(std::min<int64_t>((w.k + 255) / 256, int64_t(sms) * 8));
   finalize_kernel<<<g, 256, 0, s>>>(p, w.dtype, static_cast<uint32_t*>(out_keys), out_idx,
                                     static_cast<uint32_t*>(out_kth));
