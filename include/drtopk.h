@@ -35,6 +35,14 @@
  *   - The library allocates its temporary workspace with the stream-ordered
  *     allocator (cudaMallocAsync / cudaFreeAsync on `stream`) and owns it;
  *     the caller owns every input and output buffer.
+ *   - drtopk_kth, drtopk_topk and drtopk_topk_ex (without statistics) keep a
+ *     cache of CUDA graphs of whole queries, keyed by every argument
+ *     (pointers, sizes, dtype, alpha, beta, device, stream): a repeated call
+ *     replays one graph instead of launching ~30 kernels. Each cached entry
+ *     owns a workspace; entries are evicted least-recently-used beyond 64
+ *     entries or DRTOPK_GRAPH_CACHE_BYTES (default 16 GiB) of workspace.
+ *     DRTOPK_GRAPH_CACHE=0 disables the cache. Calls made while profiling
+ *     (drtopk_profile_begin) launch kernel by kernel.
  *   - Calls return a drtopk_status and never abort. A CUDA error returns
  *     DRTOPK_ERR_CUDA; argument checks happen before any CUDA call.
  */

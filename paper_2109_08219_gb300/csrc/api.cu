@@ -2,6 +2,7 @@
 // workspace, stage orchestration on one stream, statistics and profiling.
 #include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -119,15 +120,18 @@ std::mutex g_prof_mu;
 bool g_prof_on = false;
 std::vector<StageRec> g_prof;
 
+bool profiling_on() {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  return g_prof_on;
+}
+
+// Records a pair of events around each stage on the launching stream.
 struct StageTimer {
   cudaStream_t s;
   bool on;
   cudaEvent_t a = nullptr;
   int stage = -1;
-  explicit StageTimer(cudaStream_t st) : s(st) {
-    std::lock_guard<std::mutex> lk(g_prof_mu);
-    on = g_prof_on;
-  }
+  StageTimer(cudaStream_t st, bool enabled) : s(st), on(enabled) {}
   void begin(int st) {
     if (!on) return;
     stage = st;
@@ -168,29 +172,8 @@ drtopk_status check_args(const void* keys, int dtype, int64_t n, int64_t k) {
     }                                            \
   } while (0)
 
-drtopk_status run_query(const void* keys, int dtype, int64_t n, int64_t k, int alpha, int beta,
-                        void* out_keys, int32_t* out_idx, void* out_kth, drtopk_stats* stats,
-                        cudaStream_t s) {
-  drtopk_status st = check_args(keys, dtype, n, k);
-  if (st != DRTOPK_OK) return st;
-  const bool topk = out_keys != nullptr || out_idx != nullptr;
-  if (!topk && !out_kth) return DRTOPK_ERR_INVALID;
-  if (alpha > 0 && (alpha < kMinAlpha || alpha > kMaxAlpha)) return DRTOPK_ERR_INVALID;
-  if (beta > kMaxBeta) return DRTOPK_ERR_INVALID;
-  Plan P;
-  if (!make_plan(n, k, alpha, beta, &P)) return DRTOPK_ERR_INVALID;
-  int sms = 0;
-  st = dev_info(&sms);
-  if (st != DRTOPK_OK) return st;
-
-  const Layout L = layout(P, k, topk, false);
-  char* ws = nullptr;
-  StageTimer tm(s);
-  Work w;
-  {
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ws), L.total, s);
-    if (e != cudaSuccess) return cuda_status(e);
-  }
+void bind_work(Work& w, char* ws, const Layout& L, const Plan& P, int64_t n, int64_t k,
+               int dtype) {
   w.ctl = reinterpret_cast<Ctl*>(ws + L.ctl);
   w.dkeys = reinterpret_cast<uint32_t*>(ws + L.dkeys);
   w.dsegs = reinterpret_cast<uint16_t*>(ws + L.dsegs);
@@ -211,34 +194,215 @@ drtopk_status run_query(const void* keys, int dtype, int64_t n, int64_t k, int a
   w.alpha = P.alpha;
   w.beta = P.beta;
   w.dtype = dtype;
+}
 
-  DRTOPK_CU(cudaMemsetAsync(w.ctl, 0, sizeof(Ctl), s));
+// Every launch of one query, in order, on stream s (no allocation, no sync).
+cudaError_t enqueue_query(const Work& w, const Plan& P, const void* keys, bool topk,
+                          void* out_keys, int32_t* out_idx, void* out_kth, int sms,
+                          cudaStream_t s, StageTimer& tm) {
+  cudaError_t e = cudaMemsetAsync(w.ctl, 0, sizeof(Ctl), s);
+  if (e != cudaSuccess) return e;
   tm.begin(0);
-  DRTOPK_CU(launch_delegates(w, keys, P.fuse_hist, sms, s));
+  e = launch_delegates(w, keys, P.fuse_hist, sms, s);
   note_launch();
   tm.end();
+  if (e != cudaSuccess) return e;
   if (P.fuse_hist) {
     tm.begin(1);
-    DRTOPK_CU(launch_threshold(w, sms, s));
+    e = launch_threshold(w, sms, s);
     tm.end();
+    if (e != cudaSuccess) return e;
   }
   tm.begin(2);
-  DRTOPK_CU(launch_filter(w, keys, !topk, sms, s));
+  e = launch_filter(w, keys, !topk, sms, s);
   tm.end();
+  if (e != cudaSuccess) return e;
   if (topk) {
     tm.begin(3);
-    DRTOPK_CU(launch_ties(w, keys, sms, s));
+    e = launch_ties(w, keys, sms, s);
     tm.end();
+    if (e != cudaSuccess) return e;
   }
   tm.begin(4);
-  DRTOPK_CU(launch_gselect(w, !topk, sms, s));
-  if (!topk) DRTOPK_CU(launch_write_kth(w, out_kth, s));
+  e = launch_gselect(w, !topk, sms, s);
+  if (e == cudaSuccess && !topk) e = launch_write_kth(w, out_kth, s);
   tm.end();
+  if (e != cudaSuccess) return e;
   if (topk) {
     tm.begin(5);
-    DRTOPK_CU(launch_sort_output(w, out_keys, out_idx, out_kth, sms, s));
+    e = launch_sort_output(w, out_keys, out_idx, out_kth, sms, s);
     tm.end();
   }
+  return e;
+}
+
+// ---------------------------------------------------------- graph cache ---
+// Repeated calls with identical arguments on the same stream replay a CUDA
+// graph of the whole query (one graph launch instead of ~30 kernel launches).
+// Each entry owns its workspace; entries are evicted least-recently-used
+// past kGraphMaxEntries or DRTOPK_GRAPH_CACHE_BYTES (default 16 GiB) of
+// workspace. DRTOPK_GRAPH_CACHE=0 disables the cache.
+struct GraphKey {
+  const void* keys;
+  void* out_keys;
+  void* out_idx;
+  void* out_kth;
+  int64_t n, k;
+  int dtype, alpha, beta, dev;
+  cudaStream_t s;
+  bool operator==(const GraphKey& o) const {
+    return keys == o.keys && out_keys == o.out_keys && out_idx == o.out_idx &&
+           out_kth == o.out_kth && n == o.n && k == o.k && dtype == o.dtype &&
+           alpha == o.alpha && beta == o.beta && dev == o.dev && s == o.s;
+  }
+};
+
+struct GraphEntry {
+  GraphKey key;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  char* ws = nullptr;
+  size_t bytes = 0;
+  cudaEvent_t done = nullptr;
+  uint64_t tick = 0;
+  uint64_t nlaunch = 0;
+};
+
+constexpr size_t kGraphMaxEntries = 64;
+std::mutex g_gmu;
+std::vector<GraphEntry> g_graphs;
+uint64_t g_gtick = 0;
+size_t g_gbytes = 0;
+cudaStream_t g_capture_stream[64];
+
+bool graph_cache_enabled() {
+  static const bool on = [] {
+    const char* v = std::getenv("DRTOPK_GRAPH_CACHE");
+    return !(v && v[0] == '0');
+  }();
+  return on;
+}
+
+size_t graph_cache_budget() {
+  static const size_t b = [] {
+    const char* v = std::getenv("DRTOPK_GRAPH_CACHE_BYTES");
+    return v ? static_cast<size_t>(std::strtoull(v, nullptr, 10)) : (size_t(16) << 30);
+  }();
+  return b;
+}
+
+void destroy_entry(GraphEntry& e) {
+  if (e.done) cudaEventSynchronize(e.done);
+  if (e.exec) cudaGraphExecDestroy(e.exec);
+  if (e.graph) cudaGraphDestroy(e.graph);
+  if (e.ws) cudaFree(e.ws);
+  if (e.done) cudaEventDestroy(e.done);
+  g_gbytes -= e.bytes;
+}
+
+// Builds an entry (capture + instantiate). Caller holds g_gmu.
+cudaError_t build_entry(GraphEntry& ent, const Plan& P, const Layout& L, const void* keys,
+                        int dtype, int64_t n, int64_t k, bool topk, void* out_keys,
+                        int32_t* out_idx, void* out_kth, int sms, int dev) {
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&ent.ws), L.total);
+  if (e != cudaSuccess) return e;
+  ent.bytes = L.total;
+  g_gbytes += L.total;
+  Work w;
+  bind_work(w, ent.ws, L, P, n, k, dtype);
+  if (!g_capture_stream[dev]) {
+    e = cudaStreamCreateWithFlags(&g_capture_stream[dev], cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+  }
+  cudaStream_t cs = g_capture_stream[dev];
+  StageTimer tm(cs, false);
+  const uint64_t before = drtopk_launch_count();
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  const cudaError_t ee = enqueue_query(w, P, keys, topk, out_keys, out_idx, out_kth, sms, cs, tm);
+  e = cudaStreamEndCapture(cs, &ent.graph);
+  ent.nlaunch = drtopk_launch_count() - before;
+  g_launches.fetch_sub(ent.nlaunch);  // counted again at every replay
+  if (ee != cudaSuccess) return ee;
+  if (e != cudaSuccess) return e;
+  e = cudaGraphInstantiate(&ent.exec, ent.graph, 0);
+  if (e != cudaSuccess) return e;
+  return cudaEventCreateWithFlags(&ent.done, cudaEventDisableTiming);
+}
+
+// Replays (building on a miss) the graph of this query. Returns false when
+// the graph path is not usable; the caller then runs the direct path.
+bool run_graph(const Plan& P, const void* keys, int dtype, int64_t n, int64_t k, bool topk,
+               void* out_keys, int32_t* out_idx, void* out_kth, int sms, cudaStream_t s,
+               drtopk_status* st) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+  GraphKey key{keys, out_keys, out_idx, out_kth, n, k, dtype, P.alpha, P.beta, dev, s};
+  std::lock_guard<std::mutex> lk(g_gmu);
+  GraphEntry* ent = nullptr;
+  for (auto& e : g_graphs)
+    if (e.key == key) ent = &e;
+  if (!ent) {
+    const Layout L = layout(P, k, topk, false);
+    if (L.total > graph_cache_budget()) return false;
+    while (!g_graphs.empty() &&
+           (g_graphs.size() >= kGraphMaxEntries || g_gbytes + L.total > graph_cache_budget())) {
+      size_t v = 0;
+      for (size_t i = 1; i < g_graphs.size(); ++i)
+        if (g_graphs[i].tick < g_graphs[v].tick) v = i;
+      destroy_entry(g_graphs[v]);
+      g_graphs.erase(g_graphs.begin() + v);
+    }
+    GraphEntry fresh;
+    fresh.key = key;
+    if (build_entry(fresh, P, L, keys, dtype, n, k, topk, out_keys, out_idx, out_kth, sms, dev) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      destroy_entry(fresh);
+      return false;
+    }
+    g_graphs.push_back(fresh);
+    ent = &g_graphs.back();
+  }
+  ent->tick = ++g_gtick;
+  cudaError_t e = cudaGraphLaunch(ent->exec, s);
+  if (e == cudaSuccess) e = cudaEventRecord(ent->done, s);
+  if (e == cudaSuccess) note_launch(static_cast<int>(ent->nlaunch));
+  *st = cuda_status(e);
+  return true;
+}
+
+drtopk_status run_query(const void* keys, int dtype, int64_t n, int64_t k, int alpha, int beta,
+                        void* out_keys, int32_t* out_idx, void* out_kth, drtopk_stats* stats,
+                        cudaStream_t s, bool allow_graph) {
+  drtopk_status st = check_args(keys, dtype, n, k);
+  if (st != DRTOPK_OK) return st;
+  const bool topk = out_keys != nullptr || out_idx != nullptr;
+  if (!topk && !out_kth) return DRTOPK_ERR_INVALID;
+  if (alpha > 0 && (alpha < kMinAlpha || alpha > kMaxAlpha)) return DRTOPK_ERR_INVALID;
+  if (beta > kMaxBeta) return DRTOPK_ERR_INVALID;
+  Plan P;
+  if (!make_plan(n, k, alpha, beta, &P)) return DRTOPK_ERR_INVALID;
+  int sms = 0;
+  st = dev_info(&sms);
+  if (st != DRTOPK_OK) return st;
+  const bool prof = profiling_on();
+
+  // profiled calls run the direct path: its stage events sit between launches
+  if (allow_graph && !stats && !prof && graph_cache_enabled() &&
+      run_graph(P, keys, dtype, n, k, topk, out_keys, out_idx, out_kth, sms, s, &st))
+    return st;
+
+  const Layout L = layout(P, k, topk, false);
+  char* ws = nullptr;
+  StageTimer tm(s, prof);
+  Work w;
+  {
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ws), L.total, s);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  bind_work(w, ws, L, P, n, k, dtype);
+  DRTOPK_CU(enqueue_query(w, P, keys, topk, out_keys, out_idx, out_kth, sms, s, tm));
   if (stats) {
     Ctl c;
     DRTOPK_CU(cudaMemcpyAsync(&c, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
@@ -303,14 +467,14 @@ drtopk_status drtopk_kth(const void* keys, drtopk_dtype dtype, int64_t n, int64_
                          void* out_kth, void* stream) {
   if (!out_kth) return DRTOPK_ERR_INVALID;
   return run_query(keys, dtype, n, k, 0, 0, nullptr, nullptr, out_kth, nullptr,
-                   static_cast<cudaStream_t>(stream));
+                   static_cast<cudaStream_t>(stream), true);
 }
 
 drtopk_status drtopk_topk(const void* keys, drtopk_dtype dtype, int64_t n, int64_t k,
                           void* out_keys, int32_t* out_idx, void* stream) {
   if (!out_keys || !out_idx) return DRTOPK_ERR_INVALID;
   return run_query(keys, dtype, n, k, 0, 0, out_keys, out_idx, nullptr, nullptr,
-                   static_cast<cudaStream_t>(stream));
+                   static_cast<cudaStream_t>(stream), true);
 }
 
 drtopk_status drtopk_topk_ex(const void* keys, drtopk_dtype dtype, int64_t n, int64_t k,
@@ -319,7 +483,7 @@ drtopk_status drtopk_topk_ex(const void* keys, drtopk_dtype dtype, int64_t n, in
   if ((out_keys == nullptr) != (out_idx == nullptr)) return DRTOPK_ERR_INVALID;
   if (alpha < 0 || beta < 0) return DRTOPK_ERR_INVALID;
   return run_query(keys, dtype, n, k, alpha, beta, out_keys, out_idx, out_kth, stats,
-                   static_cast<cudaStream_t>(stream));
+                   static_cast<cudaStream_t>(stream), true);
 }
 
 drtopk_status drtopk_delegates(const void* keys, drtopk_dtype dtype, int64_t n, int alpha,
@@ -376,7 +540,7 @@ drtopk_status drtopk_topk_host(const void* keys, drtopk_dtype dtype, int64_t n, 
   e = cudaMemcpyAsync(d, keys, static_cast<size_t>(n) * 4, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) {
     st = run_query(d, dtype, n, k, 0, 0, d + kb, reinterpret_cast<int32_t*>(d + kb + ob), nullptr,
-                   nullptr, s);
+                   nullptr, s, false);
     if (st == DRTOPK_OK) {
       e = cudaMemcpyAsync(out_keys, d + kb, static_cast<size_t>(k) * 4, cudaMemcpyDeviceToHost, s);
       if (e == cudaSuccess)
