@@ -182,6 +182,97 @@ drtopk_status drtopk_topk_host(const void* keys, drtopk_dtype dtype,
                                int64_t n, int64_t k, void* out_keys,
                                int32_t* out_idx, void* stream);
 
+/*
+ * ---------------------------------------------------------------- batched --
+ * Many independent top-k queries over rows of one concatenated array, all
+ * in ONE persistent kernel launch (the paper applies the method to one
+ * vector per call; the batched form runs the same steps per row: delegate
+ * pass Sec. 3.1/3.3, threshold Rule 2 Sec. 3.2, filter Rules 2-3, second
+ * top-k Sec. 4.1, with the k-th key and ties as in drtopk_topk). One CTA
+ * takes one row at a time, largest rows first; every intermediate (the
+ * delegate vector, the candidates up to 4096) stays in shared memory.
+ *
+ * Rows: row r is keys[row_off[r] .. row_off[r+1]) (row_off: rows+1 int64,
+ * row_off[0] >= 0), with 1 <= length <= 2^24 and k_r = ks[r] (int32) in
+ * [1, min(length, 4096)]. row_off and ks may be host or device pointers
+ * (a device array is copied to the host to plan the launch: synchronous). The outputs of row r
+ * are out_keys / out_idx[o_r .. o_r + k_r) with o_r = k_0 + ... + k_{r-1}
+ * (packed in row order), sorted by (key descending, index ascending); an
+ * index is the position within the row. keys (device) must be 16-byte
+ * aligned; rows may start at any element.
+ *
+ * Per-row parameters: rows of at most 4096 keys are selected directly (no
+ * delegates). Longer rows take (alpha, beta) from the tuning table entry of
+ * (floor(log2 n_r), floor(log2 k_r)) when one is set (drtopk_tune_set,
+ * drtopk_autotune_batched), else alpha by Rule 4 / Eq. 9 and beta = 2,
+ * lowered while fewer than 2k_r delegates would exist; alpha is then raised
+ * to at least 5 and until beta * ceil(n_r / 2^alpha) <= 8192 (the delegates
+ * fit on chip).
+ */
+typedef struct drtopk_batch_plan drtopk_batch_plan;
+
+/*
+ * Builds a reusable plan for a fixed row layout: per-row parameters, the
+ * processing order and a device scratch for candidates that exceed shared
+ * memory (sized by the bound |{x > tau}| < floor((k-1)/beta) 2^alpha + k of
+ * every row). alpha / beta > 0 force the parameters of every row longer
+ * than 4096 keys (alpha in [5, 16], beta in [1, 4]; the on-chip clamp still
+ * applies); 0 picks them as described above. Allocates device memory;
+ * synchronous. *out receives the plan (release with
+ * drtopk_batch_plan_destroy).
+ */
+drtopk_status drtopk_batch_plan_create(drtopk_dtype dtype, const int64_t* row_off,
+                                       const int32_t* ks, int32_t rows, int alpha,
+                                       int beta, drtopk_batch_plan** out);
+
+/*
+ * Runs the plan on `stream`: one memset and one kernel launch, no host
+ * synchronization and no allocation, so the call may be captured in a CUDA
+ * graph. keys: device, at least row_off[rows] elements; out_keys / out_idx:
+ * device, sum(ks) entries each. Device-side errors are read by
+ * drtopk_batch_plan_status. Calls that share a plan must be ordered.
+ */
+drtopk_status drtopk_batch_plan_run(drtopk_batch_plan* plan, const void* keys,
+                                    void* out_keys, int32_t* out_idx, void* stream);
+
+/* Synchronizes `stream` and returns the device error status of the last
+ * run of the plan (DRTOPK_ERR_TIMEOUT when a bounded wait gave up). */
+drtopk_status drtopk_batch_plan_status(drtopk_batch_plan* plan, void* stream);
+
+/* (alpha, beta) the plan uses for each row, in row order (HOST arrays of
+ * `rows` entries; alpha 0 marks a direct select). */
+drtopk_status drtopk_batch_plan_params(const drtopk_batch_plan* plan, int32_t* alpha,
+                                       int32_t* beta);
+
+/* Synchronizes the device and frees the plan. */
+drtopk_status drtopk_batch_plan_destroy(drtopk_batch_plan* plan);
+
+/* One-shot batched top-k: plan, run, status, destroy. Synchronous. */
+drtopk_status drtopk_topk_batched(const void* keys, drtopk_dtype dtype,
+                                  const int64_t* row_off, const int32_t* ks,
+                                  int32_t rows, void* out_keys, int32_t* out_idx,
+                                  void* stream);
+
+/*
+ * The per-shape tuning table of the batched path (process-wide), indexed by
+ * log2n in [10, 31] and log2k in [0, 12]. alpha = 0 (the initial state)
+ * means Rule 4; set alpha in [5, 16], beta in [1, 4]. Host only.
+ */
+drtopk_status drtopk_tune_get(int32_t log2n, int32_t log2k, int* alpha, int* beta);
+drtopk_status drtopk_tune_set(int32_t log2n, int32_t log2k, int alpha, int beta);
+
+/*
+ * Autotuner (Sec. 4.2 picks alpha by a model; this measures instead): for
+ * every log2n in [min_log2n, max_log2n] (10..24) and every power-of-two k
+ * up to min(4096, n / 2), times the batched kernel on rows_per_shape rows of
+ * 2^log2n hashed keys for alpha in [Rule 4 - 3, Rule 4 + 2] (within [5, 16])
+ * and beta in {1, 2, 3, 4}, and stores the fastest pair in the table.
+ * Allocates 2^max_log2n * rows_per_shape keys; synchronous.
+ */
+drtopk_status drtopk_autotune_batched(drtopk_dtype dtype, int32_t min_log2n,
+                                      int32_t max_log2n, int32_t rows_per_shape,
+                                      void* stream);
+
 /* Stage timing (CUDA events recorded on the launching stream around each
  * stage while profiling is on). Stages: 0 delegate pass, 1 threshold
  * select, 2 filter, 3 tie ranking, 4 second top-k, 5 output sort. */

@@ -81,9 +81,24 @@ def lib():
         L.drtopk_profile_end.argtypes = [ctypes.POINTER(Profile)]
         L.drtopk_launch_count.argtypes = []
         L.drtopk_launch_count.restype = ctypes.c_uint64
+        pi32 = ctypes.POINTER(ctypes.c_int32)
+        pi64 = ctypes.POINTER(ctypes.c_int64)
+        L.drtopk_batch_plan_create.argtypes = [i32, pi64, pi32, i32, i32, i32,
+                                               ctypes.POINTER(p)]
+        L.drtopk_batch_plan_run.argtypes = [p, p, p, p, p]
+        L.drtopk_batch_plan_status.argtypes = [p, p]
+        L.drtopk_batch_plan_params.argtypes = [p, pi32, pi32]
+        L.drtopk_batch_plan_destroy.argtypes = [p]
+        L.drtopk_topk_batched.argtypes = [p, i32, pi64, pi32, i32, p, p, p]
+        L.drtopk_tune_get.argtypes = [i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+        L.drtopk_tune_set.argtypes = [i32, i32, i32, i32]
+        L.drtopk_autotune_batched.argtypes = [i32, i32, i32, i32, p]
         for fn in ("drtopk_plan", "drtopk_kth", "drtopk_topk", "drtopk_topk_ex",
                    "drtopk_delegates", "drtopk_topk_host", "drtopk_profile_begin",
-                   "drtopk_profile_end"):
+                   "drtopk_profile_end", "drtopk_batch_plan_create", "drtopk_batch_plan_run",
+                   "drtopk_batch_plan_status", "drtopk_batch_plan_params",
+                   "drtopk_batch_plan_destroy", "drtopk_topk_batched", "drtopk_tune_get",
+                   "drtopk_tune_set", "drtopk_autotune_batched"):
             getattr(L, fn).restype = i32
         _lib = L
     return _lib
@@ -251,3 +266,109 @@ def profile_end():
 
 def launch_count():
     return int(lib().drtopk_launch_count())
+
+
+# ------------------------------------------------------------------ batched --
+def _rows_arrays(row_off, ks):
+    import numpy as np
+    off = np.ascontiguousarray(np.asarray(row_off, dtype=np.int64))
+    kk = np.ascontiguousarray(np.asarray(ks, dtype=np.int32))
+    if off.ndim != 1 or kk.ndim != 1 or off.size != kk.size + 1:
+        raise ValueError("row_off needs rows + 1 entries and ks rows entries")
+    return off, kk
+
+
+class BatchPlan:
+    """A reusable plan of the batched top-k for a fixed row layout
+    (drtopk_batch_plan_*). ``row_off`` (rows + 1 offsets) and ``ks`` are host
+    sequences; ``run`` launches one kernel and may be graph-captured."""
+
+    def __init__(self, row_off, ks, dtype, alpha=0, beta=0):
+        import numpy as np
+        self.row_off, self.ks = _rows_arrays(row_off, ks)
+        if dtype not in _NAMES:
+            raise ValueError("dtype must be one of u32, i32, f32")
+        self.dtype = dtype
+        self.rows = int(self.ks.size)
+        self.out_off = np.concatenate([[0], np.cumsum(self.ks, dtype=np.int64)])
+        self._h = ctypes.c_void_p()
+        _check(lib().drtopk_batch_plan_create(
+            _NAMES[dtype], self.row_off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+            self.ks.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), self.rows, alpha, beta,
+            ctypes.byref(self._h)), "drtopk_batch_plan_create")
+
+    @property
+    def total_k(self):
+        return int(self.out_off[-1])
+
+    def params(self):
+        import numpy as np
+        a = np.zeros(self.rows, np.int32)
+        b = np.zeros(self.rows, np.int32)
+        _check(lib().drtopk_batch_plan_params(
+            self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+            b.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))), "drtopk_batch_plan_params")
+        return a, b
+
+    def run(self, keys, out_keys=None, out_idx=None, stream=None):
+        import torch
+        if out_keys is None:
+            out_keys = torch.empty(self.total_k, dtype=keys.dtype, device=keys.device)
+        if out_idx is None:
+            out_idx = torch.empty(self.total_k, dtype=torch.int32, device=keys.device)
+        if keys.numel() < int(self.row_off[-1]) or out_keys.numel() < self.total_k \
+                or out_idx.numel() < self.total_k:
+            raise ValueError("buffers smaller than the plan's rows")
+        _check(lib().drtopk_batch_plan_run(self._h, _dev(keys), _dev(out_keys), _dev(out_idx),
+                                           _stream(stream)), "drtopk_batch_plan_run")
+        return out_keys, out_idx
+
+    def status(self, stream=None):
+        _check(lib().drtopk_batch_plan_status(self._h, _stream(stream)),
+               "drtopk_batch_plan_status")
+
+    def close(self):
+        if self._h:
+            lib().drtopk_batch_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def drtopk_topk_batched(keys, row_off, ks, dtype=None, stream=None):
+    """One-shot batched top-k (synchronous). Returns (out_keys, out_idx),
+    packed by row: row r owns entries [sum(ks[:r]), sum(ks[:r+1]))."""
+    import torch
+    off, kk = _rows_arrays(row_off, ks)
+    code = _dtype_code(keys, dtype)
+    total = int(kk.sum(dtype="int64"))
+    out_keys = torch.empty(total, dtype=keys.dtype, device=keys.device)
+    out_idx = torch.empty(total, dtype=torch.int32, device=keys.device)
+    if keys.numel() < int(off[-1]):
+        raise ValueError("keys shorter than row_off[-1]")
+    _check(lib().drtopk_topk_batched(
+        _dev(keys), code, off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+        kk.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), int(kk.size), _dev(out_keys),
+        _dev(out_idx), _stream(stream)), "drtopk_topk_batched")
+    return out_keys, out_idx
+
+
+def tune_get(log2n, log2k):
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check(lib().drtopk_tune_get(log2n, log2k, ctypes.byref(a), ctypes.byref(b)),
+           "drtopk_tune_get")
+    return a.value, b.value
+
+
+def tune_set(log2n, log2k, alpha, beta):
+    _check(lib().drtopk_tune_set(log2n, log2k, alpha, beta), "drtopk_tune_set")
+
+
+def autotune_batched(dtype, min_log2n, max_log2n, rows_per_shape=152, stream=None):
+    """Measures (alpha, beta) per shape bucket and fills the tuning table."""
+    _check(lib().drtopk_autotune_batched(_NAMES[dtype], min_log2n, max_log2n, rows_per_shape,
+                                         _stream(stream)), "drtopk_autotune_batched")

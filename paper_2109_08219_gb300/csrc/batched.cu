@@ -1,0 +1,1002 @@
+// Batched ragged top-k: many independent (row, k_r) queries in ONE
+// persistent launch. Each CTA takes rows from an atomic counter (largest
+// first) and runs the whole delegate-centric method on a row on-chip:
+//   1. delegate pass (Rule 1 Sec. 3.1, Rule 3 Sec. 3.3): the row streams
+//      through a 4-stage ring of 32 KB TMA bulk copies; every thread keeps
+//      the top-beta of 32 keys by value; (key, segment) lists are merged
+//      per subrange; the delegate vector D stays in shared memory;
+//   2. threshold (Rule 2 Sec. 3.2): MSD radix select of the k-th delegate
+//      over D in shared memory;
+//   3. filter (Rules 2-3): subranges whose beta delegates all exceed tau
+//      are read again, the others give their delegates > tau; candidates
+//      G = {x > tau} go to shared memory, spilling to a per-CTA scratch;
+//   4. second top-k: MSD radix select over the (key, ~index) composites of
+//      G, or, when |G| < k, G plus the smallest-index ties at tau;
+//   5. the k_r winners are bitonic-sorted in shared memory.
+// Rows start at any 4-byte offset: each chunk is copied from the 16-byte
+// boundary below it and read at a shift, with rotated scalar reads (no
+// bank conflicts). Row sizes up to 4096 keys skip the delegates (direct
+// select). Indices in the output are positions within the row.
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+#include "delegate_core.cuh"
+#include "launch.h"
+
+namespace drtopk {
+
+struct RowDesc {
+  int64_t start;   // first key (element offset in the concatenated keys)
+  int64_t out;     // first output slot
+  int32_t n;
+  int32_t k;
+  int32_t alpha;   // 0: direct select (no delegates)
+  int32_t beta;
+};
+
+namespace {
+
+constexpr int kBT = 256;              // threads per CTA
+constexpr int kBChunk = 8192;         // keys per ring stage (32 KB)
+constexpr int kBStages = 4;
+constexpr int kBStageBytes = kBChunk * 4 + 128;  // + room for the alignment shift
+constexpr int kBDMax = 8192;          // delegate slots (S * beta) kept on chip
+constexpr int kBGS = 4096;            // candidates kept on chip
+constexpr int kBMaxK = 4096;          // largest k_r of the batched path
+constexpr int kBDirect = 4096;        // rows up to this size: direct select
+constexpr int64_t kBMaxN = int64_t(1) << 24;  // longest row of the batched path
+
+constexpr size_t kRingBytes = size_t(kBStages) * kBStageBytes;
+constexpr size_t kDynSmem = kRingBytes + size_t(kBDMax) * 4 + size_t(kBDMax) * 2 + size_t(kBGS) * 8;
+
+struct BatchParams {
+  const uint32_t* keys;
+  int64_t total;          // keys in the concatenated array
+  const RowDesc* rows;    // processing order (largest first)
+  int32_t nrows;
+  uint32_t* row_ctr;      // zeroed by the host before the launch
+  uint64_t* scratch;      // per-CTA candidate spill, scap entries each
+  int64_t scap;
+  uint32_t* out_keys;
+  int32_t* out_idx;
+  uint32_t* err;
+};
+
+struct Smem {
+  unsigned char* ring;
+  uint32_t* dkeys;
+  uint16_t* dsegs;
+  uint64_t* gbuf;
+};
+
+__device__ __forceinline__ uint32_t lanemask_lt_b() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// ------------------------------------------------------------ chunk ring ---
+struct Ring {
+  uint64_t* bar;      // kBStages mbarriers
+  uint64_t seq;       // chunks issued by this CTA so far (all rows)
+  uint64_t pol;
+};
+
+// Issues chunk c of the row into a stage buffer: one bulk copy from the
+// 16-byte boundary at or below its first key (the chunk is then read at a
+// shift of ((start + c * kBChunk) mod 4) keys). Thread 0 only.
+__device__ __forceinline__ void issue_row_chunk(const BatchParams& p, const RowDesc& r, int64_t c,
+                                                unsigned char* buf, uint64_t* bar, uint64_t pol) {
+  const int64_t e0 = r.start + c * kBChunk;                       // first key
+  const int64_t e1 = r.start + imin64(int64_t(r.n), (c + 1) * kBChunk);  // one past
+  const int64_t b0 = e0 * 4, b1 = e1 * 4;
+  const int64_t a0 = b0 & ~int64_t(15);
+  const int64_t tot16 = (p.total * 4) & ~int64_t(15);
+  const int64_t a1 = imin64((b1 + 15) & ~int64_t(15), tot16);
+  uint32_t* dst = reinterpret_cast<uint32_t*>(buf);
+  // keys past the last 16-byte boundary of the array (only at its very
+  // end) are not covered by the bulk copy: plain loads
+  const int64_t tma_end = a1 / 4;
+  for (int64_t e = (tma_end > e0 ? tma_end : e0); e < e1; ++e) dst[e - a0 / 4] = p.keys[e];
+  const int64_t bytes = a1 - a0;
+  if (bytes > 0) {
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(bar, static_cast<uint32_t>(bytes));
+    tma_load_1d(buf, reinterpret_cast<const unsigned char*>(p.keys) + a0,
+                static_cast<uint32_t>(bytes), bar, pol);
+  } else {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+  }
+}
+
+// ---------------------------------------------------- block radix select ---
+// k-th largest (1-based rank krem) of the 32-bit keys a[0..cnt) in shared
+// memory (delegates). Returns the key.
+__device__ uint32_t block_select32(const uint32_t* a, int cnt, uint32_t krem, uint32_t* hist,
+                                   uint32_t* s_bc) {
+  uint32_t prefix = 0;
+  for (int pass = 0; pass < 4; ++pass) {
+    for (int i = threadIdx.x; i < 256; i += kBT) hist[i] = 0;
+    __syncthreads();
+    const uint32_t mask = pass == 0 ? 0u : (0xFFFFFFFFu << (32 - 8 * pass));
+    const int sh = 24 - 8 * pass;
+    for (int i = threadIdx.x; i < cnt; i += kBT) {
+      const uint32_t x = a[i];
+      if ((x & mask) == (prefix & mask)) atomicAdd(&hist[(x >> sh) & 255u], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t acc = 0;
+      int d = 255;
+      for (; d > 0; --d) {
+        if (acc + hist[d] >= krem) break;
+        acc += hist[d];
+      }
+      s_bc[0] = static_cast<uint32_t>(d);
+      s_bc[1] = krem - acc;
+    }
+    __syncthreads();
+    prefix |= s_bc[0] << sh;
+    krem = s_bc[1];
+    __syncthreads();
+  }
+  return prefix;
+}
+
+// Logical candidate array: [0, kBGS) in shared memory, then the CTA's
+// scratch.
+__device__ __forceinline__ uint64_t g_get(const Smem& sm, const uint64_t* scr, uint32_t i) {
+  return i < kBGS ? sm.gbuf[i] : scr[i - kBGS];
+}
+__device__ __forceinline__ void g_put(const Smem& sm, uint64_t* scr, int64_t scap, uint32_t i,
+                                      uint64_t v, uint32_t* err) {
+  if (i < kBGS) sm.gbuf[i] = v;
+  else if (int64_t(i - kBGS) < scap) scr[i - kBGS] = v;
+  else atomicOr(err, kErrOverflowG);
+}
+
+// Warp-aggregated append of one optional item per lane to the logical G.
+__device__ __forceinline__ void g_append(const Smem& sm, uint64_t* scr, int64_t scap,
+                                         uint32_t* s_gcnt, bool has, uint64_t v, uint32_t* err) {
+  const uint32_t bal = __ballot_sync(0xFFFFFFFFu, has);
+  if (!bal) return;
+  uint32_t base = 0;
+  const uint32_t lane = lane_id();
+  if (lane == static_cast<uint32_t>(__ffs(bal) - 1)) base = atomicAdd(s_gcnt, __popc(bal));
+  base = __shfl_sync(0xFFFFFFFFu, base, __ffs(bal) - 1);
+  if (has) g_put(sm, scr, scap, base + __popc(bal & lanemask_lt_b()), v, err);
+}
+
+// k-th largest composite of the logical G (cnt entries): returns the
+// threshold T such that exactly k composites are >= T.
+__device__ uint64_t block_select64(const Smem& sm, const uint64_t* scr, uint32_t cnt, uint32_t k,
+                                   uint32_t* hist, uint32_t* s_bc) {
+  uint64_t prefix = 0;
+  uint32_t krem = k;
+  for (int pass = 0; pass < 8; ++pass) {
+    for (int i = threadIdx.x; i < 256; i += kBT) hist[i] = 0;
+    __syncthreads();
+    const uint64_t mask = pass == 0 ? 0ull : (~0ull << (64 - 8 * pass));
+    const int sh = 56 - 8 * pass;
+    for (uint32_t i = threadIdx.x; i < cnt; i += kBT) {
+      const uint64_t x = g_get(sm, scr, i);
+      if ((x & mask) == (prefix & mask)) atomicAdd(&hist[static_cast<uint32_t>(x >> sh) & 255u], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t acc = 0;
+      int d = 255;
+      for (; d > 0; --d) {
+        if (acc + hist[d] >= krem) break;
+        acc += hist[d];
+      }
+      s_bc[0] = static_cast<uint32_t>(d);
+      s_bc[1] = krem - acc;
+      s_bc[2] = hist[d];
+    }
+    __syncthreads();
+    prefix |= static_cast<uint64_t>(s_bc[0]) << sh;
+    krem = s_bc[1];
+    const bool done = s_bc[2] == krem;  // the whole bucket is needed
+    __syncthreads();
+    if (done) break;
+  }
+  return prefix;
+}
+
+// Bitonic sort (descending) of w[0..k) in shared memory, k <= kBMaxK.
+__device__ void block_sort_desc(uint64_t* w, int k) {
+  int P = 1;
+  while (P < k) P <<= 1;
+  for (int i = k + threadIdx.x; i < P; i += kBT) w[i] = 0ull;
+  __syncthreads();
+  for (int size = 2; size <= P; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = threadIdx.x; i < P; i += kBT) {
+        const int j = i ^ stride;
+        if (j > i) {
+          const bool desc = (i & size) == 0;
+          const uint64_t a = w[i], b = w[j];
+          if ((a < b) == desc) {
+            w[i] = b;
+            w[j] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ------------------------------------------------------------ one row ----
+template <int DT, int B>
+__device__ void process_row(const BatchParams& p, const RowDesc& r, const Smem& sm, Ring& ring,
+                            uint32_t* hist, uint32_t* s_bc, uint32_t* s_cnt, uint64_t* s_lists) {
+  constexpr int P = Pow2<B>::v;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
+  const int64_t n = r.n;
+  const uint32_t k = static_cast<uint32_t>(r.k);
+  const int alpha = r.alpha;
+  uint64_t* scr = p.scratch + static_cast<int64_t>(blockIdx.x) * p.scap;
+  const uint32_t* rk = p.keys + r.start;  // row keys
+
+  if (tid == 0) {
+    s_cnt[0] = 0;  // |G|
+    s_cnt[1] = 0;  // scan list length
+    s_cnt[2] = 0;  // winners
+  }
+  // the previous row wrote the ring with generic stores; the bulk copies of
+  // this row write it through the async proxy
+  fence_proxy_async_smem();
+  __syncthreads();
+
+  int64_t S = 0;
+  uint32_t tau = 0;
+  bool direct = (alpha == 0);
+  if (direct) {
+    // small row: every key is a candidate
+    for (int64_t i = tid; i < n; i += kBT)
+      g_put(sm, scr, p.scap, static_cast<uint32_t>(i), make_comp(map_key<DT>(rk[i]), uint32_t(i)),
+            p.err);
+    if (tid == 0) s_cnt[0] = static_cast<uint32_t>(n);
+    __syncthreads();
+  } else {
+    // ---------------------------------------------- 1. delegate pass ----
+    S = (n + (int64_t(1) << alpha) - 1) >> alpha;
+    const int64_t nch = (n + kBChunk - 1) / kBChunk;
+    const int cps_log = alpha > 13 ? alpha - 13 : 0;
+    const uint64_t seq0 = ring.seq;
+    if (tid == 0) {
+      for (int64_t c = 0; c < kBStages && c < nch; ++c) {
+        const uint64_t q = seq0 + c;
+        issue_row_chunk(p, r, c, sm.ring + (q % kBStages) * kBStageBytes, &ring.bar[q % kBStages],
+                        ring.pol);
+      }
+    }
+    uint64_t run[P];
+#pragma unroll
+    for (int i = 0; i < P; ++i) run[i] = 0;
+    for (int64_t c = 0; c < nch; ++c) {
+      const uint64_t q = seq0 + c;
+      const int stage = static_cast<int>(q % kBStages);
+      const bool ok = mbar_wait_bounded(&ring.bar[stage], static_cast<uint32_t>((q / kBStages) & 1));
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) {
+          atomicOr(p.err, kErrTimeout);
+          // let the copies still in flight land (bounded) before leaving
+          for (int64_t c2 = c; c2 < nch && c2 < c + kBStages; ++c2) {
+            const uint64_t q2 = seq0 + c2;
+            mbar_wait_bounded(&ring.bar[q2 % kBStages], static_cast<uint32_t>((q2 / kBStages) & 1));
+          }
+        }
+        __syncthreads();
+        return;
+      }
+      const uint32_t* cb = reinterpret_cast<const uint32_t*>(sm.ring + stage * kBStageBytes);
+      const int shift = static_cast<int>(((r.start + c * kBChunk) * 4 & 15) / 4);
+      const int64_t seg_start = c * kBChunk + int64_t(tid) * 32;  // row-relative
+      const int64_t valid = n - seg_start;
+      uint32_t m[B];
+#pragma unroll
+      for (int i = 0; i < B; ++i) m[i] = 0;
+      int cntv;
+      if (valid >= 32) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) insert1<DT, B>(m, cb[shift + tid * 32 + ((j + lane) & 31)]);
+        cntv = 32;
+      } else {
+        cntv = 0;
+        for (int j = 0; j < 32; ++j) {
+          if (j < valid) {
+            insert1<DT, B>(m, cb[shift + tid * 32 + j]);
+            ++cntv;
+          }
+        }
+      }
+      const int64_t sub = seg_start >> alpha;
+      const uint32_t seg = static_cast<uint32_t>((seg_start - (sub << alpha)) >> 5);
+      uint64_t a[P];
+#pragma unroll
+      for (int i = 0; i < P; ++i) a[i] = (i < B && i < cntv) ? make_dc(m[i < B ? i : 0], seg) : 0ull;
+      if (alpha <= 13) {
+        const int g_log = alpha - 5;
+        const int wl = g_log < 5 ? g_log : 5;
+        for (int l = 0; l < wl; ++l) shfl_merge<P>(a, 1 << l);
+        if (g_log <= 5) {
+          if ((lane & ((1 << g_log) - 1)) == 0 && sub < S) {
+#pragma unroll
+            for (int j = 0; j < B; ++j) {
+              sm.dkeys[sub * B + j] = dc_key(a[j]);
+              sm.dsegs[sub * B + j] = static_cast<uint16_t>(a[j] == 0 ? kNoSeg : dc_seg(a[j]));
+            }
+          }
+        } else {
+          if (lane == 0) {
+#pragma unroll
+            for (int i = 0; i < P; ++i) s_lists[warp * P + i] = a[i];
+          }
+          __syncthreads();
+          const int wps_log = g_log - 5;
+          const int nsub_chunk = (kBT / 32) >> wps_log;
+          if (warp < nsub_chunk) {
+            uint64_t b[P];
+            const int src = warp * (1 << wps_log) + (lane & ((1 << wps_log) - 1));
+#pragma unroll
+            for (int i = 0; i < P; ++i) b[i] = s_lists[src * P + i];
+            for (int l = 0; l < wps_log; ++l) shfl_merge<P>(b, 1 << l);
+            const int64_t sub2 = ((c * kBChunk) >> alpha) + warp;
+            if (lane == 0 && sub2 < S) {
+#pragma unroll
+              for (int j = 0; j < B; ++j) {
+                sm.dkeys[sub2 * B + j] = dc_key(b[j]);
+                sm.dsegs[sub2 * B + j] = static_cast<uint16_t>(b[j] == 0 ? kNoSeg : dc_seg(b[j]));
+              }
+            }
+          }
+        }
+      } else {
+        merge_desc<P>(run, a);
+        const int64_t cps = int64_t(1) << cps_log;
+        if (((c & (cps - 1)) == cps - 1) || (c == nch - 1)) {
+          for (int l = 0; l < 5; ++l) shfl_merge<P>(run, 1 << l);
+          if (lane == 0) {
+#pragma unroll
+            for (int i = 0; i < P; ++i) s_lists[warp * P + i] = run[i];
+          }
+          __syncthreads();
+          if (warp == 0) {
+            uint64_t b[P];
+#pragma unroll
+            for (int i = 0; i < P; ++i) b[i] = s_lists[(lane & 7) * P + i];
+            for (int l = 0; l < 3; ++l) shfl_merge<P>(b, 1 << l);
+            const int64_t sub3 = c >> cps_log;
+            if (lane == 0) {
+#pragma unroll
+              for (int j = 0; j < B; ++j) {
+                sm.dkeys[sub3 * B + j] = dc_key(b[j]);
+                sm.dsegs[sub3 * B + j] = static_cast<uint16_t>(b[j] == 0 ? kNoSeg : dc_seg(b[j]));
+              }
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < P; ++i) run[i] = 0;
+        }
+      }
+      __syncthreads();  // stage consumed
+      if (tid == 0 && c + kBStages < nch) {
+        const uint64_t qn = q + kBStages;
+        issue_row_chunk(p, r, c + kBStages, sm.ring + (qn % kBStages) * kBStageBytes,
+                        &ring.bar[qn % kBStages], ring.pol);
+      }
+    }
+    ring.seq = seq0 + static_cast<uint64_t>(nch);
+
+    // ------------------------------------------------- 2. threshold ----
+    const int dcnt = static_cast<int>(S * B);
+    tau = (dcnt >= static_cast<int>(k)) ? block_select32(sm.dkeys, dcnt, k, hist, s_bc) : 0u;
+
+    // ------------------------------------------------- 3. filter -------
+    uint16_t* scanl = reinterpret_cast<uint16_t*>(sm.ring + size_t(kBMaxK) * 8);
+    for (int64_t i0 = 0; i0 < S; i0 += kBT) {
+      const int64_t i = i0 + tid;
+      int cls = 0;
+      uint32_t dk[B];
+      uint16_t ds[B];
+      if (i < S) {
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+          dk[j] = sm.dkeys[i * B + j];
+          ds[j] = sm.dsegs[i * B + j];
+        }
+        const int64_t len = imin64(int64_t(1) << alpha, n - (i << alpha));
+        if (dk[0] > tau) cls = (dk[B - 1] > tau && len > B) ? 2 : 1;
+      }
+      if (cls == 2) scanl[atomicAdd(&s_cnt[1], 1u)] = static_cast<uint16_t>(i);
+#pragma unroll
+      for (int j = 0; j < B; ++j) {
+        bool has = false;
+        uint64_t v = 0;
+        if (cls == 1 && dk[j] > tau) {
+          // position: the (occ+1)-th key equal to dk[j] in segment ds[j]
+          int occ = 0;
+#pragma unroll
+          for (int q = 0; q < B; ++q)
+            if (q < j && dk[q] == dk[j] && ds[q] == ds[j]) ++occ;
+          const int64_t lo = (i << alpha) + int64_t(ds[j]) * 32;
+          const int64_t hi = imin64(imin64(n, lo + 32), (i + 1) << alpha);
+          int64_t pos = -1;
+          int cntq = 0;
+          for (int64_t t = lo; t < hi; ++t) {
+            if (map_key<DT>(rk[t]) == dk[j]) {
+              if (cntq == occ) {
+                pos = t;
+                break;
+              }
+              ++cntq;
+            }
+          }
+          if (pos < 0) atomicOr(p.err, kErrTieRank);
+          has = true;
+          v = make_comp(dk[j], static_cast<uint32_t>(pos));
+        }
+        g_append(sm, scr, p.scap, &s_cnt[0], has, v, p.err);
+      }
+    }
+    __syncthreads();
+    const uint32_t nq = s_cnt[1];
+    const int64_t vtotal = int64_t(nq) << alpha;
+    const int64_t vmask = (int64_t(1) << alpha) - 1;
+    for (int64_t v0 = 0; v0 < vtotal; v0 += kBT) {
+      const int64_t v = v0 + tid;
+      bool has = false;
+      uint64_t cv = 0;
+      if (v < vtotal) {
+        const int64_t gi = (int64_t(scanl[v >> alpha]) << alpha) + (v & vmask);
+        if (gi < n) {
+          const uint32_t x = map_key<DT>(rk[gi]);
+          if (x > tau) {
+            has = true;
+            cv = make_comp(x, static_cast<uint32_t>(gi));
+          }
+        }
+      }
+      g_append(sm, scr, p.scap, &s_cnt[0], has, cv, p.err);
+    }
+    __syncthreads();
+  }
+
+  // ------------------------------------------------- 4. second select ----
+  uint64_t* w = reinterpret_cast<uint64_t*>(sm.ring);  // winners (ring is free now)
+  const uint32_t gcnt = s_cnt[0];
+  if (gcnt >= k) {
+    const uint64_t T = block_select64(sm, scr, gcnt, k, hist, s_bc);
+    for (uint32_t i0 = 0; i0 < gcnt; i0 += kBT) {
+      const uint32_t i = i0 + tid;
+      const bool win = i < gcnt && g_get(sm, scr, i) >= T;
+      const uint32_t bal = __ballot_sync(0xFFFFFFFFu, win);
+      uint32_t base = 0;
+      if (bal) {
+        if (lane == __ffs(bal) - 1) base = atomicAdd(&s_cnt[2], __popc(bal));
+        base = __shfl_sync(0xFFFFFFFFu, base, __ffs(bal) - 1);
+      }
+      if (win) {
+        const uint32_t slot = base + __popc(bal & lanemask_lt_b());
+        if (slot < k) w[slot] = g_get(sm, scr, i);
+        else atomicOr(p.err, kErrOverflowW);
+      }
+    }
+    __syncthreads();
+  } else {
+    // k-th key is tau: G plus the smallest-index ties at tau, in index order
+    for (uint32_t i = tid; i < gcnt; i += kBT) w[i] = g_get(sm, scr, i);
+    const uint32_t need = k - gcnt;
+    uint32_t base = 0;  // ties placed so far (uniform)
+    for (int64_t i0 = 0; i0 < S && base < need; i0 += kBT) {
+      const int64_t i = i0 + tid;
+      uint32_t cnt = 0;
+      bool scan = false;
+      if (i < S) {
+        const int64_t len = imin64(int64_t(1) << alpha, n - (i << alpha));
+        const uint32_t m0 = sm.dkeys[i * B], mb = sm.dkeys[i * B + B - 1];
+        if (m0 >= tau) {
+          if (mb >= tau && len > B) {
+            scan = true;  // non-delegates may equal tau
+          } else {
+#pragma unroll
+            for (int j = 0; j < B; ++j)
+              cnt += (sm.dkeys[i * B + j] == tau && sm.dsegs[i * B + j] != kNoSeg) ? 1u : 0u;
+          }
+        }
+      }
+      // exact counts of the subranges that must be read: a warp each
+      __syncthreads();
+      if (tid == 0) s_cnt[3] = 0;
+      __syncthreads();
+      uint16_t* lst = reinterpret_cast<uint16_t*>(sm.ring + size_t(kBMaxK) * 8);
+      if (scan) lst[atomicAdd(&s_cnt[3], 1u)] = static_cast<uint16_t>(tid);
+      __syncthreads();
+      uint32_t* cnts = reinterpret_cast<uint32_t*>(sm.ring + size_t(kBMaxK) * 8 + 1024);
+      cnts[tid] = cnt;
+      __syncthreads();
+      const uint32_t nscan = s_cnt[3];
+      for (uint32_t q = warp; q < nscan; q += kBT / 32) {
+        const int64_t ii = i0 + lst[q];
+        const int64_t lo = ii << alpha;
+        const int64_t len = imin64(int64_t(1) << alpha, n - lo);
+        uint32_t c = 0;
+        for (int64_t t = lane; t < len; t += 32) c += (map_key<DT>(rk[lo + t]) == tau);
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+        if (lane == 0) cnts[lst[q]] = c;
+      }
+      __syncthreads();
+      uint32_t tot;
+      const uint32_t pre = base + block_scan_excl<kBT>(cnts[tid], &tot);
+      // emit: delegate-exact subranges by their thread, read ones by a warp
+      if (i < S && !scan && cnts[tid] > 0 && pre < need) {
+        uint32_t rr = pre;
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+          if (sm.dkeys[i * B + j] == tau && sm.dsegs[i * B + j] != kNoSeg && rr < need) {
+            int occ = 0;
+            for (int q = 0; q < j; ++q)
+              if (sm.dkeys[i * B + q] == tau && sm.dsegs[i * B + q] == sm.dsegs[i * B + j]) ++occ;
+            const int64_t lo = (i << alpha) + int64_t(sm.dsegs[i * B + j]) * 32;
+            const int64_t hi = imin64(imin64(n, lo + 32), (i + 1) << alpha);
+            int64_t pos = -1;
+            int cq = 0;
+            for (int64_t t = lo; t < hi; ++t) {
+              if (map_key<DT>(rk[t]) == tau) {
+                if (cq == occ) {
+                  pos = t;
+                  break;
+                }
+                ++cq;
+              }
+            }
+            if (pos < 0) atomicOr(p.err, kErrTieRank);
+            w[gcnt + rr] = make_comp(tau, static_cast<uint32_t>(pos));
+            ++rr;
+          }
+        }
+      }
+      uint32_t* pres = cnts + kBT;
+      pres[tid] = pre;
+      __syncthreads();
+      for (uint32_t q = warp; q < nscan; q += kBT / 32) {
+        const int64_t ii = i0 + lst[q];
+        uint32_t rr = pres[lst[q]];
+        const int64_t lo = ii << alpha;
+        const int64_t len = imin64(int64_t(1) << alpha, n - lo);
+        for (int64_t off = 0; off < len && rr < need; off += 32) {
+          const int64_t t = off + lane;
+          const bool is_t = t < len && map_key<DT>(rk[lo + t]) == tau;
+          const uint32_t bal = __ballot_sync(0xFFFFFFFFu, is_t);
+          const uint32_t rank = rr + __popc(bal & lanemask_lt_b());
+          if (is_t && rank < need) w[gcnt + rank] = make_comp(tau, static_cast<uint32_t>(lo + t));
+          rr += __popc(bal);
+        }
+      }
+      base += tot;
+      __syncthreads();
+    }
+    __syncthreads();
+  }
+
+  // ------------------------------------------------- 5. sort and write ----
+  block_sort_desc(w, static_cast<int>(k));
+  for (uint32_t j = tid; j < k; j += kBT) {
+    const uint64_t c = w[j];
+    p.out_keys[r.out + j] = unmap_key(DT, comp_key(c));
+    p.out_idx[r.out + j] = static_cast<int32_t>(comp_idx(c));
+  }
+  __syncthreads();
+}
+
+template <int DT>
+__global__ void __launch_bounds__(kBT, 1) batched_kernel(BatchParams p) {
+  extern __shared__ __align__(128) unsigned char bsm[];
+  __shared__ __align__(8) uint64_t bars[kBStages];
+  __shared__ uint32_t hist[256];
+  __shared__ uint32_t s_bc[4];
+  __shared__ uint32_t s_cnt[4];
+  __shared__ uint32_t s_row;
+  __shared__ uint64_t s_lists[(kBT / 32) * 4];
+  Smem sm;
+  sm.ring = bsm;
+  sm.dkeys = reinterpret_cast<uint32_t*>(bsm + kRingBytes);
+  sm.dsegs = reinterpret_cast<uint16_t*>(bsm + kRingBytes + size_t(kBDMax) * 4);
+  sm.gbuf = reinterpret_cast<uint64_t*>(bsm + kRingBytes + size_t(kBDMax) * 6);
+  Ring ring;
+  ring.bar = bars;
+  ring.seq = 0;
+  ring.pol = l2_evict_first_policy();
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kBStages; ++s) mbar_init(&bars[s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  for (;;) {
+    if (threadIdx.x == 0) s_row = atomicAdd(p.row_ctr, 1u);
+    __syncthreads();
+    const uint32_t ri = s_row;
+    __syncthreads();
+    if (ri >= static_cast<uint32_t>(p.nrows)) break;
+    const RowDesc r = p.rows[ri];
+    switch (r.beta) {
+      case 1: process_row<DT, 1>(p, r, sm, ring, hist, s_bc, s_cnt, s_lists); break;
+      case 3: process_row<DT, 3>(p, r, sm, ring, hist, s_bc, s_cnt, s_lists); break;
+      case 4: process_row<DT, 4>(p, r, sm, ring, hist, s_bc, s_cnt, s_lists); break;
+      default: process_row<DT, 2>(p, r, sm, ring, hist, s_bc, s_cnt, s_lists); break;
+    }
+    // a bounded wait gave up: copies may still be in flight, stop this CTA
+    if (__syncthreads_or(threadIdx.x == 0 && (__ldcg(p.err) & kErrTimeout))) break;
+  }
+}
+
+// Fills every key with hashed bits (tuning inputs only).
+__global__ void fill_hash_kernel(uint32_t* a, int64_t n, uint64_t seed) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    uint64_t z = seed + static_cast<uint64_t>(i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    a[i] = static_cast<uint32_t>((z ^ (z >> 31)) >> 32);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_batched(int dtype, const void* keys, int64_t total, const RowDesc* rows,
+                           int32_t nrows, uint32_t* row_ctr, uint64_t* scratch, int64_t scap,
+                           void* out_keys, int32_t* out_idx, uint32_t* err, int grid,
+                           cudaStream_t s) {
+  BatchParams p;
+  p.keys = static_cast<const uint32_t*>(keys);
+  p.total = total;
+  p.rows = rows;
+  p.nrows = nrows;
+  p.row_ctr = row_ctr;
+  p.scratch = scratch;
+  p.scap = scap;
+  p.out_keys = static_cast<uint32_t*>(out_keys);
+  p.out_idx = out_idx;
+  p.err = err;
+  switch (dtype) {
+    case DRTOPK_U32:
+      cudaFuncSetAttribute(batched_kernel<DRTOPK_U32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(kDynSmem));
+      batched_kernel<DRTOPK_U32><<<grid, kBT, kDynSmem, s>>>(p);
+      break;
+    case DRTOPK_I32:
+      cudaFuncSetAttribute(batched_kernel<DRTOPK_I32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(kDynSmem));
+      batched_kernel<DRTOPK_I32><<<grid, kBT, kDynSmem, s>>>(p);
+      break;
+    default:
+      cudaFuncSetAttribute(batched_kernel<DRTOPK_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(kDynSmem));
+      batched_kernel<DRTOPK_F32><<<grid, kBT, kDynSmem, s>>>(p);
+      break;
+  }
+  note_launch();
+  return cudaGetLastError();
+}
+
+
+// ------------------------------------------------------------------------
+// Host side: per-shape parameters, plans, the C ABI.
+// ------------------------------------------------------------------------
+namespace {
+
+constexpr int kTuneN0 = 10, kTuneN1 = 31;  // log2 n buckets
+constexpr int kTuneK1 = 12;                // log2 k buckets 0..12
+struct TuneEntry {
+  int alpha = 0;  // 0: not tuned, use Rule 4
+  int beta = 0;
+};
+std::mutex g_tune_mu;
+TuneEntry g_tune[kTuneN1 - kTuneN0 + 1][kTuneK1 + 1];
+
+int ilog2_floor(int64_t v) {
+  int l = 0;
+  while ((int64_t(1) << (l + 1)) <= v) ++l;
+  return l;
+}
+
+// Rule 4 / Eq. 9 (Sec. 4.2), const = 3, rounded down.
+int rule4(int64_t n, int64_t k) {
+  return static_cast<int>(std::floor(0.5 * (std::log2(double(n)) - std::log2(double(k)) + 3.0)));
+}
+
+struct RowPlan {
+  int alpha, beta;
+  int64_t gneed;  // candidate capacity the row may need
+};
+
+// Parameters of one row for the on-chip path: the forced or tuned (alpha,
+// beta) of the row's shape bucket, else Rule 4 and beta = 2, lowered while
+// fewer than 2k delegates would exist; in every case raised so that the
+// delegates fit on chip (beta * S <= kBDMax, alpha >= 5).
+RowPlan plan_row(int64_t n, int64_t k, int force_alpha, int force_beta) {
+  RowPlan rp{0, 0, n};
+  if (n <= kBDirect && force_alpha <= 0) return rp;  // direct select, G = the row
+  int a = 0, b = 0;
+  {
+    const int ln = std::min(std::max(ilog2_floor(n), kTuneN0), kTuneN1) - kTuneN0;
+    const int lk = std::min(ilog2_floor(k), kTuneK1);
+    std::lock_guard<std::mutex> lk2(g_tune_mu);
+    a = g_tune[ln][lk].alpha;
+    b = g_tune[ln][lk].beta;
+  }
+  if (force_beta > 0) b = force_beta;
+  if (b <= 0) b = 2;
+  if (force_alpha > 0) a = force_alpha;
+  const bool from_rule4 = a <= 0;
+  if (from_rule4) a = rule4(n, k);
+  // delegates must fit on chip: beta * S <= kBDMax
+  int amin = 5;
+  while (amin < 16 && b * ((n + (int64_t(1) << amin) - 1) >> amin) > kBDMax) ++amin;
+  a = std::max(a, amin);
+  a = std::min(a, 16);
+  if (from_rule4)
+    while (a > amin && int64_t(b) * ((n + (int64_t(1) << a) - 1) >> a) < 2 * k) --a;
+  const int64_t S = (n + (int64_t(1) << a) - 1) >> a;
+  rp.alpha = a;
+  rp.beta = b;
+  rp.gneed = (int64_t(b) * S >= k) ? std::min<int64_t>(n, ((k - 1) / b) * (int64_t(1) << a) + k) : n;
+  return rp;
+}
+
+// Copies `count` entries from a host or device pointer into `dst`.
+template <class T>
+bool fetch_host(const T* src, size_t count, std::vector<T>& dst) {
+  dst.resize(count);
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, src) == cudaSuccess &&
+      (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)) {
+    return cudaMemcpy(dst.data(), src, count * sizeof(T), cudaMemcpyDeviceToHost) == cudaSuccess;
+  }
+  cudaGetLastError();  // no device, or a plain host pointer
+  std::copy(src, src + count, dst.begin());
+  return true;
+}
+
+}  // namespace
+}  // namespace drtopk
+
+using namespace drtopk;
+
+struct drtopk_batch_plan {
+  int dtype = 0;
+  int32_t rows = 0;
+  int64_t total = 0;
+  int grid = 0;
+  int64_t scap = 0;
+  RowDesc* d_rows = nullptr;     // device, processing order
+  uint32_t* d_ctl = nullptr;     // [0] row counter, [1] error flags
+  uint64_t* d_scratch = nullptr;
+  std::vector<int32_t> alpha, beta;  // per row, row order
+};
+
+extern "C" {
+
+drtopk_status drtopk_batch_plan_create(drtopk_dtype dtype, const int64_t* row_off_in,
+                                       const int32_t* ks_in, int32_t rows, int alpha, int beta,
+                                       drtopk_batch_plan** out) {
+  if (!out || !row_off_in || !ks_in || rows < 1) return DRTOPK_ERR_INVALID;
+  std::vector<int64_t> off_h;
+  std::vector<int32_t> ks_h;
+  if (!fetch_host(row_off_in, static_cast<size_t>(rows) + 1, off_h) ||
+      !fetch_host(ks_in, static_cast<size_t>(rows), ks_h))
+    return DRTOPK_ERR_CUDA;
+  const int64_t* row_off = off_h.data();
+  const int32_t* ks = ks_h.data();
+  if (dtype != DRTOPK_U32 && dtype != DRTOPK_I32 && dtype != DRTOPK_F32) return DRTOPK_ERR_DTYPE;
+  if (alpha < 0 || alpha > 16 || (alpha > 0 && alpha < 5) || beta < 0 || beta > kMaxBeta)
+    return DRTOPK_ERR_INVALID;
+  if (row_off[0] < 0) return DRTOPK_ERR_INVALID;
+  std::vector<RowDesc> rd(static_cast<size_t>(rows));
+  std::vector<int32_t> ra(static_cast<size_t>(rows)), rb(static_cast<size_t>(rows));
+  int64_t out_pos = 0, scap = 0;
+  for (int32_t r = 0; r < rows; ++r) {
+    const int64_t n = row_off[r + 1] - row_off[r];
+    const int64_t k = ks[r];
+    if (n < 1 || n > kBMaxN) return DRTOPK_ERR_INVALID;
+    if (k < 1 || k > n || k > kBMaxK) return DRTOPK_ERR_K;
+    const RowPlan rp = plan_row(n, k, alpha, beta);
+    rd[r].start = row_off[r];
+    rd[r].out = out_pos;
+    rd[r].n = static_cast<int32_t>(n);
+    rd[r].k = static_cast<int32_t>(k);
+    rd[r].alpha = rp.alpha;
+    rd[r].beta = rp.beta;
+    ra[r] = rp.alpha;
+    rb[r] = rp.beta;
+    out_pos += k;
+    scap = std::max<int64_t>(scap, rp.gneed - kBGS);
+  }
+  // largest rows first: the CTAs that take them start earliest
+  std::stable_sort(rd.begin(), rd.end(), [](const RowDesc& a, const RowDesc& b) { return a.n > b.n; });
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return DRTOPK_ERR_CUDA;
+  auto* pl = new drtopk_batch_plan;
+  pl->dtype = dtype;
+  pl->rows = rows;
+  pl->total = row_off[rows];
+  pl->grid = std::min<int>(sms, rows);
+  pl->scap = std::max<int64_t>(scap, 1);
+  pl->alpha = std::move(ra);
+  pl->beta = std::move(rb);
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&pl->d_rows), rd.size() * sizeof(RowDesc));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(pl->d_rows, rd.data(), rd.size() * sizeof(RowDesc), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&pl->d_ctl), 2 * sizeof(uint32_t));
+  if (e == cudaSuccess)
+    e = cudaMalloc(reinterpret_cast<void**>(&pl->d_scratch),
+                   static_cast<size_t>(pl->grid) * pl->scap * sizeof(uint64_t));
+  if (e != cudaSuccess) {
+    cudaFree(pl->d_rows);
+    cudaFree(pl->d_ctl);
+    cudaFree(pl->d_scratch);
+    delete pl;
+    return e == cudaErrorMemoryAllocation ? DRTOPK_ERR_NOMEM : DRTOPK_ERR_CUDA;
+  }
+  *out = pl;
+  return DRTOPK_OK;
+}
+
+drtopk_status drtopk_batch_plan_run(drtopk_batch_plan* pl, const void* keys, void* out_keys,
+                                    int32_t* out_idx, void* stream) {
+  if (!pl || !keys || !out_keys || !out_idx) return DRTOPK_ERR_INVALID;
+  if (reinterpret_cast<uintptr_t>(keys) & 15u) return DRTOPK_ERR_INVALID;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(pl->d_ctl, 0, 2 * sizeof(uint32_t), s);
+  if (e == cudaSuccess)
+    e = launch_batched(pl->dtype, keys, pl->total, pl->d_rows, pl->rows, pl->d_ctl,
+                       pl->d_scratch, pl->scap, out_keys, out_idx, pl->d_ctl + 1, pl->grid, s);
+  return e == cudaSuccess ? DRTOPK_OK : (e == cudaErrorMemoryAllocation ? DRTOPK_ERR_NOMEM : DRTOPK_ERR_CUDA);
+}
+
+drtopk_status drtopk_batch_plan_status(drtopk_batch_plan* pl, void* stream) {
+  if (!pl) return DRTOPK_ERR_INVALID;
+  uint32_t err = 0;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaMemcpyAsync(&err, pl->d_ctl + 1, sizeof(err), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return DRTOPK_ERR_CUDA;
+  if (err & kErrTimeout) return DRTOPK_ERR_TIMEOUT;
+  return err ? DRTOPK_ERR_CUDA : DRTOPK_OK;
+}
+
+drtopk_status drtopk_batch_plan_params(const drtopk_batch_plan* pl, int32_t* alpha,
+                                       int32_t* beta) {
+  if (!pl || !alpha || !beta) return DRTOPK_ERR_INVALID;
+  std::copy(pl->alpha.begin(), pl->alpha.end(), alpha);
+  std::copy(pl->beta.begin(), pl->beta.end(), beta);
+  return DRTOPK_OK;
+}
+
+drtopk_status drtopk_batch_plan_destroy(drtopk_batch_plan* pl) {
+  if (!pl) return DRTOPK_ERR_INVALID;
+  cudaDeviceSynchronize();
+  cudaFree(pl->d_rows);
+  cudaFree(pl->d_ctl);
+  cudaFree(pl->d_scratch);
+  delete pl;
+  return DRTOPK_OK;
+}
+
+drtopk_status drtopk_topk_batched(const void* keys, drtopk_dtype dtype, const int64_t* row_off,
+                                  const int32_t* ks, int32_t rows, void* out_keys,
+                                  int32_t* out_idx, void* stream) {
+  drtopk_batch_plan* pl = nullptr;
+  drtopk_status st = drtopk_batch_plan_create(dtype, row_off, ks, rows, 0, 0, &pl);
+  if (st != DRTOPK_OK) return st;
+  st = drtopk_batch_plan_run(pl, keys, out_keys, out_idx, stream);
+  if (st == DRTOPK_OK) st = drtopk_batch_plan_status(pl, stream);
+  drtopk_batch_plan_destroy(pl);
+  return st;
+}
+
+drtopk_status drtopk_tune_get(int32_t log2n, int32_t log2k, int* alpha, int* beta) {
+  if (log2n < kTuneN0 || log2n > kTuneN1 || log2k < 0 || log2k > kTuneK1 || !alpha || !beta)
+    return DRTOPK_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  *alpha = g_tune[log2n - kTuneN0][log2k].alpha;
+  *beta = g_tune[log2n - kTuneN0][log2k].beta;
+  return DRTOPK_OK;
+}
+
+drtopk_status drtopk_tune_set(int32_t log2n, int32_t log2k, int alpha, int beta) {
+  if (log2n < kTuneN0 || log2n > kTuneN1 || log2k < 0 || log2k > kTuneK1) return DRTOPK_ERR_INVALID;
+  if (alpha < 0 || alpha > 16 || (alpha > 0 && alpha < 5) || beta < 0 || beta > kMaxBeta)
+    return DRTOPK_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[log2n - kTuneN0][log2k].alpha = alpha;
+  g_tune[log2n - kTuneN0][log2k].beta = beta;
+  return DRTOPK_OK;
+}
+
+// Measures, for every (log2 n, log2 k) bucket with min_log2n <= log2 n <=
+// max_log2n and 2^(log2 k) <= min(4096, n / 2), the batched kernel on
+// `rows_per_shape` rows of 2^log2n hashed keys with alpha in [Rule 4 - 3,
+// Rule 4 + 2] and beta in {1, 2, 3, 4}, and stores the fastest pair.
+drtopk_status drtopk_autotune_batched(drtopk_dtype dtype, int32_t min_log2n, int32_t max_log2n,
+                                      int32_t rows_per_shape, void* stream) {
+  if (min_log2n < kTuneN0 || max_log2n > 24 || min_log2n > max_log2n || rows_per_shape < 1)
+    return DRTOPK_ERR_INVALID;
+  if (dtype != DRTOPK_U32 && dtype != DRTOPK_I32 && dtype != DRTOPK_F32) return DRTOPK_ERR_DTYPE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t maxn = int64_t(1) << max_log2n;
+  const int64_t total = maxn * rows_per_shape;
+  uint32_t* d_keys = nullptr;
+  uint32_t* d_ok = nullptr;
+  int32_t* d_oi = nullptr;
+  if (cudaMalloc(reinterpret_cast<void**>(&d_keys), total * 4) != cudaSuccess) return DRTOPK_ERR_NOMEM;
+  if (cudaMalloc(reinterpret_cast<void**>(&d_ok), size_t(kBMaxK) * rows_per_shape * 4) != cudaSuccess ||
+      cudaMalloc(reinterpret_cast<void**>(&d_oi), size_t(kBMaxK) * rows_per_shape * 4) != cudaSuccess) {
+    cudaFree(d_keys);
+    cudaFree(d_ok);
+    return DRTOPK_ERR_NOMEM;
+  }
+  fill_hash_kernel<<<1024, 256, 0, s>>>(d_keys, total, 0x5EEDull);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  drtopk_status st = DRTOPK_OK;
+  for (int ln = min_log2n; ln <= max_log2n && st == DRTOPK_OK; ++ln) {
+    const int64_t n = int64_t(1) << ln;
+    std::vector<int64_t> off(rows_per_shape + 1);
+    for (int r = 0; r <= rows_per_shape; ++r) off[r] = r * n;
+    for (int lk = 0; lk <= kTuneK1 && (int64_t(1) << lk) <= std::min<int64_t>(kBMaxK, n / 2); ++lk) {
+      const int32_t k = 1 << lk;
+      std::vector<int32_t> kv(rows_per_shape, k);
+      const int a4 = rule4(n, k);
+      float best = 1e30f;
+      int best_a = 0, best_b = 2;
+      for (int b = 1; b <= 4 && st == DRTOPK_OK; ++b) {
+        for (int a = std::max(5, a4 - 3); a <= std::min(16, a4 + 2); ++a) {
+          if (n <= kBDirect) break;
+          drtopk_batch_plan* pl = nullptr;
+          if (drtopk_batch_plan_create(dtype, off.data(), kv.data(), rows_per_shape, a, b, &pl) != DRTOPK_OK)
+            continue;
+          // the clamp may have moved alpha: skip duplicates of another alpha
+          float ms_best = 1e30f;
+          for (int rep = 0; rep < 3; ++rep) {
+            cudaEventRecord(e0, s);
+            drtopk_batch_plan_run(pl, d_keys, d_ok, d_oi, s);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms_best = std::min(ms_best, ms);
+          }
+          if (drtopk_batch_plan_status(pl, s) != DRTOPK_OK) st = DRTOPK_ERR_CUDA;
+          drtopk_batch_plan_destroy(pl);
+          if (ms_best < best) {
+            best = ms_best;
+            best_a = a;
+            best_b = b;
+          }
+        }
+      }
+      if (best_a > 0) drtopk_tune_set(ln, lk, best_a, best_b);
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(d_keys);
+  cudaFree(d_ok);
+  cudaFree(d_oi);
+  return st;
+}
+
+}  // extern "C"

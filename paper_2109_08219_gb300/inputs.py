@@ -249,7 +249,8 @@ ADVERSARIAL = ["ascending", "descending", "all_equal", "distinct16", "zipf"]
 def batched_rows(rows, seed, device="cpu", lo_exp=10, hi_exp=22, kmax=1024):
     """Ragged batch recipe: row lengths round(2^U[lo, hi]), k_r uniform in
     [1, min(kmax, n_r)] (stream 20 and 21 per row). Returns (lengths, ks) as
-    Python lists; the keys come from ``normal_f32`` with seed (seed, row)."""
+    Python lists; the keys of the batch are ``normal_f32(sum(lengths), seed)``
+    with the rows laid out back to back."""
     lens, ks = [], []
     for r in range(rows):
         u = (hash_int(seed, 20, r) >> 11) * (2.0 ** -53)
