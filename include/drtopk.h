@@ -37,12 +37,14 @@
  *     the caller owns every input and output buffer.
  *   - drtopk_kth, drtopk_topk and drtopk_topk_ex (without statistics) keep a
  *     cache of CUDA graphs of whole queries, keyed by every argument
- *     (pointers, sizes, dtype, alpha, beta, device, stream): a repeated call
- *     replays one graph instead of launching ~30 kernels. Each cached entry
- *     owns a workspace; entries are evicted least-recently-used beyond 64
- *     entries or DRTOPK_GRAPH_CACHE_BYTES (default 16 GiB) of workspace.
- *     DRTOPK_GRAPH_CACHE=0 disables the cache. Calls made while profiling
- *     (drtopk_profile_begin) launch kernel by kernel.
+ *     (pointers, sizes, dtype, alpha, beta, device, stream): the second
+ *     call with a key captures a graph and later calls replay it instead of
+ *     launching ~30 kernels (the first call launches kernel by kernel). Each
+ *     cached entry owns a workspace; entries are evicted least-recently-used
+ *     beyond 64 entries or DRTOPK_GRAPH_CACHE_BYTES (default 16 GiB) of
+ *     workspace. DRTOPK_GRAPH_CACHE=0 disables the cache. Calls made while
+ *     profiling (drtopk_profile_begin) or on a stream that is being captured
+ *     launch kernel by kernel (into the caller's capture).
  *   - Calls return a drtopk_status and never abort. A CUDA error returns
  *     DRTOPK_ERR_CUDA; argument checks happen before any CUDA call.
  */
@@ -243,6 +245,18 @@ drtopk_status drtopk_batch_plan_status(drtopk_batch_plan* plan, void* stream);
  * `rows` entries; alpha 0 marks a direct select). */
 drtopk_status drtopk_batch_plan_params(const drtopk_batch_plan* plan, int32_t* alpha,
                                        int32_t* beta);
+
+/*
+ * Device cycles (clock64 of the first thread of each CTA, summed over CTAs
+ * and over runs since the last reset) spent in each step of the batched
+ * kernel: out[0] delegate pass, [1] threshold select, [2] filter, [3] second
+ * select (or sort of all candidates), [4] tie ranking, [5] final sort and
+ * output, [6] loading rows of the direct select. out: HOST, 7 entries.
+ * reset != 0 clears the counters. Synchronizes `stream`.
+ */
+#define DRTOPK_BATCH_PHASES 7
+drtopk_status drtopk_batch_plan_phase_cycles(drtopk_batch_plan* plan, uint64_t* out,
+                                             int reset, void* stream);
 
 /* Synchronizes the device and frees the plan. */
 drtopk_status drtopk_batch_plan_destroy(drtopk_batch_plan* plan);

@@ -26,6 +26,8 @@ STATUS = ["DRTOPK_OK", "DRTOPK_ERR_INVALID", "DRTOPK_ERR_K", "DRTOPK_ERR_DTYPE",
           "DRTOPK_ERR_TIMEOUT", "DRTOPK_PENDING"]
 NUM_STAGES = 6
 STAGE_NAMES = ["delegate", "threshold", "filter", "ties", "second_select", "sort"]
+BATCH_PHASES = ["delegate", "threshold", "filter", "second_select", "ties", "sort_output",
+                "direct_load"]
 
 
 class DrTopkError(RuntimeError):
@@ -89,6 +91,7 @@ def lib():
         L.drtopk_batch_plan_status.argtypes = [p, p]
         L.drtopk_batch_plan_params.argtypes = [p, pi32, pi32]
         L.drtopk_batch_plan_destroy.argtypes = [p]
+        L.drtopk_batch_plan_phase_cycles.argtypes = [p, ctypes.POINTER(ctypes.c_uint64), i32, p]
         L.drtopk_topk_batched.argtypes = [p, i32, pi64, pi32, i32, p, p, p]
         L.drtopk_tune_get.argtypes = [i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
         L.drtopk_tune_set.argtypes = [i32, i32, i32, i32]
@@ -97,7 +100,8 @@ def lib():
                    "drtopk_delegates", "drtopk_topk_host", "drtopk_profile_begin",
                    "drtopk_profile_end", "drtopk_batch_plan_create", "drtopk_batch_plan_run",
                    "drtopk_batch_plan_status", "drtopk_batch_plan_params",
-                   "drtopk_batch_plan_destroy", "drtopk_topk_batched", "drtopk_tune_get",
+                   "drtopk_batch_plan_destroy", "drtopk_batch_plan_phase_cycles",
+                   "drtopk_topk_batched", "drtopk_tune_get",
                    "drtopk_tune_set", "drtopk_autotune_batched"):
             getattr(L, fn).restype = i32
         _lib = L
@@ -326,6 +330,15 @@ class BatchPlan:
     def status(self, stream=None):
         _check(lib().drtopk_batch_plan_status(self._h, _stream(stream)),
                "drtopk_batch_plan_status")
+
+    def phase_cycles(self, reset=False, stream=None):
+        """Cycles per step of the batched kernel, summed over CTAs and runs:
+        a dict over BATCH_PHASES."""
+        out = (ctypes.c_uint64 * len(BATCH_PHASES))()
+        _check(lib().drtopk_batch_plan_phase_cycles(self._h, out, 1 if reset else 0,
+                                                    _stream(stream)),
+               "drtopk_batch_plan_phase_cycles")
+        return {name: int(v) for name, v in zip(BATCH_PHASES, out)}
 
     def close(self):
         if self._h:

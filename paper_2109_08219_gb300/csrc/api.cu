@@ -239,9 +239,12 @@ cudaError_t enqueue_query(const Work& w, const Plan& P, const void* keys, bool t
 // ---------------------------------------------------------- graph cache ---
 // Repeated calls with identical arguments on the same stream replay a CUDA
 // graph of the whole query (one graph launch instead of ~30 kernel launches).
-// Each entry owns its workspace; entries are evicted least-recently-used
-// past kGraphMaxEntries or DRTOPK_GRAPH_CACHE_BYTES (default 16 GiB) of
-// workspace. DRTOPK_GRAPH_CACHE=0 disables the cache.
+// A graph is built on the second call with a key (the last kSeenKeys keys
+// are remembered), so one-off calls never pay for a capture. Each entry
+// owns its workspace; entries are evicted least-recently-used past
+// kGraphMaxEntries or DRTOPK_GRAPH_CACHE_BYTES (default 16 GiB) of
+// workspace. Calls on a stream that is being captured launch kernel by
+// kernel into that capture. DRTOPK_GRAPH_CACHE=0 disables the cache.
 struct GraphKey {
   const void* keys;
   void* out_keys;
@@ -269,8 +272,11 @@ struct GraphEntry {
 };
 
 constexpr size_t kGraphMaxEntries = 64;
+constexpr size_t kSeenKeys = 256;
 std::mutex g_gmu;
 std::vector<GraphEntry> g_graphs;
+GraphKey g_seen[kSeenKeys];
+size_t g_seen_next = 0;
 uint64_t g_gtick = 0;
 size_t g_gbytes = 0;
 cudaStream_t g_capture_stream[64];
@@ -337,12 +343,26 @@ bool run_graph(const Plan& P, const void* keys, int dtype, int64_t n, int64_t k,
                drtopk_status* st) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (cap != cudaStreamCaptureStatusNone) return false;
   GraphKey key{keys, out_keys, out_idx, out_kth, n, k, dtype, P.alpha, P.beta, dev, s};
   std::lock_guard<std::mutex> lk(g_gmu);
   GraphEntry* ent = nullptr;
   for (auto& e : g_graphs)
     if (e.key == key) ent = &e;
   if (!ent) {
+    // admit a key on its second call
+    bool seen = false;
+    for (size_t i = 0; i < kSeenKeys && !seen; ++i) seen = g_seen[i] == key;
+    if (!seen) {
+      g_seen[g_seen_next] = key;
+      g_seen_next = (g_seen_next + 1) % kSeenKeys;
+      return false;
+    }
     const Layout L = layout(P, k, topk, false);
     if (L.total > graph_cache_budget()) return false;
     while (!g_graphs.empty() &&

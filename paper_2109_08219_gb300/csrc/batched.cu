@@ -2,7 +2,7 @@
 // persistent launch. Each CTA takes rows from an atomic counter (largest
 // first) and runs the whole delegate-centric method on a row on-chip:
 //   1. delegate pass (Rule 1 Sec. 3.1, Rule 3 Sec. 3.3): the row streams
-//      through a 4-stage ring of 32 KB TMA bulk copies; every thread keeps
+//      through a 2-stage ring of 64 KB TMA bulk copies; every thread keeps
 //      the top-beta of 32 keys by value; (key, segment) lists are merged
 //      per subrange; the delegate vector D stays in shared memory;
 //   2. threshold (Rule 2 Sec. 3.2): MSD radix select of the k-th delegate
@@ -39,9 +39,13 @@ struct RowDesc {
 
 namespace {
 
-constexpr int kBT = 256;              // threads per CTA
-constexpr int kBChunk = 8192;         // keys per ring stage (32 KB)
-constexpr int kBStages = 4;
+constexpr int kBT = 512;              // threads per CTA (one CTA per SM)
+constexpr int kBWarps = kBT / 32;
+constexpr int kBLogWarps = 4;
+constexpr int kBLogChunk = 14;        // keys per ring stage: 32 per thread
+constexpr int kBChunk = 1 << kBLogChunk;
+constexpr int kBStages = 2;
+static_assert((1 << kBLogWarps) == kBWarps && kBChunk == kBT * 32, "chunk geometry");
 constexpr int kBStageBytes = kBChunk * 4 + 128;  // + room for the alignment shift
 constexpr int kBDMax = 8192;          // delegate slots (S * beta) kept on chip
 constexpr int kBGS = 4096;            // candidates kept on chip
@@ -50,6 +54,10 @@ constexpr int kBDirect = 4096;        // rows up to this size: direct select
 constexpr int64_t kBMaxN = int64_t(1) << 24;  // longest row of the batched path
 
 constexpr size_t kRingBytes = size_t(kBStages) * kBStageBytes;
+// the ring is free after the delegate pass; the filter keeps its lists there
+constexpr size_t kScanOff = 0;                          // u16 subrange list, <= kBDMax
+constexpr size_t kReqOff = size_t(kBDMax) * 2;          // u64 resolve requests, <= kBDMax
+static_assert(kReqOff + size_t(kBDMax) * 8 <= kRingBytes, "filter lists exceed the ring");
 constexpr size_t kDynSmem = kRingBytes + size_t(kBDMax) * 4 + size_t(kBDMax) * 2 + size_t(kBGS) * 8;
 
 struct BatchParams {
@@ -63,7 +71,22 @@ struct BatchParams {
   uint32_t* out_keys;
   int32_t* out_idx;
   uint32_t* err;
+  unsigned long long* phase;  // kBPhases cycle counters (thread 0 of each CTA)
 };
+
+// Cycle counters of the batched kernel, summed over CTAs: 0 delegate pass,
+// 1 threshold select, 2 filter, 3 second select (or sort of all
+// candidates), 4 tie ranking, 5 final sort and output, 6 loading the rows
+// of the direct select.
+constexpr int kBPhases = 7;
+
+__device__ __forceinline__ void phase_mark(const BatchParams& p, int ph, long long& tmark) {
+  if (threadIdx.x == 0) {
+    const long long t = clock64();
+    atomicAdd(p.phase + ph, static_cast<unsigned long long>(t - tmark));
+    tmark = t;
+  }
+}
 
 struct Smem {
   unsigned char* ring;
@@ -113,6 +136,46 @@ __device__ __forceinline__ void issue_row_chunk(const BatchParams& p, const RowD
 }
 
 // ---------------------------------------------------- block radix select ---
+// Warp 0: finds the digit d (from the top) at which the descending running
+// count of hist[] reaches krem; s_bc = {d, krem - count above d, hist[d]}.
+// Each lane sums 8 buckets; a warp scan locates the crossing lane.
+__device__ __forceinline__ void bucket_search(const uint32_t* hist, uint32_t krem, uint32_t* s_bc) {
+  const int lane = threadIdx.x & 31;
+  const int top = 255 - lane * 8;  // this lane's buckets: top, top-1, ..., top-7
+  uint32_t h[8];
+  uint32_t sum = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    h[q] = hist[top - q];
+    sum += h[q];
+  }
+  uint32_t incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  const uint32_t hit = __ballot_sync(0xFFFFFFFFu, incl >= krem);
+  const int f = hit ? __ffs(hit) - 1 : 31;
+  if (lane == f) {
+    uint32_t acc = incl - sum;
+    int d = top - 7;
+    uint32_t hd = h[7];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      if (acc + h[q] >= krem || q == 7) {
+        d = top - q;
+        hd = h[q];
+        break;
+      }
+      acc += h[q];
+    }
+    s_bc[0] = static_cast<uint32_t>(d);
+    s_bc[1] = krem - acc;
+    s_bc[2] = hd;
+  }
+}
+
 // k-th largest (1-based rank krem) of the 32-bit keys a[0..cnt) in shared
 // memory (delegates). Returns the key.
 __device__ uint32_t block_select32(const uint32_t* a, int cnt, uint32_t krem, uint32_t* hist,
@@ -128,16 +191,7 @@ __device__ uint32_t block_select32(const uint32_t* a, int cnt, uint32_t krem, ui
       if ((x & mask) == (prefix & mask)) atomicAdd(&hist[(x >> sh) & 255u], 1u);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      uint32_t acc = 0;
-      int d = 255;
-      for (; d > 0; --d) {
-        if (acc + hist[d] >= krem) break;
-        acc += hist[d];
-      }
-      s_bc[0] = static_cast<uint32_t>(d);
-      s_bc[1] = krem - acc;
-    }
+    if (threadIdx.x < 32) bucket_search(hist, krem, s_bc);
     __syncthreads();
     prefix |= s_bc[0] << sh;
     krem = s_bc[1];
@@ -186,17 +240,7 @@ __device__ uint64_t block_select64(const Smem& sm, const uint64_t* scr, uint32_t
       if ((x & mask) == (prefix & mask)) atomicAdd(&hist[static_cast<uint32_t>(x >> sh) & 255u], 1u);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      uint32_t acc = 0;
-      int d = 255;
-      for (; d > 0; --d) {
-        if (acc + hist[d] >= krem) break;
-        acc += hist[d];
-      }
-      s_bc[0] = static_cast<uint32_t>(d);
-      s_bc[1] = krem - acc;
-      s_bc[2] = hist[d];
-    }
+    if (threadIdx.x < 32) bucket_search(hist, krem, s_bc);
     __syncthreads();
     prefix |= static_cast<uint64_t>(s_bc[0]) << sh;
     krem = s_bc[1];
@@ -207,23 +251,24 @@ __device__ uint64_t block_select64(const Smem& sm, const uint64_t* scr, uint32_t
   return prefix;
 }
 
-// Bitonic sort (descending) of w[0..k) in shared memory, k <= kBMaxK.
-__device__ void block_sort_desc(uint64_t* w, int k) {
+// Bitonic sort (descending) of w[0..cnt) in shared memory, cnt <= kBGS;
+// pads w[cnt..P) with 0 (P = next power of two), which sorts last.
+__device__ void block_sort_desc(uint64_t* w, int cnt) {
   int P = 1;
-  while (P < k) P <<= 1;
-  for (int i = k + threadIdx.x; i < P; i += kBT) w[i] = 0ull;
+  while (P < cnt) P <<= 1;
+  for (int i = cnt + threadIdx.x; i < P; i += kBT) w[i] = 0ull;
   __syncthreads();
+  const int half = P >> 1;
   for (int size = 2; size <= P; size <<= 1) {
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      for (int i = threadIdx.x; i < P; i += kBT) {
-        const int j = i ^ stride;
-        if (j > i) {
-          const bool desc = (i & size) == 0;
-          const uint64_t a = w[i], b = w[j];
-          if ((a < b) == desc) {
-            w[i] = b;
-            w[j] = a;
-          }
+      for (int q = threadIdx.x; q < half; q += kBT) {
+        const int i = 2 * q - (q & (stride - 1));
+        const int j = i + stride;
+        const bool desc = (i & size) == 0;
+        const uint64_t a = w[i], b = w[j];
+        if ((a < b) == desc) {
+          w[i] = b;
+          w[j] = a;
         }
       }
       __syncthreads();
@@ -249,12 +294,14 @@ __device__ void process_row(const BatchParams& p, const RowDesc& r, const Smem& 
     s_cnt[0] = 0;  // |G|
     s_cnt[1] = 0;  // scan list length
     s_cnt[2] = 0;  // winners
+    s_cnt[3] = 0;  // resolve requests
   }
   // the previous row wrote the ring with generic stores; the bulk copies of
   // this row write it through the async proxy
   fence_proxy_async_smem();
   __syncthreads();
 
+  long long tmark = clock64();
   int64_t S = 0;
   uint32_t tau = 0;
   bool direct = (alpha == 0);
@@ -269,7 +316,7 @@ __device__ void process_row(const BatchParams& p, const RowDesc& r, const Smem& 
     // ---------------------------------------------- 1. delegate pass ----
     S = (n + (int64_t(1) << alpha) - 1) >> alpha;
     const int64_t nch = (n + kBChunk - 1) / kBChunk;
-    const int cps_log = alpha > 13 ? alpha - 13 : 0;
+    const int cps_log = alpha > kBLogChunk ? alpha - kBLogChunk : 0;
     const uint64_t seq0 = ring.seq;
     if (tid == 0) {
       for (int64_t c = 0; c < kBStages && c < nch; ++c) {
@@ -323,7 +370,7 @@ __device__ void process_row(const BatchParams& p, const RowDesc& r, const Smem& 
       uint64_t a[P];
 #pragma unroll
       for (int i = 0; i < P; ++i) a[i] = (i < B && i < cntv) ? make_dc(m[i < B ? i : 0], seg) : 0ull;
-      if (alpha <= 13) {
+      if (alpha <= kBLogChunk) {
         const int g_log = alpha - 5;
         const int wl = g_log < 5 ? g_log : 5;
         for (int l = 0; l < wl; ++l) shfl_merge<P>(a, 1 << l);
@@ -342,7 +389,7 @@ __device__ void process_row(const BatchParams& p, const RowDesc& r, const Smem& 
           }
           __syncthreads();
           const int wps_log = g_log - 5;
-          const int nsub_chunk = (kBT / 32) >> wps_log;
+          const int nsub_chunk = kBWarps >> wps_log;
           if (warp < nsub_chunk) {
             uint64_t b[P];
             const int src = warp * (1 << wps_log) + (lane & ((1 << wps_log) - 1));
@@ -372,8 +419,8 @@ __device__ void process_row(const BatchParams& p, const RowDesc& r, const Smem& 
           if (warp == 0) {
             uint64_t b[P];
 #pragma unroll
-            for (int i = 0; i < P; ++i) b[i] = s_lists[(lane & 7) * P + i];
-            for (int l = 0; l < 3; ++l) shfl_merge<P>(b, 1 << l);
+            for (int i = 0; i < P; ++i) b[i] = s_lists[(lane & (kBWarps - 1)) * P + i];
+            for (int l = 0; l < kBLogWarps; ++l) shfl_merge<P>(b, 1 << l);
             const int64_t sub3 = c >> cps_log;
             if (lane == 0) {
 #pragma unroll
@@ -395,105 +442,164 @@ __device__ void process_row(const BatchParams& p, const RowDesc& r, const Smem& 
       }
     }
     ring.seq = seq0 + static_cast<uint64_t>(nch);
+    phase_mark(p, 0, tmark);
 
     // ------------------------------------------------- 2. threshold ----
     const int dcnt = static_cast<int>(S * B);
     tau = (dcnt >= static_cast<int>(k)) ? block_select32(sm.dkeys, dcnt, k, hist, s_bc) : 0u;
+    phase_mark(p, 1, tmark);
 
     // ------------------------------------------------- 3. filter -------
-    uint16_t* scanl = reinterpret_cast<uint16_t*>(sm.ring + size_t(kBMaxK) * 8);
+    // (a) classify each subrange: read again when its beta-th delegate
+    // exceeds tau (non-delegates may too), else its delegates > tau are
+    // candidates whose positions are resolved in (b).
+    uint16_t* scanl = reinterpret_cast<uint16_t*>(sm.ring + kScanOff);
+    uint64_t* reql = reinterpret_cast<uint64_t*>(sm.ring + kReqOff);
     for (int64_t i0 = 0; i0 < S; i0 += kBT) {
       const int64_t i = i0 + tid;
-      int cls = 0;
-      uint32_t dk[B];
-      uint16_t ds[B];
       if (i < S) {
+        uint32_t dk[B];
+        uint16_t ds[B];
 #pragma unroll
         for (int j = 0; j < B; ++j) {
           dk[j] = sm.dkeys[i * B + j];
           ds[j] = sm.dsegs[i * B + j];
         }
         const int64_t len = imin64(int64_t(1) << alpha, n - (i << alpha));
-        if (dk[0] > tau) cls = (dk[B - 1] > tau && len > B) ? 2 : 1;
-      }
-      if (cls == 2) scanl[atomicAdd(&s_cnt[1], 1u)] = static_cast<uint16_t>(i);
+        if (dk[0] > tau) {
+          if (dk[B - 1] > tau && len > B) {
+            scanl[atomicAdd(&s_cnt[1], 1u)] = static_cast<uint16_t>(i);
+          } else {
 #pragma unroll
-      for (int j = 0; j < B; ++j) {
-        bool has = false;
-        uint64_t v = 0;
-        if (cls == 1 && dk[j] > tau) {
-          // position: the (occ+1)-th key equal to dk[j] in segment ds[j]
-          int occ = 0;
+            for (int j = 0; j < B; ++j) {
+              if (dk[j] > tau) {
+                // the (occ+1)-th key equal to dk[j] in segment ds[j]
+                uint32_t occ = 0;
 #pragma unroll
-          for (int q = 0; q < B; ++q)
-            if (q < j && dk[q] == dk[j] && ds[q] == ds[j]) ++occ;
-          const int64_t lo = (i << alpha) + int64_t(ds[j]) * 32;
-          const int64_t hi = imin64(imin64(n, lo + 32), (i + 1) << alpha);
-          int64_t pos = -1;
-          int cntq = 0;
-          for (int64_t t = lo; t < hi; ++t) {
-            if (map_key<DT>(rk[t]) == dk[j]) {
-              if (cntq == occ) {
-                pos = t;
-                break;
+                for (int q = 0; q < j; ++q) occ += (dk[q] == dk[j] && ds[q] == ds[j]) ? 1u : 0u;
+                const uint64_t lo = static_cast<uint64_t>((i << alpha) + int64_t(ds[j]) * 32);
+                reql[atomicAdd(&s_cnt[3], 1u)] = (uint64_t(dk[j]) << 32) | (uint64_t(occ) << 24) | lo;
               }
-              ++cntq;
             }
           }
-          if (pos < 0) atomicOr(p.err, kErrTieRank);
-          has = true;
-          v = make_comp(dk[j], static_cast<uint32_t>(pos));
         }
-        g_append(sm, scr, p.scap, &s_cnt[0], has, v, p.err);
       }
     }
     __syncthreads();
-    const uint32_t nq = s_cnt[1];
-    const int64_t vtotal = int64_t(nq) << alpha;
-    const int64_t vmask = (int64_t(1) << alpha) - 1;
-    for (int64_t v0 = 0; v0 < vtotal; v0 += kBT) {
-      const int64_t v = v0 + tid;
-      bool has = false;
-      uint64_t cv = 0;
-      if (v < vtotal) {
-        const int64_t gi = (int64_t(scanl[v >> alpha]) << alpha) + (v & vmask);
-        if (gi < n) {
-          const uint32_t x = map_key<DT>(rk[gi]);
-          if (x > tau) {
-            has = true;
-            cv = make_comp(x, static_cast<uint32_t>(gi));
+    // (b) resolve positions: a warp reads a 32-key segment per request
+    // (coalesced), kRU requests in flight per warp
+    {
+      constexpr int kRU = 8;
+      const uint32_t nreq = s_cnt[3];
+      for (uint32_t q0 = warp * kRU; q0 < nreq; q0 += (kBT / 32) * kRU) {
+        uint32_t x[kRU];
+        uint64_t rq[kRU];
+#pragma unroll
+        for (int u = 0; u < kRU; ++u) {
+          rq[u] = (q0 + u < nreq) ? reql[q0 + u] : 0ull;
+          const int64_t lo = static_cast<int64_t>(rq[u] & 0xFFFFFFu);
+          const int64_t hi = imin64(imin64(n, lo + 32), ((lo >> alpha) + 1) << alpha);
+          x[u] = (q0 + u < nreq && lo + lane < hi) ? rk[lo + lane] : 0u;
+          if (!(q0 + u < nreq && lo + lane < hi)) rq[u] |= (1ull << 31);  // lane not in segment
+        }
+#pragma unroll
+        for (int u = 0; u < kRU; ++u) {
+          if (q0 + u >= nreq) break;
+          const uint32_t key = static_cast<uint32_t>(rq[u] >> 32);
+          const bool m = !((rq[u] >> 31) & 1u) && map_key<DT>(x[u]) == key;
+          uint32_t bal = __ballot_sync(0xFFFFFFFFu, m);
+          const uint32_t occ = static_cast<uint32_t>(rq[u] >> 24) & 3u;
+          for (uint32_t t = 0; t < occ; ++t) bal &= bal - 1;
+          if (lane == 0) {
+            const int64_t lo = static_cast<int64_t>(rq[u] & 0xFFFFFFu);
+            int64_t pos = -1;
+            if (bal) pos = lo + (__ffs(bal) - 1);
+            else atomicOr(p.err, kErrTieRank);
+            g_put(sm, scr, p.scap, atomicAdd(&s_cnt[0], 1u),
+                  make_comp(key, static_cast<uint32_t>(pos)), p.err);
           }
         }
       }
-      g_append(sm, scr, p.scap, &s_cnt[0], has, cv, p.err);
+    }
+    // (c) read the listed subranges again: kFU keys per thread in flight
+    {
+      constexpr int kFU = 8;
+      const uint32_t nq = s_cnt[1];
+      const int64_t vtotal = int64_t(nq) << alpha;
+      const int64_t vmask = (int64_t(1) << alpha) - 1;
+      for (int64_t v0 = 0; v0 < vtotal; v0 += int64_t(kBT) * kFU) {
+        uint32_t x[kFU];
+        int64_t gi[kFU];
+#pragma unroll
+        for (int u = 0; u < kFU; ++u) {
+          const int64_t v = v0 + int64_t(u) * kBT + tid;
+          gi[u] = v < vtotal ? (int64_t(scanl[v >> alpha]) << alpha) + (v & vmask) : n;
+          x[u] = gi[u] < n ? rk[gi[u]] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < kFU; ++u) {
+          const uint32_t mk = map_key<DT>(x[u]);
+          const bool has = gi[u] < n && mk > tau;
+          g_append(sm, scr, p.scap, &s_cnt[0], has, make_comp(mk, static_cast<uint32_t>(gi[u])),
+                   p.err);
+        }
+      }
     }
     __syncthreads();
   }
 
-  // ------------------------------------------------- 4. second select ----
-  uint64_t* w = reinterpret_cast<uint64_t*>(sm.ring);  // winners (ring is free now)
+  // ------------------------------------------------- 4. second top-k ----
+  // Winners are built in place over the on-chip candidates.
+  uint64_t* w = sm.gbuf;
   const uint32_t gcnt = s_cnt[0];
+  phase_mark(p, direct ? 6 : 2, tmark);
   if (gcnt >= k) {
-    const uint64_t T = block_select64(sm, scr, gcnt, k, hist, s_bc);
-    for (uint32_t i0 = 0; i0 < gcnt; i0 += kBT) {
-      const uint32_t i = i0 + tid;
-      const bool win = i < gcnt && g_get(sm, scr, i) >= T;
-      const uint32_t bal = __ballot_sync(0xFFFFFFFFu, win);
-      uint32_t base = 0;
-      if (bal) {
-        if (lane == __ffs(bal) - 1) base = atomicAdd(&s_cnt[2], __popc(bal));
-        base = __shfl_sync(0xFFFFFFFFu, base, __ffs(bal) - 1);
+    if (gcnt <= 2 * k && gcnt <= static_cast<uint32_t>(kBGS)) {
+      // few candidates beyond k: sorting them all is cheaper than a select
+      block_sort_desc(w, static_cast<int>(gcnt));
+      phase_mark(p, 3, tmark);
+    } else {
+      const uint64_t T = block_select64(sm, scr, gcnt, k, hist, s_bc);
+      // compaction of the composites >= T into w[0..k): a chunk is read
+      // into registers before any of its winners is written, and a winner's
+      // slot never exceeds the number of candidates read so far
+      constexpr int kCI = 16;
+      for (uint32_t c0 = 0; c0 < gcnt; c0 += kBT * kCI) {
+        uint64_t v[kCI];
+        uint32_t valid = 0;
+#pragma unroll
+        for (int j = 0; j < kCI; ++j) {
+          const uint32_t i = c0 + j * kBT + tid;
+          v[j] = i < gcnt ? g_get(sm, scr, i) : 0ull;
+          valid |= (i < gcnt && v[j] >= T) ? (1u << j) : 0u;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kCI; ++j) {
+          const bool win = (valid >> j) & 1u;
+          const uint32_t bal = __ballot_sync(0xFFFFFFFFu, win);
+          if (!bal) continue;
+          uint32_t base = 0;
+          if (lane == __ffs(bal) - 1) base = atomicAdd(&s_cnt[2], __popc(bal));
+          base = __shfl_sync(0xFFFFFFFFu, base, __ffs(bal) - 1);
+          if (win) {
+            const uint32_t slot = base + __popc(bal & lanemask_lt_b());
+            if (slot < k) w[slot] = v[j];
+            else atomicOr(p.err, kErrOverflowW);
+          }
+        }
+        __syncthreads();
       }
-      if (win) {
-        const uint32_t slot = base + __popc(bal & lanemask_lt_b());
-        if (slot < k) w[slot] = g_get(sm, scr, i);
-        else atomicOr(p.err, kErrOverflowW);
-      }
+      phase_mark(p, 3, tmark);
+      block_sort_desc(w, static_cast<int>(k));
+      phase_mark(p, 5, tmark);
     }
-    __syncthreads();
   } else {
-    // k-th key is tau: G plus the smallest-index ties at tau, in index order
-    for (uint32_t i = tid; i < gcnt; i += kBT) w[i] = g_get(sm, scr, i);
+    // the k-th key is tau: G (all > tau, fewer than k <= kBGS, on chip)
+    // sorted, then the smallest-index ties at tau in index order, which
+    // keeps the whole output sorted
+    block_sort_desc(w, static_cast<int>(gcnt));
+    phase_mark(p, 3, tmark);
     const uint32_t need = k - gcnt;
     uint32_t base = 0;  // ties placed so far (uniform)
     for (int64_t i0 = 0; i0 < S && base < need; i0 += kBT) {
@@ -517,10 +623,10 @@ __device__ void process_row(const BatchParams& p, const RowDesc& r, const Smem& 
       __syncthreads();
       if (tid == 0) s_cnt[3] = 0;
       __syncthreads();
-      uint16_t* lst = reinterpret_cast<uint16_t*>(sm.ring + size_t(kBMaxK) * 8);
+      uint16_t* lst = reinterpret_cast<uint16_t*>(sm.ring);
       if (scan) lst[atomicAdd(&s_cnt[3], 1u)] = static_cast<uint16_t>(tid);
       __syncthreads();
-      uint32_t* cnts = reinterpret_cast<uint32_t*>(sm.ring + size_t(kBMaxK) * 8 + 1024);
+      uint32_t* cnts = reinterpret_cast<uint32_t*>(sm.ring + 1024);
       cnts[tid] = cnt;
       __syncthreads();
       const uint32_t nscan = s_cnt[3];
@@ -586,16 +692,17 @@ __device__ void process_row(const BatchParams& p, const RowDesc& r, const Smem& 
       __syncthreads();
     }
     __syncthreads();
+    phase_mark(p, 4, tmark);
   }
 
-  // ------------------------------------------------- 5. sort and write ----
-  block_sort_desc(w, static_cast<int>(k));
+  // ------------------------------------------------- 5. write ------------
   for (uint32_t j = tid; j < k; j += kBT) {
     const uint64_t c = w[j];
     p.out_keys[r.out + j] = unmap_key(DT, comp_key(c));
     p.out_idx[r.out + j] = static_cast<int32_t>(comp_idx(c));
   }
   __syncthreads();
+  phase_mark(p, 5, tmark);
 }
 
 template <int DT>
@@ -606,7 +713,7 @@ __global__ void __launch_bounds__(kBT, 1) batched_kernel(BatchParams p) {
   __shared__ uint32_t s_bc[4];
   __shared__ uint32_t s_cnt[4];
   __shared__ uint32_t s_row;
-  __shared__ uint64_t s_lists[(kBT / 32) * 4];
+  __shared__ uint64_t s_lists[kBWarps * 4];
   Smem sm;
   sm.ring = bsm;
   sm.dkeys = reinterpret_cast<uint32_t*>(bsm + kRingBytes);
@@ -654,8 +761,8 @@ __global__ void fill_hash_kernel(uint32_t* a, int64_t n, uint64_t seed) {
 
 cudaError_t launch_batched(int dtype, const void* keys, int64_t total, const RowDesc* rows,
                            int32_t nrows, uint32_t* row_ctr, uint64_t* scratch, int64_t scap,
-                           void* out_keys, int32_t* out_idx, uint32_t* err, int grid,
-                           cudaStream_t s) {
+                           void* out_keys, int32_t* out_idx, uint32_t* err,
+                           unsigned long long* phase, int grid, cudaStream_t s) {
   BatchParams p;
   p.keys = static_cast<const uint32_t*>(keys);
   p.total = total;
@@ -667,6 +774,7 @@ cudaError_t launch_batched(int dtype, const void* keys, int64_t total, const Row
   p.out_keys = static_cast<uint32_t*>(out_keys);
   p.out_idx = out_idx;
   p.err = err;
+  p.phase = phase;
   switch (dtype) {
     case DRTOPK_U32:
       cudaFuncSetAttribute(batched_kernel<DRTOPK_U32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -780,6 +888,7 @@ struct drtopk_batch_plan {
   int64_t scap = 0;
   RowDesc* d_rows = nullptr;     // device, processing order
   uint32_t* d_ctl = nullptr;     // [0] row counter, [1] error flags
+  unsigned long long* d_phase = nullptr;  // kBPhases cycle counters
   uint64_t* d_scratch = nullptr;
   std::vector<int32_t> alpha, beta;  // per row, row order
 };
@@ -840,11 +949,15 @@ drtopk_status drtopk_batch_plan_create(drtopk_dtype dtype, const int64_t* row_of
     e = cudaMemcpy(pl->d_rows, rd.data(), rd.size() * sizeof(RowDesc), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&pl->d_ctl), 2 * sizeof(uint32_t));
   if (e == cudaSuccess)
+    e = cudaMalloc(reinterpret_cast<void**>(&pl->d_phase), kBPhases * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(pl->d_phase, 0, kBPhases * sizeof(unsigned long long));
+  if (e == cudaSuccess)
     e = cudaMalloc(reinterpret_cast<void**>(&pl->d_scratch),
                    static_cast<size_t>(pl->grid) * pl->scap * sizeof(uint64_t));
   if (e != cudaSuccess) {
     cudaFree(pl->d_rows);
     cudaFree(pl->d_ctl);
+    cudaFree(pl->d_phase);
     cudaFree(pl->d_scratch);
     delete pl;
     return e == cudaErrorMemoryAllocation ? DRTOPK_ERR_NOMEM : DRTOPK_ERR_CUDA;
@@ -861,7 +974,8 @@ drtopk_status drtopk_batch_plan_run(drtopk_batch_plan* pl, const void* keys, voi
   cudaError_t e = cudaMemsetAsync(pl->d_ctl, 0, 2 * sizeof(uint32_t), s);
   if (e == cudaSuccess)
     e = launch_batched(pl->dtype, keys, pl->total, pl->d_rows, pl->rows, pl->d_ctl,
-                       pl->d_scratch, pl->scap, out_keys, out_idx, pl->d_ctl + 1, pl->grid, s);
+                       pl->d_scratch, pl->scap, out_keys, out_idx, pl->d_ctl + 1, pl->d_phase,
+                       pl->grid, s);
   return e == cudaSuccess ? DRTOPK_OK : (e == cudaErrorMemoryAllocation ? DRTOPK_ERR_NOMEM : DRTOPK_ERR_CUDA);
 }
 
@@ -884,11 +998,25 @@ drtopk_status drtopk_batch_plan_params(const drtopk_batch_plan* pl, int32_t* alp
   return DRTOPK_OK;
 }
 
+drtopk_status drtopk_batch_plan_phase_cycles(drtopk_batch_plan* pl, uint64_t* out, int reset,
+                                             void* stream) {
+  if (!pl || !out) return DRTOPK_ERR_INVALID;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned long long h[kBPhases];
+  cudaError_t e = cudaMemcpyAsync(h, pl->d_phase, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && reset) e = cudaMemsetAsync(pl->d_phase, 0, sizeof(h), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return DRTOPK_ERR_CUDA;
+  for (int i = 0; i < kBPhases; ++i) out[i] = h[i];
+  return DRTOPK_OK;
+}
+
 drtopk_status drtopk_batch_plan_destroy(drtopk_batch_plan* pl) {
   if (!pl) return DRTOPK_ERR_INVALID;
   cudaDeviceSynchronize();
   cudaFree(pl->d_rows);
   cudaFree(pl->d_ctl);
+  cudaFree(pl->d_phase);
   cudaFree(pl->d_scratch);
   delete pl;
   return DRTOPK_OK;

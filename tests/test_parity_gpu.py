@@ -250,3 +250,26 @@ def test_many_distinct_calls_evict_cleanly():
             rk, ri = oracle.topk(bits, oracle.U32, k)
             assert np.array_equal(host_bits(ok), rk) and np.array_equal(oi.cpu().numpy(), ri)
     torch.cuda.synchronize()
+
+
+def test_queries_inside_a_user_graph():
+    """Calls on a stream under capture launch kernel by kernel into the
+    caller's graph (workspace as graph allocation nodes)."""
+    n, k = 200003, 513
+    x = torch.empty(n, dtype=torch.int32, device="cuda")
+    ok = torch.empty(k, dtype=torch.int32, device="cuda")
+    oi = torch.empty(k, dtype=torch.int32, device="cuda")
+    kt = torch.empty(1, dtype=torch.int32, device="cuda")
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        drtopk.drtopk_topk(x, k, out_keys=ok, out_idx=oi, dtype="u32", stream=s)
+        drtopk.drtopk_kth(x, 7, out=kt, dtype="u32", stream=s)
+    for it, kind in enumerate(["uniform", "few", "desc"]):
+        bits = make(kind, n, 70 + it, "u32")
+        x.copy_(torch.from_numpy(bits.view(np.int32)))
+        g.replay()
+        torch.cuda.synchronize()
+        rk, ri = oracle.topk(bits, oracle.U32, k)
+        assert np.array_equal(host_bits(ok), rk) and np.array_equal(oi.cpu().numpy(), ri), kind
+        assert int(host_bits(kt)[0]) == oracle.kth(bits, oracle.U32, 7)
