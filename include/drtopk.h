@@ -204,14 +204,28 @@ drtopk_status drtopk_topk_host(const void* keys, drtopk_dtype dtype,
  * aligned; rows may start at any element.
  *
  * Per-row parameters: rows of at most 4096 keys are selected directly (no
- * delegates). Longer rows take (alpha, beta) from the tuning table entry of
- * (floor(log2 n_r), floor(log2 k_r)) when one is set (drtopk_tune_set,
- * drtopk_autotune_batched), else alpha by Rule 4 / Eq. 9 and beta = 2,
- * lowered while fewer than 2k_r delegates would exist; alpha is then raised
- * to at least 5 and until beta * ceil(n_r / 2^alpha) <= 8192 (the delegates
- * fit on chip).
+ * delegates: the row is held on chip and radix-selected). Longer rows take
+ * (alpha, beta) from the tuning table entry of (floor(log2 n_r),
+ * floor(log2 k_r)) when one is set (drtopk_tune_set,
+ * drtopk_autotune_batched; alpha = 1 there means the direct select), else
+ * the direct select when the row fits on chip (direct_max_onchip of
+ * drtopk_batch_limits) and 2 * ceil(n_r / 32) < 2k_r (even one subrange per
+ * 32 keys gives too few delegates), else alpha by Rule 4 / Eq. 9 and
+ * beta = 2, lowered while fewer than 2k_r delegates would exist. alpha is
+ * then raised to at least 5 and until beta * ceil(n_r / 2^alpha) <=
+ * max_delegates (the delegates fit on chip).
  */
 typedef struct drtopk_batch_plan drtopk_batch_plan;
+
+/* Limits of the batched path (host only; any pointer may be NULL):
+ * max_k = 4096, max_row = 2^24 keys, direct_max = 4096 (rows up to this
+ * length always skip the delegates), direct_max_onchip = longest row the
+ * direct select can hold on chip, max_delegates = delegate slots per row
+ * kept on chip, onchip_candidates = candidates kept on chip before
+ * spilling to the plan's device scratch. */
+drtopk_status drtopk_batch_limits(int32_t* max_k, int64_t* max_row, int32_t* direct_max,
+                                  int32_t* direct_max_onchip, int32_t* max_delegates,
+                                  int32_t* onchip_candidates);
 
 /*
  * Builds a reusable plan for a fixed row layout: per-row parameters, the
@@ -219,7 +233,8 @@ typedef struct drtopk_batch_plan drtopk_batch_plan;
  * memory (sized by the bound |{x > tau}| < floor((k-1)/beta) 2^alpha + k of
  * every row). alpha / beta > 0 force the parameters of every row longer
  * than 4096 keys (alpha in [5, 16], beta in [1, 4]; the on-chip clamp still
- * applies); 0 picks them as described above. Allocates device memory;
+ * applies; alpha = 1 selects directly every row that fits on chip); 0 picks
+ * them as described above. Allocates device memory;
  * synchronous. *out receives the plan (release with
  * drtopk_batch_plan_destroy).
  */
@@ -249,12 +264,13 @@ drtopk_status drtopk_batch_plan_params(const drtopk_batch_plan* plan, int32_t* a
 /*
  * Device cycles (clock64 of the first thread of each CTA, summed over CTAs
  * and over runs since the last reset) spent in each step of the batched
- * kernel: out[0] delegate pass, [1] threshold select, [2] filter, [3] second
- * select (or sort of all candidates), [4] tie ranking, [5] final sort and
- * output, [6] loading rows of the direct select. out: HOST, 7 entries.
+ * kernel. Rows with delegates: out[0] delegate pass, [1] threshold select,
+ * [2] filter, [3] second select (or sort of all candidates), [4] tie
+ * ranking, [5] final sort and output. Directly selected rows: [6] load,
+ * [7] select, [8] collection, [9] sort and output. out: HOST, 10 entries.
  * reset != 0 clears the counters. Synchronizes `stream`.
  */
-#define DRTOPK_BATCH_PHASES 7
+#define DRTOPK_BATCH_PHASES 10
 drtopk_status drtopk_batch_plan_phase_cycles(drtopk_batch_plan* plan, uint64_t* out,
                                              int reset, void* stream);
 
@@ -270,7 +286,8 @@ drtopk_status drtopk_topk_batched(const void* keys, drtopk_dtype dtype,
 /*
  * The per-shape tuning table of the batched path (process-wide), indexed by
  * log2n in [10, 31] and log2k in [0, 12]. alpha = 0 (the initial state)
- * means Rule 4; set alpha in [5, 16], beta in [1, 4]. Host only.
+ * means the default choice; set alpha in [5, 16] with beta in [1, 4], or
+ * alpha = 1 for the direct select. Host only.
  */
 drtopk_status drtopk_tune_get(int32_t log2n, int32_t log2k, int* alpha, int* beta);
 drtopk_status drtopk_tune_set(int32_t log2n, int32_t log2k, int alpha, int beta);

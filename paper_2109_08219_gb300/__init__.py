@@ -27,7 +27,7 @@ STATUS = ["DRTOPK_OK", "DRTOPK_ERR_INVALID", "DRTOPK_ERR_K", "DRTOPK_ERR_DTYPE",
 NUM_STAGES = 6
 STAGE_NAMES = ["delegate", "threshold", "filter", "ties", "second_select", "sort"]
 BATCH_PHASES = ["delegate", "threshold", "filter", "second_select", "ties", "sort_output",
-                "direct_load"]
+                "direct_load", "direct_select", "direct_collect", "direct_sort_output"]
 
 
 class DrTopkError(RuntimeError):
@@ -93,6 +93,7 @@ def lib():
         L.drtopk_batch_plan_destroy.argtypes = [p]
         L.drtopk_batch_plan_phase_cycles.argtypes = [p, ctypes.POINTER(ctypes.c_uint64), i32, p]
         L.drtopk_topk_batched.argtypes = [p, i32, pi64, pi32, i32, p, p, p]
+        L.drtopk_batch_limits.argtypes = [pi32, pi64, pi32, pi32, pi32, pi32]
         L.drtopk_tune_get.argtypes = [i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
         L.drtopk_tune_set.argtypes = [i32, i32, i32, i32]
         L.drtopk_autotune_batched.argtypes = [i32, i32, i32, i32, p]
@@ -101,7 +102,7 @@ def lib():
                    "drtopk_profile_end", "drtopk_batch_plan_create", "drtopk_batch_plan_run",
                    "drtopk_batch_plan_status", "drtopk_batch_plan_params",
                    "drtopk_batch_plan_destroy", "drtopk_batch_plan_phase_cycles",
-                   "drtopk_topk_batched", "drtopk_tune_get",
+                   "drtopk_topk_batched", "drtopk_batch_limits", "drtopk_tune_get",
                    "drtopk_tune_set", "drtopk_autotune_batched"):
             getattr(L, fn).restype = i32
         _lib = L
@@ -368,6 +369,18 @@ def drtopk_topk_batched(keys, row_off, ks, dtype=None, stream=None):
         kk.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), int(kk.size), _dev(out_keys),
         _dev(out_idx), _stream(stream)), "drtopk_topk_batched")
     return out_keys, out_idx
+
+
+def batch_limits():
+    """Limits of the batched path (drtopk_batch_limits) as a dict."""
+    mk, mr, dm, do, md, oc = (ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32(),
+                              ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32())
+    _check(lib().drtopk_batch_limits(ctypes.byref(mk), ctypes.byref(mr), ctypes.byref(dm),
+                                     ctypes.byref(do), ctypes.byref(md), ctypes.byref(oc)),
+           "drtopk_batch_limits")
+    return {"max_k": mk.value, "max_row": mr.value, "direct_max": dm.value,
+            "direct_max_onchip": do.value, "max_delegates": md.value,
+            "onchip_candidates": oc.value}
 
 
 def tune_get(log2n, log2k):

@@ -42,22 +42,27 @@ namespace {
 constexpr int kBT = 512;              // threads per CTA (one CTA per SM)
 constexpr int kBWarps = kBT / 32;
 constexpr int kBLogWarps = 4;
-constexpr int kBLogChunk = 14;        // keys per ring stage: 32 per thread
+constexpr int kBLogChunk = kBLogWarps + 10;          // keys per ring stage: 32 per thread
 constexpr int kBChunk = 1 << kBLogChunk;
 constexpr int kBStages = 2;
 static_assert((1 << kBLogWarps) == kBWarps && kBChunk == kBT * 32, "chunk geometry");
 constexpr int kBStageBytes = kBChunk * 4 + 128;  // + room for the alignment shift
 constexpr int kBDMax = 8192;          // delegate slots (S * beta) kept on chip
-constexpr int kBGS = 4096;            // candidates kept on chip
+constexpr int kBGS = 4096;            // candidates kept on chip (more spill to scratch)
 constexpr int kBMaxK = 4096;          // largest k_r of the batched path
-constexpr int kBDirect = 4096;        // rows up to this size: direct select
+constexpr int kBDirect = 4096;        // rows up to this size: always direct select
+constexpr int kBDirectMax = kBStages * kBChunk;  // longest row a direct select holds on chip
 constexpr int64_t kBMaxN = int64_t(1) << 24;  // longest row of the batched path
+constexpr int64_t kBKeepL2 = int64_t(1) << 20;  // rows up to 1 MB: normal L2 priority
 
 constexpr size_t kRingBytes = size_t(kBStages) * kBStageBytes;
-// the ring is free after the delegate pass; the filter keeps its lists there
+// The ring is free after the delegate pass. The filter keeps its lists
+// there; then the winners (up to kBMaxK) and the tie ranking's lists.
 constexpr size_t kScanOff = 0;                          // u16 subrange list, <= kBDMax
 constexpr size_t kReqOff = size_t(kBDMax) * 2;          // u64 resolve requests, <= kBDMax
+constexpr size_t kTieOff = size_t(kBMaxK) * 8;          // u16 + 2 x u32 per thread
 static_assert(kReqOff + size_t(kBDMax) * 8 <= kRingBytes, "filter lists exceed the ring");
+static_assert(kTieOff + size_t(kBT) * 10 <= kRingBytes, "tie lists exceed the ring");
 constexpr size_t kDynSmem = kRingBytes + size_t(kBDMax) * 4 + size_t(kBDMax) * 2 + size_t(kBGS) * 8;
 
 struct BatchParams {
@@ -74,11 +79,11 @@ struct BatchParams {
   unsigned long long* phase;  // kBPhases cycle counters (thread 0 of each CTA)
 };
 
-// Cycle counters of the batched kernel, summed over CTAs: 0 delegate pass,
-// 1 threshold select, 2 filter, 3 second select (or sort of all
-// candidates), 4 tie ranking, 5 final sort and output, 6 loading the rows
-// of the direct select.
-constexpr int kBPhases = 7;
+// Cycle counters of the batched kernel, summed over CTAs. Rows with
+// delegates: 0 delegate pass, 1 threshold select, 2 filter, 3 second select
+// (or sort of all candidates), 4 tie ranking, 5 final sort and output.
+// Direct rows: 6 load, 7 select, 8 collection, 9 sort and output.
+constexpr int kBPhases = 10;
 
 __device__ __forceinline__ void phase_mark(const BatchParams& p, int ph, long long& tmark) {
   if (threadIdx.x == 0) {
@@ -105,7 +110,8 @@ __device__ __forceinline__ uint32_t lanemask_lt_b() {
 struct Ring {
   uint64_t* bar;      // kBStages mbarriers
   uint64_t seq;       // chunks issued by this CTA so far (all rows)
-  uint64_t pol;
+  uint64_t pol_first;   // rows read once (long rows)
+  uint64_t pol_normal;  // rows read again by the filter while still in L2
 };
 
 // Issues chunk c of the row into a stage buffer: one bulk copy from the
@@ -176,30 +182,6 @@ __device__ __forceinline__ void bucket_search(const uint32_t* hist, uint32_t kre
   }
 }
 
-// k-th largest (1-based rank krem) of the 32-bit keys a[0..cnt) in shared
-// memory (delegates). Returns the key.
-__device__ uint32_t block_select32(const uint32_t* a, int cnt, uint32_t krem, uint32_t* hist,
-                                   uint32_t* s_bc) {
-  uint32_t prefix = 0;
-  for (int pass = 0; pass < 4; ++pass) {
-    for (int i = threadIdx.x; i < 256; i += kBT) hist[i] = 0;
-    __syncthreads();
-    const uint32_t mask = pass == 0 ? 0u : (0xFFFFFFFFu << (32 - 8 * pass));
-    const int sh = 24 - 8 * pass;
-    for (int i = threadIdx.x; i < cnt; i += kBT) {
-      const uint32_t x = a[i];
-      if ((x & mask) == (prefix & mask)) atomicAdd(&hist[(x >> sh) & 255u], 1u);
-    }
-    __syncthreads();
-    if (threadIdx.x < 32) bucket_search(hist, krem, s_bc);
-    __syncthreads();
-    prefix |= s_bc[0] << sh;
-    krem = s_bc[1];
-    __syncthreads();
-  }
-  return prefix;
-}
-
 // Logical candidate array: [0, kBGS) in shared memory, then the CTA's
 // scratch.
 __device__ __forceinline__ uint64_t g_get(const Smem& sm, const uint64_t* scr, uint32_t i) {
@@ -224,35 +206,102 @@ __device__ __forceinline__ void g_append(const Smem& sm, uint64_t* scr, int64_t 
   if (has) g_put(sm, scr, scap, base + __popc(bal & lanemask_lt_b()), v, err);
 }
 
-// k-th largest composite of the logical G (cnt entries): returns the
-// threshold T such that exactly k composites are >= T.
-__device__ uint64_t block_select64(const Smem& sm, const uint64_t* scr, uint32_t cnt, uint32_t k,
-                                   uint32_t* hist, uint32_t* s_bc) {
-  uint64_t prefix = 0;
-  uint32_t krem = k;
-  for (int pass = 0; pass < 8; ++pass) {
-    for (int i = threadIdx.x; i < 256; i += kBT) hist[i] = 0;
-    __syncthreads();
-    const uint64_t mask = pass == 0 ? 0ull : (~0ull << (64 - 8 * pass));
-    const int sh = 56 - 8 * pass;
-    for (uint32_t i = threadIdx.x; i < cnt; i += kBT) {
-      const uint64_t x = g_get(sm, scr, i);
-      if ((x & mask) == (prefix & mask)) atomicAdd(&hist[static_cast<uint32_t>(x >> sh) & 255u], 1u);
-    }
-    __syncthreads();
-    if (threadIdx.x < 32) bucket_search(hist, krem, s_bc);
-    __syncthreads();
-    prefix |= static_cast<uint64_t>(s_bc[0]) << sh;
-    krem = s_bc[1];
-    const bool done = s_bc[2] == krem;  // the whole bucket is needed
-    __syncthreads();
-    if (done) break;
+template <class V>
+__device__ __forceinline__ V warp_min(V v) {
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    const V t = __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    v = t < v ? t : v;
   }
-  return prefix;
+  return v;
+}
+template <class V>
+__device__ __forceinline__ V warp_max(V v) {
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    const V t = __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    v = t > v ? t : v;
+  }
+  return v;
 }
 
-// Bitonic sort (descending) of w[0..cnt) in shared memory, cnt <= kBGS;
-// pads w[cnt..P) with 0 (P = next power of two), which sorts last.
+template <class V>
+struct SelResult {
+  V value;        // exact mode: the krem-th largest; else a threshold T
+  uint32_t need;  // exact mode: values equal to it among the top krem
+};
+
+// The krem-th largest of cnt values get(i) (MSD radix select, Sec. 4.1's
+// digits of 8 bits). When every value of the selected bucket is among the
+// top krem the search stops: in exact mode the answer is the bucket's
+// minimum (found by one more pass); otherwise the returned T (the bucket's
+// prefix, low bits 0) still has exactly krem values >= T when the values
+// are distinct. mm: one 64-bit shared word.
+template <class V, bool kExact, class Get>
+__device__ SelResult<V> block_select(Get get, uint32_t cnt, uint32_t krem, uint32_t* hist,
+                                     uint32_t* s_bc, unsigned long long* mm) {
+  constexpr int kBits = sizeof(V) * 8;
+  const int tid = threadIdx.x;
+  int hb = kBits;  // bits above hb are fixed in prefix
+  V prefix = 0;
+  while (hb > 0) {
+    const int width = hb < 8 ? hb : 8;
+    const int sh = hb - width;
+    for (int i = tid; i < 256; i += kBT) hist[i] = 0;
+    __syncthreads();
+    for (uint32_t i = tid; i < cnt; i += kBT) {
+      const V x = get(i);
+      if (hb >= kBits || (x >> hb) == (prefix >> hb))
+        atomicAdd(&hist[static_cast<uint32_t>(x >> sh) & ((1u << width) - 1u)], 1u);
+    }
+    __syncthreads();
+    if (tid < 32) bucket_search(hist, krem, s_bc);
+    __syncthreads();
+    prefix |= static_cast<V>(s_bc[0]) << sh;
+    krem = s_bc[1];
+    const uint32_t hd = s_bc[2];
+    __syncthreads();
+    hb = sh;
+    if (hd == krem && hb > 0) {
+      if constexpr (!kExact) {
+        return {prefix, 0u};
+      } else {
+        // the whole bucket is among the top: the answer is its minimum,
+        // needed as many times as it occurs
+        if (tid == 0) {
+          mm[0] = ~0ull;
+          s_bc[3] = 0;
+        }
+        __syncthreads();
+        V lo = static_cast<V>(~V(0));
+        for (uint32_t i = tid; i < cnt; i += kBT) {
+          const V x = get(i);
+          if ((x >> hb) == (prefix >> hb)) lo = x < lo ? x : lo;
+        }
+        lo = warp_min(lo);
+        if ((tid & 31) == 0) atomicMin(&mm[0], static_cast<unsigned long long>(lo));
+        __syncthreads();
+        const V v = static_cast<V>(mm[0]);
+        uint32_t c = 0;
+        for (uint32_t i = tid; i < cnt; i += kBT) c += get(i) == v ? 1u : 0u;
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+        if ((tid & 31) == 0) atomicAdd(&s_bc[3], c);
+        __syncthreads();
+        const uint32_t need = s_bc[3];
+        __syncthreads();
+        return {v, need};
+      }
+    }
+  }
+  return {prefix, krem};
+}
+
+// Bitonic sort (descending) of w[0..cnt) in shared memory, cnt <= kBMaxK;
+// pads w[cnt..P) with 0 (P = next power of two), which sorts last. The
+// pairs q of a warp in one sweep, [32m, 32m + 32), touch only elements
+// [64m, 64m + 64) while the stride is at most 32, so such consecutive
+// stages need only the warp in step.
 __device__ void block_sort_desc(uint64_t* w, int cnt) {
   int P = 1;
   while (P < cnt) P <<= 1;
@@ -271,15 +320,136 @@ __device__ void block_sort_desc(uint64_t* w, int cnt) {
           w[j] = a;
         }
       }
-      __syncthreads();
+      const int next = stride > 1 ? stride >> 1 : size;  // stride of the next stage
+      if (stride > 32 || next > 32) __syncthreads();
+      else __syncwarp();
     }
   }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------ direct row --
+// Rows of at most kBDirectMax keys where delegates cannot reduce the work
+// (short rows, or beta * n / 32 < 2k): the row is copied into the ring and
+// the k-th largest key is found by an MSD radix select over it (Sec. 4.1's
+// 8-bit digits); then one ordered pass collects the keys above it and the
+// smallest-index keys equal to it, which go straight to the output.
+template <int DT>
+__device__ void direct_row(const BatchParams& p, const RowDesc& r, const Smem& sm, Ring& ring,
+                           uint32_t* hist, uint32_t* s_bc, uint32_t* s_cnt,
+                           unsigned long long* mm, long long& tmark) {
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
+  const int64_t n = r.n;
+  const uint32_t k = static_cast<uint32_t>(r.k);
+  const int nch = static_cast<int>((n + kBChunk - 1) / kBChunk);  // <= kBStages
+  const uint64_t seq0 = ring.seq;
+  if (tid == 0) {
+    for (int c = 0; c < nch; ++c) {
+      const uint64_t q = seq0 + c;
+      issue_row_chunk(p, r, c, sm.ring + (q % kBStages) * kBStageBytes, &ring.bar[q % kBStages],
+                      ring.pol_first);
+    }
+  }
+  const uint32_t* base[kBStages];
+  bool ok = true;
+#pragma unroll
+  for (int c = 0; c < kBStages; ++c) {
+    const uint64_t q = seq0 + c;
+    const int shift = static_cast<int>(((r.start + int64_t(c) * kBChunk) * 4 & 15) / 4);
+    base[c] = reinterpret_cast<const uint32_t*>(sm.ring + (q % kBStages) * kBStageBytes) + shift;
+    if (c < nch) ok = mbar_wait_bounded(&ring.bar[q % kBStages], static_cast<uint32_t>((q / kBStages) & 1)) && ok;
+  }
+  ring.seq = seq0 + static_cast<uint64_t>(nch);
+  if (__syncthreads_or(!ok)) {
+    if (tid == 0) atomicOr(p.err, kErrTimeout);
+    return;
+  }
+  static_assert(kBStages == 2, "a direct row spans at most two stage buffers");
+  const uint32_t* b0 = base[0];
+  const uint32_t* b1 = base[1];
+  auto key_at = [&](int64_t i) -> uint32_t {
+    return map_key<DT>((i < kBChunk ? b0 : b1)[i & (kBChunk - 1)]);
+  };
+  phase_mark(p, 6, tmark);
+
+  // k-th largest mapped key: four 8-bit digit passes over the row on chip
+  const SelResult<uint32_t> sel = block_select<uint32_t, true>(
+      [&](uint32_t i) { return key_at(i); }, static_cast<uint32_t>(n), k, hist, s_bc, mm);
+  const uint32_t kth = sel.value;
+  const uint32_t need = sel.need;  // keys equal to kth among the top k
+  phase_mark(p, 7, tmark);
+  const uint32_t gt = k - need; // keys above kth
+
+  // ordered pass: keys > kth to gbuf (any order), ties in index order to
+  // the output after the gt largest
+  constexpr int kU = 8;
+  uint32_t* wt = hist;  // per-warp tie counts
+  uint32_t tbase = 0;
+  const uint32_t tie_raw = unmap_key(DT, kth);
+  for (int64_t t0 = 0; t0 < n; t0 += int64_t(kBT) * kU) {
+    const int64_t wb = t0 + int64_t(warp) * 32 * kU;
+    uint32_t bal[kU];
+    uint32_t wcount = 0;
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int64_t i = wb + u * 32 + lane;
+      const uint32_t x = i < n ? key_at(i) : 0u;
+      const bool big = i < n && x > kth;
+      const uint32_t bb = __ballot_sync(0xFFFFFFFFu, big);
+      if (bb) {
+        uint32_t b0 = 0;
+        if (lane == __ffs(bb) - 1) b0 = atomicAdd(&s_cnt[0], __popc(bb));
+        b0 = __shfl_sync(0xFFFFFFFFu, b0, __ffs(bb) - 1);
+        if (big) {
+          const uint32_t slot = b0 + __popc(bb & lanemask_lt_b());
+          if (slot < gt) sm.gbuf[slot] = make_comp(x, static_cast<uint32_t>(i));
+          else atomicOr(p.err, kErrOverflowW);
+        }
+      }
+      bal[u] = __ballot_sync(0xFFFFFFFFu, i < n && x == kth);
+      wcount += __popc(bal[u]);
+    }
+    if (lane == 0) wt[warp] = wcount;
+    __syncthreads();
+    uint32_t pre = tbase, tot = 0;
+#pragma unroll
+    for (int q = 0; q < kBWarps; ++q) {
+      const uint32_t c = wt[q];
+      pre += q < warp ? c : 0u;
+      tot += c;
+    }
+    if (pre < tbase + need) {
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const uint32_t rank = pre + __popc(bal[u] & lanemask_lt_b());
+        if (((bal[u] >> lane) & 1u) && rank < need) {
+          p.out_keys[r.out + gt + rank] = tie_raw;
+          p.out_idx[r.out + gt + rank] = static_cast<int32_t>(wb + u * 32 + lane);
+        }
+        pre += __popc(bal[u]);
+      }
+    }
+    tbase += tot;
+    __syncthreads();
+  }
+  phase_mark(p, 8, tmark);
+  block_sort_desc(sm.gbuf, static_cast<int>(gt));
+  for (uint32_t j = tid; j < gt; j += kBT) {
+    const uint64_t c = sm.gbuf[j];
+    p.out_keys[r.out + j] = unmap_key(DT, comp_key(c));
+    p.out_idx[r.out + j] = static_cast<int32_t>(comp_idx(c));
+  }
+  __syncthreads();
+  phase_mark(p, 9, tmark);
 }
 
 // ------------------------------------------------------------ one row ----
 template <int DT, int B>
 __device__ void process_row(const BatchParams& p, const RowDesc& r, const Smem& sm, Ring& ring,
-                            uint32_t* hist, uint32_t* s_bc, uint32_t* s_cnt, uint64_t* s_lists) {
+                            uint32_t* hist, uint32_t* s_bc, uint32_t* s_cnt, uint64_t* s_lists,
+                            unsigned long long* mm) {
   constexpr int P = Pow2<B>::v;
   const int tid = threadIdx.x;
   const int lane = tid & 31;
@@ -304,25 +474,23 @@ __device__ void process_row(const BatchParams& p, const RowDesc& r, const Smem& 
   long long tmark = clock64();
   int64_t S = 0;
   uint32_t tau = 0;
-  bool direct = (alpha == 0);
-  if (direct) {
-    // small row: every key is a candidate
-    for (int64_t i = tid; i < n; i += kBT)
-      g_put(sm, scr, p.scap, static_cast<uint32_t>(i), make_comp(map_key<DT>(rk[i]), uint32_t(i)),
-            p.err);
-    if (tid == 0) s_cnt[0] = static_cast<uint32_t>(n);
-    __syncthreads();
-  } else {
+  if (alpha == 0) {
+    direct_row<DT>(p, r, sm, ring, hist, s_bc, s_cnt, mm, tmark);
+    return;
+  }
+  {
     // ---------------------------------------------- 1. delegate pass ----
     S = (n + (int64_t(1) << alpha) - 1) >> alpha;
     const int64_t nch = (n + kBChunk - 1) / kBChunk;
     const int cps_log = alpha > kBLogChunk ? alpha - kBLogChunk : 0;
     const uint64_t seq0 = ring.seq;
+    // rows up to kBKeepL2 bytes stay in L2 for the filter's second reads
+    const uint64_t pol = n * 4 <= kBKeepL2 ? ring.pol_normal : ring.pol_first;
     if (tid == 0) {
       for (int64_t c = 0; c < kBStages && c < nch; ++c) {
         const uint64_t q = seq0 + c;
         issue_row_chunk(p, r, c, sm.ring + (q % kBStages) * kBStageBytes, &ring.bar[q % kBStages],
-                        ring.pol);
+                        pol);
       }
     }
     uint64_t run[P];
@@ -353,6 +521,7 @@ __device__ void process_row(const BatchParams& p, const RowDesc& r, const Smem& 
       for (int i = 0; i < B; ++i) m[i] = 0;
       int cntv;
       if (valid >= 32) {
+        // rotated reads: lane l starts at word l of its 32 (no bank conflicts)
 #pragma unroll
         for (int j = 0; j < 32; ++j) insert1<DT, B>(m, cb[shift + tid * 32 + ((j + lane) & 31)]);
         cntv = 32;
@@ -438,7 +607,7 @@ __device__ void process_row(const BatchParams& p, const RowDesc& r, const Smem& 
       if (tid == 0 && c + kBStages < nch) {
         const uint64_t qn = q + kBStages;
         issue_row_chunk(p, r, c + kBStages, sm.ring + (qn % kBStages) * kBStageBytes,
-                        &ring.bar[qn % kBStages], ring.pol);
+                        &ring.bar[qn % kBStages], pol);
       }
     }
     ring.seq = seq0 + static_cast<uint64_t>(nch);
@@ -446,7 +615,11 @@ __device__ void process_row(const BatchParams& p, const RowDesc& r, const Smem& 
 
     // ------------------------------------------------- 2. threshold ----
     const int dcnt = static_cast<int>(S * B);
-    tau = (dcnt >= static_cast<int>(k)) ? block_select32(sm.dkeys, dcnt, k, hist, s_bc) : 0u;
+    if (dcnt >= static_cast<int>(k)) {
+      const uint32_t* dk = sm.dkeys;
+      tau = block_select<uint32_t, true>([dk](uint32_t i) { return dk[i]; },
+                                         static_cast<uint32_t>(dcnt), k, hist, s_bc, mm).value;
+    }
     phase_mark(p, 1, tmark);
 
     // ------------------------------------------------- 3. filter -------
@@ -523,25 +696,26 @@ __device__ void process_row(const BatchParams& p, const RowDesc& r, const Smem& 
     }
     // (c) read the listed subranges again: kFU keys per thread in flight
     {
-      constexpr int kFU = 8;
+      constexpr int kFU = 16;
       const uint32_t nq = s_cnt[1];
       const int64_t vtotal = int64_t(nq) << alpha;
       const int64_t vmask = (int64_t(1) << alpha) - 1;
+      const uint32_t nn = static_cast<uint32_t>(n);
       for (int64_t v0 = 0; v0 < vtotal; v0 += int64_t(kBT) * kFU) {
         uint32_t x[kFU];
-        int64_t gi[kFU];
+        uint32_t gi[kFU];
 #pragma unroll
         for (int u = 0; u < kFU; ++u) {
           const int64_t v = v0 + int64_t(u) * kBT + tid;
-          gi[u] = v < vtotal ? (int64_t(scanl[v >> alpha]) << alpha) + (v & vmask) : n;
-          x[u] = gi[u] < n ? rk[gi[u]] : 0u;
+          gi[u] = v < vtotal ? static_cast<uint32_t>((int64_t(scanl[v >> alpha]) << alpha) + (v & vmask))
+                             : nn;
+          x[u] = gi[u] < nn ? rk[gi[u]] : 0u;
         }
 #pragma unroll
         for (int u = 0; u < kFU; ++u) {
           const uint32_t mk = map_key<DT>(x[u]);
-          const bool has = gi[u] < n && mk > tau;
-          g_append(sm, scr, p.scap, &s_cnt[0], has, make_comp(mk, static_cast<uint32_t>(gi[u])),
-                   p.err);
+          const bool has = gi[u] < nn && mk > tau;
+          g_append(sm, scr, p.scap, &s_cnt[0], has, make_comp(mk, gi[u]), p.err);
         }
       }
     }
@@ -549,55 +723,46 @@ __device__ void process_row(const BatchParams& p, const RowDesc& r, const Smem& 
   }
 
   // ------------------------------------------------- 4. second top-k ----
-  // Winners are built in place over the on-chip candidates.
-  uint64_t* w = sm.gbuf;
+  uint64_t* w = reinterpret_cast<uint64_t*>(sm.ring);  // winners (the ring is free)
   const uint32_t gcnt = s_cnt[0];
-  phase_mark(p, direct ? 6 : 2, tmark);
+  phase_mark(p, 2, tmark);
   if (gcnt >= k) {
-    if (gcnt <= 2 * k && gcnt <= static_cast<uint32_t>(kBGS)) {
+    if (gcnt <= 2 * k && gcnt <= static_cast<uint32_t>(kBMaxK)) {
       // few candidates beyond k: sorting them all is cheaper than a select
+      for (uint32_t i = tid; i < gcnt; i += kBT) w[i] = g_get(sm, scr, i);
       block_sort_desc(w, static_cast<int>(gcnt));
       phase_mark(p, 3, tmark);
     } else {
-      const uint64_t T = block_select64(sm, scr, gcnt, k, hist, s_bc);
-      // compaction of the composites >= T into w[0..k): a chunk is read
-      // into registers before any of its winners is written, and a winner's
-      // slot never exceeds the number of candidates read so far
-      constexpr int kCI = 16;
-      for (uint32_t c0 = 0; c0 < gcnt; c0 += kBT * kCI) {
-        uint64_t v[kCI];
-        uint32_t valid = 0;
-#pragma unroll
-        for (int j = 0; j < kCI; ++j) {
-          const uint32_t i = c0 + j * kBT + tid;
-          v[j] = i < gcnt ? g_get(sm, scr, i) : 0ull;
-          valid |= (i < gcnt && v[j] >= T) ? (1u << j) : 0u;
+      const uint64_t T = block_select<uint64_t, false>(
+          [&sm, scr](uint32_t i) { return g_get(sm, scr, i); }, gcnt, k, hist, s_bc, mm).value;
+      for (uint32_t i0 = 0; i0 < gcnt; i0 += kBT) {
+        const uint32_t i = i0 + tid;
+        uint64_t v = 0;
+        bool win = false;
+        if (i < gcnt) {
+          v = g_get(sm, scr, i);
+          win = v >= T;
         }
-        __syncthreads();
-#pragma unroll
-        for (int j = 0; j < kCI; ++j) {
-          const bool win = (valid >> j) & 1u;
-          const uint32_t bal = __ballot_sync(0xFFFFFFFFu, win);
-          if (!bal) continue;
-          uint32_t base = 0;
-          if (lane == __ffs(bal) - 1) base = atomicAdd(&s_cnt[2], __popc(bal));
-          base = __shfl_sync(0xFFFFFFFFu, base, __ffs(bal) - 1);
-          if (win) {
-            const uint32_t slot = base + __popc(bal & lanemask_lt_b());
-            if (slot < k) w[slot] = v[j];
-            else atomicOr(p.err, kErrOverflowW);
-          }
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, win);
+        if (!bal) continue;
+        uint32_t base = 0;
+        if (lane == __ffs(bal) - 1) base = atomicAdd(&s_cnt[2], __popc(bal));
+        base = __shfl_sync(0xFFFFFFFFu, base, __ffs(bal) - 1);
+        if (win) {
+          const uint32_t slot = base + __popc(bal & lanemask_lt_b());
+          if (slot < k) w[slot] = v;
+          else atomicOr(p.err, kErrOverflowW);
         }
-        __syncthreads();
       }
       phase_mark(p, 3, tmark);
       block_sort_desc(w, static_cast<int>(k));
       phase_mark(p, 5, tmark);
     }
   } else {
-    // the k-th key is tau: G (all > tau, fewer than k <= kBGS, on chip)
-    // sorted, then the smallest-index ties at tau in index order, which
-    // keeps the whole output sorted
+    // the k-th key is tau: G (all > tau, fewer than k) sorted, then the
+    // smallest-index ties at tau in index order, which keeps the whole
+    // output sorted
+    for (uint32_t i = tid; i < gcnt; i += kBT) w[i] = g_get(sm, scr, i);
     block_sort_desc(w, static_cast<int>(gcnt));
     phase_mark(p, 3, tmark);
     const uint32_t need = k - gcnt;
@@ -623,10 +788,10 @@ __device__ void process_row(const BatchParams& p, const RowDesc& r, const Smem& 
       __syncthreads();
       if (tid == 0) s_cnt[3] = 0;
       __syncthreads();
-      uint16_t* lst = reinterpret_cast<uint16_t*>(sm.ring);
+      uint16_t* lst = reinterpret_cast<uint16_t*>(sm.ring + kTieOff);
       if (scan) lst[atomicAdd(&s_cnt[3], 1u)] = static_cast<uint16_t>(tid);
       __syncthreads();
-      uint32_t* cnts = reinterpret_cast<uint32_t*>(sm.ring + 1024);
+      uint32_t* cnts = reinterpret_cast<uint32_t*>(sm.ring + kTieOff + size_t(kBT) * 2);
       cnts[tid] = cnt;
       __syncthreads();
       const uint32_t nscan = s_cnt[3];
@@ -710,6 +875,7 @@ __global__ void __launch_bounds__(kBT, 1) batched_kernel(BatchParams p) {
   extern __shared__ __align__(128) unsigned char bsm[];
   __shared__ __align__(8) uint64_t bars[kBStages];
   __shared__ uint32_t hist[256];
+  __shared__ unsigned long long mm[2];
   __shared__ uint32_t s_bc[4];
   __shared__ uint32_t s_cnt[4];
   __shared__ uint32_t s_row;
@@ -722,7 +888,8 @@ __global__ void __launch_bounds__(kBT, 1) batched_kernel(BatchParams p) {
   Ring ring;
   ring.bar = bars;
   ring.seq = 0;
-  ring.pol = l2_evict_first_policy();
+  ring.pol_first = l2_evict_first_policy();
+  ring.pol_normal = l2_evict_normal_policy();
   if (threadIdx.x == 0) {
     for (int s = 0; s < kBStages; ++s) mbar_init(&bars[s], 1);
     fence_mbar_init();
@@ -736,10 +903,10 @@ __global__ void __launch_bounds__(kBT, 1) batched_kernel(BatchParams p) {
     if (ri >= static_cast<uint32_t>(p.nrows)) break;
     const RowDesc r = p.rows[ri];
     switch (r.beta) {
-      case 1: process_row<DT, 1>(p, r, sm, ring, hist, s_bc, s_cnt, s_lists); break;
-      case 3: process_row<DT, 3>(p, r, sm, ring, hist, s_bc, s_cnt, s_lists); break;
-      case 4: process_row<DT, 4>(p, r, sm, ring, hist, s_bc, s_cnt, s_lists); break;
-      default: process_row<DT, 2>(p, r, sm, ring, hist, s_bc, s_cnt, s_lists); break;
+      case 1: process_row<DT, 1>(p, r, sm, ring, hist, s_bc, s_cnt, s_lists, mm); break;
+      case 3: process_row<DT, 3>(p, r, sm, ring, hist, s_bc, s_cnt, s_lists, mm); break;
+      case 4: process_row<DT, 4>(p, r, sm, ring, hist, s_bc, s_cnt, s_lists, mm); break;
+      default: process_row<DT, 2>(p, r, sm, ring, hist, s_bc, s_cnt, s_lists, mm); break;
     }
     // a bounded wait gave up: copies may still be in flight, stop this CTA
     if (__syncthreads_or(threadIdx.x == 0 && (__ldcg(p.err) & kErrTimeout))) break;
@@ -832,8 +999,8 @@ struct RowPlan {
 // fewer than 2k delegates would exist; in every case raised so that the
 // delegates fit on chip (beta * S <= kBDMax, alpha >= 5).
 RowPlan plan_row(int64_t n, int64_t k, int force_alpha, int force_beta) {
-  RowPlan rp{0, 0, n};
-  if (n <= kBDirect && force_alpha <= 0) return rp;  // direct select, G = the row
+  const RowPlan direct{0, 0, 0};  // on-chip select, no scratch
+  if (force_alpha <= 0 && n <= kBDirect) return direct;
   int a = 0, b = 0;
   {
     const int ln = std::min(std::max(ilog2_floor(n), kTuneN0), kTuneN1) - kTuneN0;
@@ -842,10 +1009,17 @@ RowPlan plan_row(int64_t n, int64_t k, int force_alpha, int force_beta) {
     a = g_tune[ln][lk].alpha;
     b = g_tune[ln][lk].beta;
   }
+  if (force_alpha > 0) a = force_alpha;
   if (force_beta > 0) b = force_beta;
   if (b <= 0) b = 2;
-  if (force_alpha > 0) a = force_alpha;
+  if (a == 1) {
+    if (n <= kBDirectMax) return direct;
+    a = 0;  // too long to hold on chip: Rule 4
+  }
   const bool from_rule4 = a <= 0;
+  // fewer than 2k delegates even with one segment per subrange: the
+  // delegates cannot reduce the row, select it directly when it fits
+  if (from_rule4 && n <= kBDirectMax && int64_t(b) * ((n + 31) / 32) < 2 * k) return direct;
   if (from_rule4) a = rule4(n, k);
   // delegates must fit on chip: beta * S <= kBDMax
   int amin = 5;
@@ -855,6 +1029,7 @@ RowPlan plan_row(int64_t n, int64_t k, int force_alpha, int force_beta) {
   if (from_rule4)
     while (a > amin && int64_t(b) * ((n + (int64_t(1) << a) - 1) >> a) < 2 * k) --a;
   const int64_t S = (n + (int64_t(1) << a) - 1) >> a;
+  RowPlan rp;
   rp.alpha = a;
   rp.beta = b;
   rp.gneed = (int64_t(b) * S >= k) ? std::min<int64_t>(n, ((k - 1) / b) * (int64_t(1) << a) + k) : n;
@@ -907,7 +1082,7 @@ drtopk_status drtopk_batch_plan_create(drtopk_dtype dtype, const int64_t* row_of
   const int64_t* row_off = off_h.data();
   const int32_t* ks = ks_h.data();
   if (dtype != DRTOPK_U32 && dtype != DRTOPK_I32 && dtype != DRTOPK_F32) return DRTOPK_ERR_DTYPE;
-  if (alpha < 0 || alpha > 16 || (alpha > 0 && alpha < 5) || beta < 0 || beta > kMaxBeta)
+  if (alpha < 0 || alpha > 16 || (alpha > 1 && alpha < 5) || beta < 0 || beta > kMaxBeta)
     return DRTOPK_ERR_INVALID;
   if (row_off[0] < 0) return DRTOPK_ERR_INVALID;
   std::vector<RowDesc> rd(static_cast<size_t>(rows));
@@ -963,6 +1138,18 @@ drtopk_status drtopk_batch_plan_create(drtopk_dtype dtype, const int64_t* row_of
     return e == cudaErrorMemoryAllocation ? DRTOPK_ERR_NOMEM : DRTOPK_ERR_CUDA;
   }
   *out = pl;
+  return DRTOPK_OK;
+}
+
+drtopk_status drtopk_batch_limits(int32_t* max_k, int64_t* max_row, int32_t* direct_max,
+                                  int32_t* direct_max_onchip, int32_t* max_delegates,
+                                  int32_t* onchip_candidates) {
+  if (max_k) *max_k = kBMaxK;
+  if (max_row) *max_row = kBMaxN;
+  if (direct_max) *direct_max = kBDirect;
+  if (direct_max_onchip) *direct_max_onchip = kBDirectMax;
+  if (max_delegates) *max_delegates = kBDMax;
+  if (onchip_candidates) *onchip_candidates = kBGS;
   return DRTOPK_OK;
 }
 
@@ -1045,7 +1232,7 @@ drtopk_status drtopk_tune_get(int32_t log2n, int32_t log2k, int* alpha, int* bet
 
 drtopk_status drtopk_tune_set(int32_t log2n, int32_t log2k, int alpha, int beta) {
   if (log2n < kTuneN0 || log2n > kTuneN1 || log2k < 0 || log2k > kTuneK1) return DRTOPK_ERR_INVALID;
-  if (alpha < 0 || alpha > 16 || (alpha > 0 && alpha < 5) || beta < 0 || beta > kMaxBeta)
+  if (alpha < 0 || alpha > 16 || (alpha > 1 && alpha < 5) || beta < 0 || beta > kMaxBeta)
     return DRTOPK_ERR_INVALID;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune[log2n - kTuneN0][log2k].alpha = alpha;
@@ -1055,8 +1242,9 @@ drtopk_status drtopk_tune_set(int32_t log2n, int32_t log2k, int alpha, int beta)
 
 // Measures, for every (log2 n, log2 k) bucket with min_log2n <= log2 n <=
 // max_log2n and 2^(log2 k) <= min(4096, n / 2), the batched kernel on
-// `rows_per_shape` rows of 2^log2n hashed keys with alpha in [Rule 4 - 3,
-// Rule 4 + 2] and beta in {1, 2, 3, 4}, and stores the fastest pair.
+// `rows_per_shape` rows of 2^log2n hashed keys with k = 2^(log2 k + 1/2):
+// the direct select (rows that fit on chip) and alpha in [Rule 4 - 3,
+// Rule 4 + 2] with beta in {1, 2, 3, 4}; stores the fastest choice.
 drtopk_status drtopk_autotune_batched(drtopk_dtype dtype, int32_t min_log2n, int32_t max_log2n,
                                       int32_t rows_per_shape, void* stream) {
   if (min_log2n < kTuneN0 || max_log2n > 24 || min_log2n > max_log2n || rows_per_shape < 1)
@@ -1084,36 +1272,41 @@ drtopk_status drtopk_autotune_batched(drtopk_dtype dtype, int32_t min_log2n, int
     const int64_t n = int64_t(1) << ln;
     std::vector<int64_t> off(rows_per_shape + 1);
     for (int r = 0; r <= rows_per_shape; ++r) off[r] = r * n;
+    if (n <= kBDirect) continue;  // always selected directly
     for (int lk = 0; lk <= kTuneK1 && (int64_t(1) << lk) <= std::min<int64_t>(kBMaxK, n / 2); ++lk) {
-      const int32_t k = 1 << lk;
+      // a k in the middle of the bucket [2^lk, 2^(lk+1))
+      const int32_t k = static_cast<int32_t>(std::min<int64_t>(
+          std::min<int64_t>(kBMaxK, n / 2), std::llround(std::exp2(lk + 0.5))));
       std::vector<int32_t> kv(rows_per_shape, k);
       const int a4 = rule4(n, k);
+      std::vector<std::pair<int, int>> cand;
+      if (n <= kBDirectMax) cand.push_back({1, 0});
+      for (int b = 1; b <= 4; ++b)
+        for (int a = std::max(5, a4 - 3); a <= std::min(16, a4 + 2); ++a) cand.push_back({a, b});
       float best = 1e30f;
-      int best_a = 0, best_b = 2;
-      for (int b = 1; b <= 4 && st == DRTOPK_OK; ++b) {
-        for (int a = std::max(5, a4 - 3); a <= std::min(16, a4 + 2); ++a) {
-          if (n <= kBDirect) break;
-          drtopk_batch_plan* pl = nullptr;
-          if (drtopk_batch_plan_create(dtype, off.data(), kv.data(), rows_per_shape, a, b, &pl) != DRTOPK_OK)
-            continue;
-          // the clamp may have moved alpha: skip duplicates of another alpha
-          float ms_best = 1e30f;
-          for (int rep = 0; rep < 3; ++rep) {
-            cudaEventRecord(e0, s);
-            drtopk_batch_plan_run(pl, d_keys, d_ok, d_oi, s);
-            cudaEventRecord(e1, s);
-            cudaEventSynchronize(e1);
-            float ms = 0;
-            cudaEventElapsedTime(&ms, e0, e1);
-            ms_best = std::min(ms_best, ms);
-          }
-          if (drtopk_batch_plan_status(pl, s) != DRTOPK_OK) st = DRTOPK_ERR_CUDA;
-          drtopk_batch_plan_destroy(pl);
-          if (ms_best < best) {
-            best = ms_best;
-            best_a = a;
-            best_b = b;
-          }
+      int best_a = 0, best_b = 0;
+      for (const auto& ab : cand) {
+        if (st != DRTOPK_OK) break;
+        drtopk_batch_plan* pl = nullptr;
+        if (drtopk_batch_plan_create(dtype, off.data(), kv.data(), rows_per_shape, ab.first,
+                                     ab.second, &pl) != DRTOPK_OK)
+          continue;
+        float ms_best = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+          cudaEventRecord(e0, s);
+          drtopk_batch_plan_run(pl, d_keys, d_ok, d_oi, s);
+          cudaEventRecord(e1, s);
+          cudaEventSynchronize(e1);
+          float ms = 0;
+          cudaEventElapsedTime(&ms, e0, e1);
+          ms_best = std::min(ms_best, ms);
+        }
+        if (drtopk_batch_plan_status(pl, s) != DRTOPK_OK) st = DRTOPK_ERR_CUDA;
+        drtopk_batch_plan_destroy(pl);
+        if (ms_best < best) {
+          best = ms_best;
+          best_a = ab.first;
+          best_b = ab.second;
         }
       }
       if (best_a > 0) drtopk_tune_set(ln, lk, best_a, best_b);

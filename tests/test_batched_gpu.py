@@ -137,47 +137,64 @@ def test_batched_forced_alpha_beta(beta):
     kinds = ["uniform", "few", "asc", "equal", "desc", "normal"]
     bits, _ = build_batch(lens, kinds, beta, "u32", gap_max=0)
     row_off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
-    for alpha in range(5, 17):
+    for alpha in [1] + list(range(5, 17)):
         for k in (1, 37, 1000, 4096):
             ks = np.array([min(k, n) for n in lens], np.int32)
             a, b = run_and_check(bits, row_off, ks, "u32", alpha=alpha, beta=beta)
             for n, ar, br in zip(lens, a, b):
+                if alpha == 1:   # direct select where the row fits on chip
+                    if n <= drtopk.batch_limits()["direct_max_onchip"]:
+                        assert (ar, br) == (0, 0)
+                    continue
                 assert br == beta
-                # raised only to keep beta * S <= 8192 on chip
+                # raised only to keep beta * S on chip
                 amin = 5
-                while beta * math.ceil(n / 2**amin) > 8192:
+                while beta * math.ceil(n / 2**amin) > drtopk.batch_limits()["max_delegates"]:
                     amin += 1
                 assert ar == max(alpha, amin)
 
 
+def expected_params(n, k, lim):
+    """The default per-row choice (no table entry)."""
+    if n <= lim["direct_max"]:
+        return 0, 0
+    if n <= lim["direct_max_onchip"] and 2 * math.ceil(n / 32) < 2 * k:
+        return 0, 0
+    r4 = int(math.floor(0.5 * (math.log2(n) - math.log2(k) + 3)))
+    amin = 5
+    while 2 * math.ceil(n / 2**amin) > lim["max_delegates"]:
+        amin += 1
+    a = min(max(r4, amin), 16)
+    while a > amin and 2 * math.ceil(n / 2**a) < 2 * k:
+        a -= 1
+    return a, 2
+
+
 def test_batched_parameters_follow_rule4_and_table():
-    lens = [100, 4096, 4097, 1 << 16, 1 << 20, (1 << 22) + 3]
-    ks = [7, 4096, 5, 1024, 1000, 1]
+    lim = drtopk.batch_limits()
+    lens = [100, 4096, 4097, 20000, 40000, 1 << 16, 1 << 20, (1 << 22) + 3, 16500]
+    ks = [7, 4096, 5, 700, 4000, 1024, 1000, 1, 600]
     rng = np.random.default_rng(3)
     bits = rng.integers(0, 2**32, sum(lens), dtype=np.uint64).astype(np.uint32)
     row_off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
     a, b = run_and_check(bits, row_off, np.array(ks, np.int32), "u32")
     for n, k, ar, br in zip(lens, ks, a, b):
-        if n <= 4096:
-            assert ar == 0
-            continue
-        assert br == 2
-        r4 = int(math.floor(0.5 * (math.log2(n) - math.log2(k) + 3)))
-        amin = 5
-        while 2 * math.ceil(n / 2**amin) > 8192:
-            amin += 1
-        exp = min(max(r4, amin), 16)
-        while exp > amin and 2 * math.ceil(n / 2**exp) < 2 * k:
-            exp -= 1
-        assert ar == exp, (n, k, ar, exp)
-    # a table entry overrides Rule 4 for its shape bucket
-    drtopk.tune_set(20, 9, 12, 3)  # n in [2^20, 2^21), k in [512, 1024)
+        assert (ar, br) == expected_params(n, k, lim), (n, k, ar, br)
+    assert a[3] == 0 and a[4] > 0   # 20000/700 is selected directly, 40000 is too long
+    # table entries override the default for their shape bucket
+    drtopk.tune_set(20, 9, 12, 3)   # n in [2^20, 2^21), k in [512, 1024)
+    drtopk.tune_set(14, 9, 6, 4)    # n in [2^14, 2^15), k in [512, 1024): delegates
     try:
         a, b = run_and_check(bits, row_off, np.array(ks, np.int32), "u32")
-        assert (a[4], b[4]) == (12, 3)
-        assert (a[3], b[3]) != (12, 3)
+        assert (a[6], b[6]) == (12, 3)
+        assert (a[5], b[5]) == expected_params(lens[5], ks[5], lim)
+        assert (a[8], b[8]) == (6, 4)
+        drtopk.tune_set(20, 9, 1, 0)  # direct, but 2^20 keys do not fit on chip
+        a, b = run_and_check(bits, row_off, np.array(ks, np.int32), "u32")
+        assert (a[6], b[6]) == expected_params(lens[6], ks[6], lim)
     finally:
         drtopk.tune_set(20, 9, 0, 0)
+        drtopk.tune_set(14, 9, 0, 0)
 
 
 def test_batched_unaligned_starts_and_gaps():

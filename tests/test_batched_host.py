@@ -47,7 +47,9 @@ def test_plan_argument_checks(L):
 
 
 def test_tuning_table_roundtrip(L):
-    assert drtopk.tune_get(20, 10) == (0, 0)   # untouched: Rule 4
+    assert drtopk.tune_get(20, 10) == (0, 0)
+    drtopk.tune_set(20, 10, 1, 0)              # direct select
+    assert drtopk.tune_get(20, 10) == (1, 0)   # untouched: Rule 4
     drtopk.tune_set(20, 10, 9, 3)
     assert drtopk.tune_get(20, 10) == (9, 3)
     drtopk.tune_set(20, 10, 0, 0)
@@ -58,3 +60,10 @@ def test_tuning_table_roundtrip(L):
             drtopk.tune_set(*bad)
     with pytest.raises(drtopk.DrTopkError):
         drtopk.tune_get(40, 0)
+
+
+def test_batch_limits(L):
+    lim = drtopk.batch_limits()
+    assert lim["max_k"] == 4096 and lim["max_row"] == 1 << 24 and lim["direct_max"] == 4096
+    assert lim["max_delegates"] >= 4096 and lim["onchip_candidates"] >= 2048
+    assert lim["direct_max_onchip"] >= lim["direct_max"]
