@@ -200,8 +200,9 @@ drtopk_status drtopk_topk_host(const void* keys, drtopk_dtype dtype,
  * (a device array is copied to the host to plan the launch: synchronous). The outputs of row r
  * are out_keys / out_idx[o_r .. o_r + k_r) with o_r = k_0 + ... + k_{r-1}
  * (packed in row order), sorted by (key descending, index ascending); an
- * index is the position within the row. keys (device) must be 16-byte
- * aligned; rows may start at any element.
+ * index is the position within the row. keys (device) must be 4-byte
+ * aligned; rows may start at any element (a row's bulk copies may read the
+ * bytes of its first 16-byte block before its first key, never past it).
  *
  * Per-row parameters: rows of at most 4096 keys are selected directly (no
  * delegates: the row is held on chip and radix-selected). Longer rows take
@@ -303,6 +304,78 @@ drtopk_status drtopk_tune_set(int32_t log2n, int32_t log2k, int alpha, int beta)
 drtopk_status drtopk_autotune_batched(drtopk_dtype dtype, int32_t min_log2n,
                                       int32_t max_log2n, int32_t rows_per_shape,
                                       void* stream);
+
+/*
+ * ----------------------------------------------------------------- server --
+ * Continuous batching of top-k requests (no counterpart in the paper, which
+ * answers one query per call). A scheduler thread admits submitted requests
+ * in arrival order while the device-resident state of the admitted ones fits
+ * the HBM budget: for each request its keys (4n bytes), outputs (8k bytes)
+ * and, for a single query, the workspace drtopk_plan reports; plus the
+ * server's own buffers (fixed_bytes of the statistics, about 0.6 GB for 152
+ * SMs). Admitted requests with n <= batch_max_n (default 2^20), k <= 4096
+ * and candidates within the batched scratch are coalesced, per dtype, into
+ * batched launches (drtopk_topk_batched's kernel, up to 4096 rows, two
+ * launches in flight); the others run as single queries, round-robin over
+ * four streams, so that large and small work overlap. Results are those of
+ * drtopk_topk on the same arguments, bit for bit.
+ *
+ * Ownership: the caller owns keys (device, 4-byte aligned), out_keys and
+ * out_idx (device, k entries each); keys must stay alive and unmodified and
+ * the outputs untouched until the ticket completes. Submit, poll and wait
+ * may be called from any host thread.
+ */
+typedef struct drtopk_server drtopk_server;
+
+/* flags of drtopk_server_create_ex */
+#define DRTOPK_SERVER_PLAIN 1 /* no batching: every request is one plain
+                                 single-query launch sequence on one stream,
+                                 in arrival order (the baseline) */
+
+typedef struct {
+  uint64_t submitted, completed, failed;
+  uint64_t batches;          /* batched launches */
+  uint64_t batched_requests; /* requests served by them */
+  uint64_t single_queries;   /* requests served as single queries */
+  uint64_t peak_bytes;       /* largest admitted state + fixed_bytes */
+  uint64_t in_use_bytes;     /* admitted state now + fixed_bytes */
+  uint64_t fixed_bytes;      /* the server's own device buffers */
+} drtopk_server_stats;
+
+/* Creates a server on `device` (starts its scheduler thread). Returns
+ * DRTOPK_ERR_BUDGET when the budget does not exceed the server's own
+ * buffers. batch_max_n: largest n sent to batched launches (0: 2^20). */
+drtopk_status drtopk_server_create(size_t hbm_budget_bytes, int device, drtopk_server** out);
+drtopk_status drtopk_server_create_ex(size_t hbm_budget_bytes, int device, int flags,
+                                      int64_t batch_max_n, drtopk_server** out);
+
+/* Queues a top-k request (1 <= k <= n <= 2^31 - 1). *ticket identifies it.
+ * DRTOPK_ERR_BUDGET when the request alone exceeds the budget. Never
+ * blocks on the GPU. */
+drtopk_status drtopk_server_submit(drtopk_server* srv, const void* keys, drtopk_dtype dtype,
+                                   int64_t n, int64_t k, void* out_keys, int32_t* out_idx,
+                                   uint64_t* ticket);
+
+/* DRTOPK_PENDING while the request runs; else its final status (DRTOPK_OK
+ * when the outputs are written), after which the ticket is forgotten (a
+ * later poll returns DRTOPK_ERR_INVALID). _ex also returns the latency from
+ * submission to completion seen by the scheduler, in microseconds. */
+drtopk_status drtopk_server_poll(drtopk_server* srv, uint64_t ticket);
+drtopk_status drtopk_server_poll_ex(drtopk_server* srv, uint64_t ticket, double* latency_us);
+
+/* Blocks until the request completes; then as drtopk_server_poll_ex. */
+drtopk_status drtopk_server_wait(drtopk_server* srv, uint64_t ticket, double* latency_us);
+
+drtopk_status drtopk_server_get_stats(drtopk_server* srv, drtopk_server_stats* out);
+
+/* Host only: the bytes a request counts against the budget and whether it
+ * would be batched (flags and batch_max_n as for drtopk_server_create_ex). */
+drtopk_status drtopk_server_footprint(drtopk_dtype dtype, int64_t n, int64_t k, int flags,
+                                      int64_t batch_max_n, size_t* bytes, int* batched);
+
+/* Finishes every submitted request, stops the scheduler and frees the
+ * server. Tickets not yet polled are forgotten. */
+drtopk_status drtopk_server_destroy(drtopk_server* srv);
 
 /* Stage timing (CUDA events recorded on the launching stream around each
  * stage while profiling is on). Stages: 0 delegate pass, 1 threshold

@@ -50,6 +50,15 @@ class Stats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
 
+class ServerStats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_uint64) for f in
+                ("submitted", "completed", "failed", "batches", "batched_requests",
+                 "single_queries", "peak_bytes", "in_use_bytes", "fixed_bytes")]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class Profile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * NUM_STAGES),
                 ("launches", ctypes.c_int64 * NUM_STAGES)]
@@ -94,6 +103,15 @@ def lib():
         L.drtopk_batch_plan_phase_cycles.argtypes = [p, ctypes.POINTER(ctypes.c_uint64), i32, p]
         L.drtopk_topk_batched.argtypes = [p, i32, pi64, pi32, i32, p, p, p]
         L.drtopk_batch_limits.argtypes = [pi32, pi64, pi32, pi32, pi32, pi32]
+        L.drtopk_server_create_ex.argtypes = [ctypes.c_size_t, i32, i32, i64, ctypes.POINTER(p)]
+        L.drtopk_server_submit.argtypes = [p, p, i32, i64, i64, p, p,
+                                           ctypes.POINTER(ctypes.c_uint64)]
+        L.drtopk_server_poll_ex.argtypes = [p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]
+        L.drtopk_server_wait.argtypes = [p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]
+        L.drtopk_server_get_stats.argtypes = [p, ctypes.POINTER(ServerStats)]
+        L.drtopk_server_footprint.argtypes = [i32, i64, i64, i32, i64,
+                                              ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(i32)]
+        L.drtopk_server_destroy.argtypes = [p]
         L.drtopk_tune_get.argtypes = [i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
         L.drtopk_tune_set.argtypes = [i32, i32, i32, i32]
         L.drtopk_autotune_batched.argtypes = [i32, i32, i32, i32, p]
@@ -103,7 +121,10 @@ def lib():
                    "drtopk_batch_plan_status", "drtopk_batch_plan_params",
                    "drtopk_batch_plan_destroy", "drtopk_batch_plan_phase_cycles",
                    "drtopk_topk_batched", "drtopk_batch_limits", "drtopk_tune_get",
-                   "drtopk_tune_set", "drtopk_autotune_batched"):
+                   "drtopk_tune_set", "drtopk_autotune_batched", "drtopk_server_create_ex",
+                   "drtopk_server_submit", "drtopk_server_poll_ex", "drtopk_server_wait",
+                   "drtopk_server_get_stats", "drtopk_server_footprint",
+                   "drtopk_server_destroy"):
             getattr(L, fn).restype = i32
         _lib = L
     return _lib
@@ -398,3 +419,72 @@ def autotune_batched(dtype, min_log2n, max_log2n, rows_per_shape=152, stream=Non
     """Measures (alpha, beta) per shape bucket and fills the tuning table."""
     _check(lib().drtopk_autotune_batched(_NAMES[dtype], min_log2n, max_log2n, rows_per_shape,
                                          _stream(stream)), "drtopk_autotune_batched")
+
+
+# ------------------------------------------------------------------- server --
+SERVER_PLAIN = 1
+PENDING = 8
+
+
+def server_footprint(n, k, dtype="f32", flags=0, batch_max_n=0):
+    """(bytes counted against the budget, batched?) of a request. Host only."""
+    b, bt = ctypes.c_size_t(), ctypes.c_int()
+    _check(lib().drtopk_server_footprint(_NAMES[dtype], n, k, flags, batch_max_n,
+                                         ctypes.byref(b), ctypes.byref(bt)),
+           "drtopk_server_footprint")
+    return b.value, bool(bt.value)
+
+
+class Server:
+    """Continuous-batching top-k server (drtopk_server_*). Requests are
+    device tensors owned by the caller; keep them alive until done."""
+
+    def __init__(self, hbm_budget_bytes, device=0, plain=False, batch_max_n=0):
+        self._h = ctypes.c_void_p()
+        _check(lib().drtopk_server_create_ex(hbm_budget_bytes, device,
+                                             SERVER_PLAIN if plain else 0, batch_max_n,
+                                             ctypes.byref(self._h)), "drtopk_server_create")
+
+    def submit(self, keys, k, out_keys, out_idx, dtype=None):
+        t = ctypes.c_uint64()
+        _check(lib().drtopk_server_submit(self._h, _dev(keys), _dtype_code(keys, dtype),
+                                          keys.numel(), k, _dev(out_keys), _dev(out_idx),
+                                          ctypes.byref(t)), "drtopk_server_submit")
+        return t.value
+
+    def poll(self, ticket):
+        """None while pending, else the latency in microseconds (raises on
+        a failed request)."""
+        lat = ctypes.c_double()
+        rc = lib().drtopk_server_poll_ex(self._h, ticket, ctypes.byref(lat))
+        if rc == PENDING:
+            return None
+        _check(rc, "drtopk_server_poll")
+        return lat.value
+
+    def wait(self, ticket):
+        lat = ctypes.c_double()
+        _check(lib().drtopk_server_wait(self._h, ticket, ctypes.byref(lat)), "drtopk_server_wait")
+        return lat.value
+
+    def stats(self):
+        st = ServerStats()
+        _check(lib().drtopk_server_get_stats(self._h, ctypes.byref(st)), "drtopk_server_get_stats")
+        return st.as_dict()
+
+    def close(self):
+        if self._h:
+            lib().drtopk_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

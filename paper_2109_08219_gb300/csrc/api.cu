@@ -451,6 +451,12 @@ done:
 }
 
 }  // namespace
+
+drtopk_status topk_kernel_by_kernel(const void* keys, int dtype, int64_t n, int64_t k,
+                                    void* out_keys, int32_t* out_idx, cudaStream_t s) {
+  return run_query(keys, dtype, n, k, 0, 0, out_keys, out_idx, nullptr, nullptr, s, false);
+}
+
 }  // namespace drtopk
 
 using namespace drtopk;

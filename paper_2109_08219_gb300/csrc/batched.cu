@@ -28,15 +28,6 @@
 
 namespace drtopk {
 
-struct RowDesc {
-  int64_t start;   // first key (element offset in the concatenated keys)
-  int64_t out;     // first output slot
-  int32_t n;
-  int32_t k;
-  int32_t alpha;   // 0: direct select (no delegates)
-  int32_t beta;
-};
-
 namespace {
 
 constexpr int kBT = 512;              // threads per CTA (one CTA per SM)
@@ -66,15 +57,14 @@ static_assert(kTieOff + size_t(kBT) * 10 <= kRingBytes, "tie lists exceed the ri
 constexpr size_t kDynSmem = kRingBytes + size_t(kBDMax) * 4 + size_t(kBDMax) * 2 + size_t(kBGS) * 8;
 
 struct BatchParams {
-  const uint32_t* keys;
-  int64_t total;          // keys in the concatenated array
+  uint64_t keys_base;     // base addresses of RowDesc's offsets
+  uint64_t out_keys_base;
+  uint64_t out_idx_base;
   const RowDesc* rows;    // processing order (largest first)
   int32_t nrows;
   uint32_t* row_ctr;      // zeroed by the host before the launch
   uint64_t* scratch;      // per-CTA candidate spill, scap entries each
   int64_t scap;
-  uint32_t* out_keys;
-  int32_t* out_idx;
   uint32_t* err;
   unsigned long long* phase;  // kBPhases cycle counters (thread 0 of each CTA)
 };
@@ -84,6 +74,7 @@ struct BatchParams {
 // (or sort of all candidates), 4 tie ranking, 5 final sort and output.
 // Direct rows: 6 load, 7 select, 8 collection, 9 sort and output.
 constexpr int kBPhases = 10;
+static_assert(kBPhases == kBatchPhases, "phase counters");
 
 __device__ __forceinline__ void phase_mark(const BatchParams& p, int ph, long long& tmark) {
   if (threadIdx.x == 0) {
@@ -114,28 +105,48 @@ struct Ring {
   uint64_t pol_normal;  // rows read again by the filter while still in L2
 };
 
+__device__ __forceinline__ const uint32_t* row_keys(const BatchParams& p, const RowDesc& r) {
+  return reinterpret_cast<const uint32_t*>(p.keys_base + r.keys);
+}
+__device__ __forceinline__ uint32_t* row_out_keys(const BatchParams& p, const RowDesc& r) {
+  return reinterpret_cast<uint32_t*>(p.out_keys_base + r.out_keys);
+}
+__device__ __forceinline__ int32_t* row_out_idx(const BatchParams& p, const RowDesc& r) {
+  return reinterpret_cast<int32_t*>(p.out_idx_base + r.out_idx);
+}
+// Key shift of the row inside its 16-byte blocks (chunks start at
+// multiples of 16 bytes from the row start, so it holds for every chunk).
+__device__ __forceinline__ int row_shift(const BatchParams& p, const RowDesc& r) {
+  return static_cast<int>(((p.keys_base + r.keys) & 15u) >> 2);
+}
+
 // Issues chunk c of the row into a stage buffer: one bulk copy from the
-// 16-byte boundary at or below its first key (the chunk is then read at a
-// shift of ((start + c * kBChunk) mod 4) keys). Thread 0 only.
+// 16-byte boundary at or below its first key (the chunk is then read at
+// row_shift keys), up to the last 16-byte boundary inside the row; the keys
+// after that boundary come by plain loads. The copy may read the bytes of
+// the row's first 16-byte block that precede its first key (always inside
+// the same allocation, whose base is at least 16-byte aligned), never bytes
+// past the row. Thread 0 only.
 __device__ __forceinline__ void issue_row_chunk(const BatchParams& p, const RowDesc& r, int64_t c,
                                                 unsigned char* buf, uint64_t* bar, uint64_t pol) {
-  const int64_t e0 = r.start + c * kBChunk;                       // first key
-  const int64_t e1 = r.start + imin64(int64_t(r.n), (c + 1) * kBChunk);  // one past
-  const int64_t b0 = e0 * 4, b1 = e1 * 4;
-  const int64_t a0 = b0 & ~int64_t(15);
-  const int64_t tot16 = (p.total * 4) & ~int64_t(15);
-  const int64_t a1 = imin64((b1 + 15) & ~int64_t(15), tot16);
+  const uint32_t* rk = row_keys(p, r);
+  const int64_t base = static_cast<int64_t>(p.keys_base + r.keys);
+  const int s = row_shift(p, r);
+  const int64_t e0 = c * kBChunk;                                  // first key (row index)
+  const int64_t e1 = imin64(int64_t(r.n), (c + 1) * kBChunk);      // one past
+  const int64_t a0 = (base + e0 * 4) & ~int64_t(15);
+  const int64_t end16 = (base + int64_t(r.n) * 4) & ~int64_t(15);
+  const int64_t a1 = imin64((base + e1 * 4 + 15) & ~int64_t(15), end16);
+  const int64_t bytes = a1 > a0 ? a1 - a0 : 0;
   uint32_t* dst = reinterpret_cast<uint32_t*>(buf);
-  // keys past the last 16-byte boundary of the array (only at its very
-  // end) are not covered by the bulk copy: plain loads
-  const int64_t tma_end = a1 / 4;
-  for (int64_t e = (tma_end > e0 ? tma_end : e0); e < e1; ++e) dst[e - a0 / 4] = p.keys[e];
-  const int64_t bytes = a1 - a0;
+  // buffer word w holds row key e0 + w - s
+  const int64_t covered = e0 + bytes / 4 - s;  // first key not in the bulk copy
+  for (int64_t e = (covered > e0 ? covered : e0); e < e1; ++e) dst[e - e0 + s] = rk[e];
   if (bytes > 0) {
     fence_proxy_async_smem();
     mbar_arrive_expect_tx(bar, static_cast<uint32_t>(bytes));
-    tma_load_1d(buf, reinterpret_cast<const unsigned char*>(p.keys) + a0,
-                static_cast<uint32_t>(bytes), bar, pol);
+    tma_load_1d(buf, reinterpret_cast<const unsigned char*>(a0), static_cast<uint32_t>(bytes), bar,
+                pol);
   } else {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
   }
@@ -357,7 +368,7 @@ __device__ void direct_row(const BatchParams& p, const RowDesc& r, const Smem& s
 #pragma unroll
   for (int c = 0; c < kBStages; ++c) {
     const uint64_t q = seq0 + c;
-    const int shift = static_cast<int>(((r.start + int64_t(c) * kBChunk) * 4 & 15) / 4);
+    const int shift = row_shift(p, r);
     base[c] = reinterpret_cast<const uint32_t*>(sm.ring + (q % kBStages) * kBStageBytes) + shift;
     if (c < nch) ok = mbar_wait_bounded(&ring.bar[q % kBStages], static_cast<uint32_t>((q / kBStages) & 1)) && ok;
   }
@@ -425,8 +436,8 @@ __device__ void direct_row(const BatchParams& p, const RowDesc& r, const Smem& s
       for (int u = 0; u < kU; ++u) {
         const uint32_t rank = pre + __popc(bal[u] & lanemask_lt_b());
         if (((bal[u] >> lane) & 1u) && rank < need) {
-          p.out_keys[r.out + gt + rank] = tie_raw;
-          p.out_idx[r.out + gt + rank] = static_cast<int32_t>(wb + u * 32 + lane);
+          row_out_keys(p, r)[gt + rank] = tie_raw;
+          row_out_idx(p, r)[gt + rank] = static_cast<int32_t>(wb + u * 32 + lane);
         }
         pre += __popc(bal[u]);
       }
@@ -438,8 +449,8 @@ __device__ void direct_row(const BatchParams& p, const RowDesc& r, const Smem& s
   block_sort_desc(sm.gbuf, static_cast<int>(gt));
   for (uint32_t j = tid; j < gt; j += kBT) {
     const uint64_t c = sm.gbuf[j];
-    p.out_keys[r.out + j] = unmap_key(DT, comp_key(c));
-    p.out_idx[r.out + j] = static_cast<int32_t>(comp_idx(c));
+    row_out_keys(p, r)[j] = unmap_key(DT, comp_key(c));
+    row_out_idx(p, r)[j] = static_cast<int32_t>(comp_idx(c));
   }
   __syncthreads();
   phase_mark(p, 9, tmark);
@@ -458,7 +469,7 @@ __device__ void process_row(const BatchParams& p, const RowDesc& r, const Smem& 
   const uint32_t k = static_cast<uint32_t>(r.k);
   const int alpha = r.alpha;
   uint64_t* scr = p.scratch + static_cast<int64_t>(blockIdx.x) * p.scap;
-  const uint32_t* rk = p.keys + r.start;  // row keys
+  const uint32_t* rk = row_keys(p, r);
 
   if (tid == 0) {
     s_cnt[0] = 0;  // |G|
@@ -513,7 +524,7 @@ __device__ void process_row(const BatchParams& p, const RowDesc& r, const Smem& 
         return;
       }
       const uint32_t* cb = reinterpret_cast<const uint32_t*>(sm.ring + stage * kBStageBytes);
-      const int shift = static_cast<int>(((r.start + c * kBChunk) * 4 & 15) / 4);
+      const int shift = row_shift(p, r);
       const int64_t seg_start = c * kBChunk + int64_t(tid) * 32;  // row-relative
       const int64_t valid = n - seg_start;
       uint32_t m[B];
@@ -863,8 +874,8 @@ __device__ void process_row(const BatchParams& p, const RowDesc& r, const Smem& 
   // ------------------------------------------------- 5. write ------------
   for (uint32_t j = tid; j < k; j += kBT) {
     const uint64_t c = w[j];
-    p.out_keys[r.out + j] = unmap_key(DT, comp_key(c));
-    p.out_idx[r.out + j] = static_cast<int32_t>(comp_idx(c));
+    row_out_keys(p, r)[j] = unmap_key(DT, comp_key(c));
+    row_out_idx(p, r)[j] = static_cast<int32_t>(comp_idx(c));
   }
   __syncthreads();
   phase_mark(p, 5, tmark);
@@ -926,20 +937,19 @@ __global__ void fill_hash_kernel(uint32_t* a, int64_t n, uint64_t seed) {
 
 }  // namespace
 
-cudaError_t launch_batched(int dtype, const void* keys, int64_t total, const RowDesc* rows,
-                           int32_t nrows, uint32_t* row_ctr, uint64_t* scratch, int64_t scap,
-                           void* out_keys, int32_t* out_idx, uint32_t* err,
+cudaError_t launch_batched(int dtype, uint64_t keys_base, uint64_t out_keys_base,
+                           uint64_t out_idx_base, const RowDesc* rows, int32_t nrows,
+                           uint32_t* row_ctr, uint64_t* scratch, int64_t scap, uint32_t* err,
                            unsigned long long* phase, int grid, cudaStream_t s) {
   BatchParams p;
-  p.keys = static_cast<const uint32_t*>(keys);
-  p.total = total;
+  p.keys_base = keys_base;
+  p.out_keys_base = out_keys_base;
+  p.out_idx_base = out_idx_base;
   p.rows = rows;
   p.nrows = nrows;
   p.row_ctr = row_ctr;
   p.scratch = scratch;
   p.scap = scap;
-  p.out_keys = static_cast<uint32_t*>(out_keys);
-  p.out_idx = out_idx;
   p.err = err;
   p.phase = phase;
   switch (dtype) {
@@ -1051,6 +1061,16 @@ bool fetch_host(const T* src, size_t count, std::vector<T>& dst) {
 }
 
 }  // namespace
+
+BatchRowPlan batch_plan_row(int64_t n, int64_t k) {
+  const RowPlan rp = plan_row(n, k, 0, 0);
+  return {rp.alpha, rp.beta, rp.gneed};
+}
+int batch_grid(int sms) { return sms; }
+int64_t batch_onchip_candidates() { return kBGS; }
+int64_t batch_max_k() { return kBMaxK; }
+int64_t batch_max_n() { return kBMaxN; }
+
 }  // namespace drtopk
 
 using namespace drtopk;
@@ -1094,8 +1114,9 @@ drtopk_status drtopk_batch_plan_create(drtopk_dtype dtype, const int64_t* row_of
     if (n < 1 || n > kBMaxN) return DRTOPK_ERR_INVALID;
     if (k < 1 || k > n || k > kBMaxK) return DRTOPK_ERR_K;
     const RowPlan rp = plan_row(n, k, alpha, beta);
-    rd[r].start = row_off[r];
-    rd[r].out = out_pos;
+    rd[r].keys = static_cast<uint64_t>(row_off[r]) * 4;
+    rd[r].out_keys = static_cast<uint64_t>(out_pos) * 4;
+    rd[r].out_idx = static_cast<uint64_t>(out_pos) * 4;
     rd[r].n = static_cast<int32_t>(n);
     rd[r].k = static_cast<int32_t>(k);
     rd[r].alpha = rp.alpha;
@@ -1156,13 +1177,16 @@ drtopk_status drtopk_batch_limits(int32_t* max_k, int64_t* max_row, int32_t* dir
 drtopk_status drtopk_batch_plan_run(drtopk_batch_plan* pl, const void* keys, void* out_keys,
                                     int32_t* out_idx, void* stream) {
   if (!pl || !keys || !out_keys || !out_idx) return DRTOPK_ERR_INVALID;
-  if (reinterpret_cast<uintptr_t>(keys) & 15u) return DRTOPK_ERR_INVALID;
+  if ((reinterpret_cast<uintptr_t>(keys) | reinterpret_cast<uintptr_t>(out_keys) |
+       reinterpret_cast<uintptr_t>(out_idx)) & 3u)
+    return DRTOPK_ERR_INVALID;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemsetAsync(pl->d_ctl, 0, 2 * sizeof(uint32_t), s);
   if (e == cudaSuccess)
-    e = launch_batched(pl->dtype, keys, pl->total, pl->d_rows, pl->rows, pl->d_ctl,
-                       pl->d_scratch, pl->scap, out_keys, out_idx, pl->d_ctl + 1, pl->d_phase,
-                       pl->grid, s);
+    e = launch_batched(pl->dtype, reinterpret_cast<uint64_t>(keys),
+                       reinterpret_cast<uint64_t>(out_keys), reinterpret_cast<uint64_t>(out_idx),
+                       pl->d_rows, pl->rows, pl->d_ctl, pl->d_scratch, pl->scap, pl->d_ctl + 1,
+                       pl->d_phase, pl->grid, s);
   return e == cudaSuccess ? DRTOPK_OK : (e == cudaErrorMemoryAllocation ? DRTOPK_ERR_NOMEM : DRTOPK_ERR_CUDA);
 }
 

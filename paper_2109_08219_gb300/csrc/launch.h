@@ -46,4 +46,45 @@ int64_t tie_blocks(int64_t S);
 cudaError_t launch_resolve_delegates(const Work& w, const void* keys, int32_t* d_idx,
                                      cudaStream_t s);
 
+// drtopk_topk without the graph cache: every kernel launched on `s`
+// (api.cu). For one-off queries, e.g. those of the server.
+drtopk_status topk_kernel_by_kernel(const void* keys, int dtype, int64_t n, int64_t k,
+                                    void* out_keys, int32_t* out_idx, cudaStream_t s);
+
+// ------------------------------------------------------------- batched ---
+// One row of a batch. Its keys, output keys and output indices sit at the
+// byte offsets keys / out_keys / out_idx from the launch's three base
+// addresses (a plan over one concatenated array uses the arrays as bases;
+// the server uses base 0 and absolute addresses).
+struct RowDesc {
+  uint64_t keys;      // first key, 4-byte aligned
+  uint64_t out_keys;  // k outputs
+  uint64_t out_idx;   // k int32 indices
+  int32_t n;
+  int32_t k;
+  int32_t alpha;   // 0: direct select (no delegates)
+  int32_t beta;
+};
+
+// The batched kernel (batched.cu): one persistent CTA per SM takes rows
+// [0, nrows) of `rows` through *row_ctr (zeroed before the launch).
+cudaError_t launch_batched(int dtype, uint64_t keys_base, uint64_t out_keys_base,
+                           uint64_t out_idx_base, const RowDesc* rows, int32_t nrows,
+                           uint32_t* row_ctr, uint64_t* scratch, int64_t scap, uint32_t* err,
+                           unsigned long long* phase, int grid, cudaStream_t s);
+
+// Per-row parameters of the batched path with the default policy (tuning
+// table, direct select, Rule 4): alpha 0 = direct select; gneed = candidate
+// capacity the row may need (scratch holds what exceeds the on-chip part).
+struct BatchRowPlan {
+  int alpha, beta;
+  int64_t gneed;
+};
+BatchRowPlan batch_plan_row(int64_t n, int64_t k);
+int batch_grid(int sms);                 // CTAs of one batched launch
+int64_t batch_onchip_candidates();
+int64_t batch_max_k();
+int64_t batch_max_n();
+constexpr int kBatchPhases = 10;         // cycle counters of a batched launch
+
 }  // namespace drtopk
