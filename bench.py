@@ -15,7 +15,17 @@ Extra measurements in the same line:
                 memory, H2D copy and D2H of the results inside the timing);
   cpu_baseline  the CPU oracle (single thread) on a bounded sample;
   clocks        nvidia-smi samples taken during the timed region;
-  breakdown     per (distribution, k): ms, candidates kept, stage times.
+  breakdown     per (distribution, k): ms, candidates kept, stage times;
+  batched       the ragged batch (4096 float32 rows, lengths round(2^U[10,22]),
+                k_r uniform in [1, min(1024, n_r)], N(0,1)) in one graph-replayed
+                persistent launch, default and autotuned parameters, against the
+                same rows as 4096 plain per-row calls (and those calls captured in
+                one CUDA graph);
+  served        Poisson arrivals of float32 requests (n log-uniform in
+                [2^12, 2^28], k log-uniform in [1, 2^14], normal or uniform
+                values by coin flip) at swept offered loads through the server
+                (64 GB HBM budget) and through its plain mode (one launch
+                sequence per request, one stream): throughput, p50 / p99 latency.
 
 --impl reference times the CPU oracle instead (rank 0 only).
 Multi-GPU (torchrun): every rank runs the same workload on its own GPU
@@ -57,6 +67,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip breakdown/context runs")
+    ap.add_argument("--no-batched", action="store_true", help="skip the ragged batch")
+    ap.add_argument("--no-served", action="store_true", help="skip the served workload")
+    ap.add_argument("--served-requests", type=int, default=1500,
+                    help="arrivals per offered load")
     return ap.parse_args()
 
 
@@ -218,6 +232,177 @@ def workload_config(args, dists, ks):
 
 
 # ----------------------------------------------------------------- main ----
+# -------------------------------------------------------------- batched ----
+def batched_measure(drtopk, inputs, dev, peak, reps=10):
+    import numpy as np
+    import torch
+    lens, ks = inputs.batched_rows(4096, 4)
+    row_off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    total = int(row_off[-1])
+    ksn = np.array(ks, np.int32)
+    x = inputs.normal_f32(total, 4, device=dev)
+    out = {"workload": "4096 float32 rows, len round(2^U[10,22]), k_r U{1..min(1024,n_r)}, "
+                       "N(0,1), seed 4", "keys": total, "rows": 4096,
+           "inputs_larger_than_L2": True}
+
+    def time_plan(tag):
+        plan = drtopk.BatchPlan(row_off, ksn, "f32")
+        ok = torch.empty(plan.total_k, dtype=torch.float32, device=dev)
+        oi = torch.empty(plan.total_k, dtype=torch.int32, device=dev)
+        s = torch.cuda.Stream(dev)
+        with torch.cuda.stream(s):
+            for _ in range(3):
+                plan.run(x, ok, oi, stream=s)
+        s.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            plan.run(x, ok, oi, stream=s)
+        plan.phase_cycles(reset=True, stream=s)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(s):
+            e0.record(s)
+            for _ in range(reps):
+                g.replay()
+            e1.record(s)
+        s.synchronize()
+        plan.status(s)
+        ms = e0.elapsed_time(e1) / reps
+        cyc = plan.phase_cycles(stream=s)
+        a, b = plan.params()
+        plan.close()
+        tot = float(sum(cyc.values())) or 1.0
+        out[tag] = {"ms": ms, "gkeys_s": total / ms / 1e6, "gbs": 4.0 * total / ms / 1e6,
+                    "hbm_frac_of_measured": 4.0 * total / ms / 1e6 / peak,
+                    "kernels_per_batch": 1,
+                    "direct_rows": int((a == 0).sum()),
+                    "cycle_share": {k: round(v / tot, 4) for k, v in cyc.items()}}
+        return ok, oi
+
+    ok0, oi0 = time_plan("rule4")
+    t0 = time.perf_counter()
+    drtopk.autotune_batched("f32", 12, 22, rows_per_shape=152)
+    out["autotune_s"] = time.perf_counter() - t0
+    ok1, oi1 = time_plan("autotuned")
+    out["autotuned_equals_rule4"] = bool(torch.equal(ok0.view(torch.int32), ok1.view(torch.int32))
+                                         and torch.equal(oi0, oi1))
+    # the same rows as one plain call each
+    oo = np.concatenate([[0], np.cumsum(ksn.astype(np.int64))])
+    pk = torch.empty(int(oo[-1]), dtype=torch.float32, device=dev)
+    pi = torch.empty(int(oo[-1]), dtype=torch.int32, device=dev)
+
+    def per_row():
+        for r in range(4096):
+            a, b, o, k = int(row_off[r]), int(row_off[r + 1]), int(oo[r]), int(ksn[r])
+            drtopk.drtopk_topk(x[a:b], k, out_keys=pk[o:o + k], out_idx=pi[o:o + k])
+
+    per_row()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    per_row()
+    e1.record()
+    torch.cuda.synchronize()
+    out["per_row_plain_ms"] = e0.elapsed_time(e1)
+    out["per_row_equals_batched"] = bool(torch.equal(pk.view(torch.int32), ok0.view(torch.int32))
+                                         and torch.equal(pi, oi0))
+    try:
+        s = torch.cuda.Stream(dev)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            per_row()
+        with torch.cuda.stream(s):
+            g.replay()
+            e0.record(s)
+            g.replay()
+            g.replay()
+            e1.record(s)
+        s.synchronize()
+        out["per_row_graph_ms"] = e0.elapsed_time(e1) / 2
+        del g
+    except Exception as ex:  # report, do not fail the bench
+        out["per_row_graph_ms"] = None
+        out["per_row_graph_error"] = repr(ex)[:200]
+    best = min(out["rule4"]["ms"], out["autotuned"]["ms"])
+    out["speedup_vs_per_row_plain"] = out["per_row_plain_ms"] / best
+    if out.get("per_row_graph_ms"):
+        out["speedup_vs_per_row_graph"] = out["per_row_graph_ms"] / best
+    del x, pk, pi
+    torch.cuda.empty_cache()
+    return out
+
+
+# --------------------------------------------------------------- served ----
+def served_measure(drtopk, dev, arrivals, budget=64 << 30, pool=192, seed=5):
+    import numpy as np
+    import torch
+    rng = np.random.default_rng(seed)
+    reqs = []
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    for _ in range(pool):
+        n = int(round(2.0 ** rng.uniform(12, 28)))
+        k = min(n, int(round(2.0 ** rng.uniform(0, 14))))
+        if rng.random() < 0.5:
+            x = torch.randn(n, device=dev, generator=g)
+        else:
+            x = torch.rand(n, device=dev, generator=g)
+        reqs.append((x, k))
+    kmax = max(k for _, k in reqs)
+    mean_keys = float(np.mean([x.numel() for x, _ in reqs]))
+    order = rng.integers(0, pool, arrivals)
+    outs = [(torch.empty(kmax, device=dev), torch.empty(kmax, dtype=torch.int32, device=dev))
+            for _ in range(arrivals)]
+    torch.cuda.synchronize()
+
+    def run(plain, rate):
+        """rate None: all requests at once (closed loop, capacity)."""
+        srv = drtopk.Server(budget, device=dev.index or 0, plain=plain)
+        # warm-up: one of each request shape class
+        for i in range(min(8, pool)):
+            x, k = reqs[i]
+            srv.wait(srv.submit(x, k, outs[i][0], outs[i][1]))
+        gaps = rng.exponential(1.0 / rate, arrivals) if rate else np.zeros(arrivals)
+        t_arr = np.cumsum(gaps)
+        tickets = []
+        t0 = time.perf_counter()
+        for j in range(arrivals):
+            while time.perf_counter() - t0 < t_arr[j]:
+                pass
+            x, k = reqs[order[j]]
+            tickets.append(srv.submit(x, k, outs[j][0], outs[j][1]))
+        lats = [srv.wait(t) for t in tickets]
+        t1 = time.perf_counter()
+        st = srv.stats()
+        srv.close()
+        lats = np.sort(np.array(lats))
+        keys = float(sum(reqs[i][0].numel() for i in order))
+        return {"offered_rps": rate, "achieved_rps": arrivals / (t1 - t0),
+                "gkeys_s": keys / (t1 - t0) / 1e9,
+                "p50_us": float(lats[len(lats) // 2]),
+                "p99_us": float(lats[min(len(lats) - 1, int(0.99 * len(lats)))]),
+                "mean_us": float(lats.mean()), "batches": st["batches"],
+                "batched_requests": st["batched_requests"],
+                "peak_gb": st["peak_bytes"] / 1e9}
+
+    cap_server = run(False, None)
+    cap_plain = run(True, None)
+    loads = []
+    base = cap_plain["achieved_rps"]
+    for frac in (0.25, 0.5, 0.8, 1.2):
+        rate = frac * base
+        loads.append({"offered_frac_of_plain_capacity": frac,
+                      "server": run(False, rate), "plain": run(True, rate)})
+    del reqs, outs
+    torch.cuda.empty_cache()
+    return {"workload": "Poisson arrivals, float32, n log-uniform [2^12, 2^28], k log-uniform "
+                        "[1, 2^14], N(0,1) or U(0,1) by coin flip, %d distinct requests "
+                        "(mean n %.3g), %d arrivals per load" % (pool, mean_keys, arrivals),
+            "budget_gb": budget / 2**30, "latency": "submit to completion seen by the scheduler",
+            "capacity": {"server": cap_server, "plain": cap_plain}, "loads": loads}
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup()
@@ -379,6 +564,11 @@ def main():
             "paper_ms_v100s": PAPER_UD_MS if args.log2n == 30 else None,
             "note": "paper number is V100S (1134 GB/s), context only"}
         del ud
+
+    if not args.no_batched and world == 1:
+        out["batched"] = batched_measure(drtopk, inputs, dev, peak)
+    if not args.no_served and world == 1:
+        out["served"] = served_measure(drtopk, dev, args.served_requests)
 
     if not args.no_cpu and world == 1:
         sample_log2 = min(26, args.log2n)
