@@ -22,8 +22,9 @@ Extra measurements in the same line:
                 same rows as 4096 plain per-row calls (and those calls captured in
                 one CUDA graph);
   served        Poisson arrivals of float32 requests (n log-uniform in
-                [2^12, 2^28], k log-uniform in [1, 2^14], normal or uniform
-                values by coin flip) at swept offered loads through the server
+                [2^12, 2^28], k log-uniform in [1, 2^14], N(0,1) or U[-1,1)
+                by coin flip) at offered loads {0.25 .. 1.2} x the plain mode's
+                measured saturation rate through the server
                 (64 GB HBM budget) and through its plain mode (one launch
                 sequence per request, one stream): throughput, p50 / p99 latency.
 
@@ -52,7 +53,7 @@ PAPER_UD_MS = 6.4  # Dr. Top-k radix, |V| = 2^30 UD, k = 1024, V100S (Sec. 5.1)
 # DRAM bytes (read + write) per key of one delegate-pass launch, from the ncu
 # capture in profiles/delegate_kernel_zipf_u32_2p27_k1024.md (scaled by keys).
 # Must be re-measured (or set to None) whenever the delegate kernel changes.
-DELEG_DRAM_BYTES_PER_KEY = (536.93e6 + 4.21e6) / (1 << 27)
+DELEG_DRAM_BYTES_PER_KEY = (536.93e6 + 3.38e6) / (1 << 27)
 
 
 def parse():
@@ -69,7 +70,9 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="skip breakdown/context runs")
     ap.add_argument("--no-batched", action="store_true", help="skip the ragged batch")
     ap.add_argument("--no-served", action="store_true", help="skip the served workload")
-    ap.add_argument("--served-requests", type=int, default=1500,
+    ap.add_argument("--batched-rows", type=int, default=4096,
+                    help="rows of the ragged batch (the first rows of the 4096-row recipe)")
+    ap.add_argument("--served-requests", type=int, default=2000,
                     help="arrivals per offered load")
     return ap.parse_args()
 
@@ -233,16 +236,16 @@ def workload_config(args, dists, ks):
 
 # ----------------------------------------------------------------- main ----
 # -------------------------------------------------------------- batched ----
-def batched_measure(drtopk, inputs, dev, peak, reps=10):
+def batched_measure(drtopk, inputs, dev, peak, rows=4096, reps=10):
     import numpy as np
     import torch
-    lens, ks = inputs.batched_rows(4096, 4)
+    lens, ks = inputs.batched_rows(rows, 4)
     row_off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
     total = int(row_off[-1])
     ksn = np.array(ks, np.int32)
     x = inputs.normal_f32(total, 4, device=dev)
-    out = {"workload": "4096 float32 rows, len round(2^U[10,22]), k_r U{1..min(1024,n_r)}, "
-                       "N(0,1), seed 4", "keys": total, "rows": 4096,
+    out = {"workload": "%d float32 rows, len round(2^U[10,22]), k_r U{1..min(1024,n_r)}, "
+                       "N(0,1), seed 4" % rows, "keys": total, "rows": rows,
            "inputs_larger_than_L2": True}
 
     def time_plan(tag):
@@ -292,7 +295,7 @@ def batched_measure(drtopk, inputs, dev, peak, reps=10):
     pi = torch.empty(int(oo[-1]), dtype=torch.int32, device=dev)
 
     def per_row():
-        for r in range(4096):
+        for r in range(rows):
             a, b, o, k = int(row_off[r]), int(row_off[r + 1]), int(oo[r]), int(ksn[r])
             drtopk.drtopk_topk(x[a:b], k, out_keys=pk[o:o + k], out_idx=pi[o:o + k])
 
@@ -347,7 +350,7 @@ def served_measure(drtopk, dev, arrivals, budget=64 << 30, pool=192, seed=5):
         if rng.random() < 0.5:
             x = torch.randn(n, device=dev, generator=g)
         else:
-            x = torch.rand(n, device=dev, generator=g)
+            x = torch.rand(n, device=dev, generator=g) * 2 - 1
         reqs.append((x, k))
     kmax = max(k for _, k in reqs)
     mean_keys = float(np.mean([x.numel() for x, _ in reqs]))
@@ -390,14 +393,14 @@ def served_measure(drtopk, dev, arrivals, budget=64 << 30, pool=192, seed=5):
     cap_plain = run(True, None)
     loads = []
     base = cap_plain["achieved_rps"]
-    for frac in (0.25, 0.5, 0.8, 1.2):
+    for frac in (0.25, 0.5, 0.75, 0.9, 1.0, 1.2):
         rate = frac * base
         loads.append({"offered_frac_of_plain_capacity": frac,
                       "server": run(False, rate), "plain": run(True, rate)})
     del reqs, outs
     torch.cuda.empty_cache()
     return {"workload": "Poisson arrivals, float32, n log-uniform [2^12, 2^28], k log-uniform "
-                        "[1, 2^14], N(0,1) or U(0,1) by coin flip, %d distinct requests "
+                        "[1, 2^14], N(0,1) or U[-1,1) by coin flip, %d distinct requests "
                         "(mean n %.3g), %d arrivals per load" % (pool, mean_keys, arrivals),
             "budget_gb": budget / 2**30, "latency": "submit to completion seen by the scheduler",
             "capacity": {"server": cap_server, "plain": cap_plain}, "loads": loads}
@@ -566,7 +569,7 @@ def main():
         del ud
 
     if not args.no_batched and world == 1:
-        out["batched"] = batched_measure(drtopk, inputs, dev, peak)
+        out["batched"] = batched_measure(drtopk, inputs, dev, peak, rows=args.batched_rows)
     if not args.no_served and world == 1:
         out["served"] = served_measure(drtopk, dev, args.served_requests)
 
