@@ -169,6 +169,11 @@ def max_over_ranks(v, world):
     return float(t.item())
 
 
+def aggregate_value(n, queries, steps, world, ms_max):
+    """Whole-job Gkeys/s: keys of all ranks over the slowest rank's time."""
+    return float(n) * queries * steps * world / (ms_max * 1e-3) / 1e9
+
+
 # ------------------------------------------------------------ oracle leg ---
 def oracle_sample(dists, ks, sample_log2, reps=1, data=None):
     """Single-thread CPU oracle over the first 2^sample_log2 keys of each query
@@ -477,8 +482,7 @@ def main():
     prof = drtopk.profile_end()
     prof_ms_step = ep0.elapsed_time(ep1) / psteps
     queries = len(dists) * len(ks)
-    keys_all = float(n) * queries * args.steps * world
-    value = keys_all / (ms_max * 1e-3) / 1e9
+    value = aggregate_value(n, queries, args.steps, world, ms_max)
 
     if rank != 0:
         return
