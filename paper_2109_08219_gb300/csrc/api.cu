@@ -61,7 +61,7 @@ constexpr size_t kAlign = 256;
 size_t al(size_t b) { return (b + kAlign - 1) & ~(kAlign - 1); }
 
 struct Layout {
-  size_t ctl, dkeys, dsegs, ds, scanq, g, sv, w, w2, tcnt, bsum, tieq, sstat, total;
+  size_t ctl, dkeys, dsegs, ds, scanq, g, sv, w, w2, tstat, sstat, total;
 };
 
 Layout layout(const Plan& p, int64_t k, bool need_topk, bool external_dkeys) {
@@ -77,9 +77,7 @@ Layout layout(const Plan& p, int64_t k, bool need_topk, bool external_dkeys) {
   L.sv = o; o += al(static_cast<size_t>(p.g_cap) * 8);
   L.w = o; if (need_topk) o += al(static_cast<size_t>(k) * 8);
   L.w2 = o; if (need_topk && k > 4096) o += al(static_cast<size_t>(k) * 8);
-  L.tcnt = o; if (need_topk) o += al(static_cast<size_t>(p.S) * 4);
-  L.bsum = o; if (need_topk) o += al(static_cast<size_t>(2 * tie_blocks(p.S)) * 4);
-  L.tieq = o; if (need_topk) o += al(static_cast<size_t>(2 * p.S) * 4);
+  L.tstat = o; if (need_topk) o += al(tie_bytes(p.S, p.alpha));
   L.sstat = o; if (need_topk) o += al(sort_status_words(k) * 8);
   L.total = o;
   return L;
@@ -183,9 +181,7 @@ void bind_work(Work& w, char* ws, const Layout& L, const Plan& P, int64_t n, int
   w.sv = reinterpret_cast<uint64_t*>(ws + L.sv);
   w.w = reinterpret_cast<uint64_t*>(ws + L.w);
   w.w2 = reinterpret_cast<uint64_t*>(ws + L.w2);
-  w.tcnt = reinterpret_cast<uint32_t*>(ws + L.tcnt);
-  w.bsum = reinterpret_cast<uint32_t*>(ws + L.bsum);
-  w.tieq = reinterpret_cast<uint32_t*>(ws + L.tieq);
+  w.tstat = reinterpret_cast<uint64_t*>(ws + L.tstat);
   w.sort_status = reinterpret_cast<uint64_t*>(ws + L.sstat);
   w.n = n;
   w.S = P.S;

@@ -98,15 +98,16 @@ struct Ctl {
   uint32_t kth_mapped;
   uint32_t ds_count;       // delegate keys surviving the first threshold digit
   uint32_t scanq_count;    // subranges queued for the filter scan
-  uint32_t tieq1_count;    // subranges queued for exact tie counts
-  uint32_t tieq2_count;    // subranges queued for tie emission
+  uint32_t tie_ticket;     // next tile of the tie path
+  uint32_t tie_cut_inv;    // ~(first tile whose tie prefix reaches `need`); 0: none yet
   uint32_t stage_count[10];  // survivors entering each second-select stage
   uint32_t ds_inplace;       // threshold passes 2-3 read the delegate keys in place
   uint32_t sort_ticket;
   uint32_t sort_tiles[8];    // dynamic tile ids of the output radix sort
   uint32_t sort_hist[8][256];  // digit counts of the output composites
   uint32_t sort_skip[8];
-  uint32_t pad_[2];
+  uint32_t tie_nlist;        // tiles listed for the tie emission
+  uint32_t pad_;
 };
 
 // Device views of the workspace of one query.
@@ -119,9 +120,8 @@ struct Work {
   uint64_t* sv;       // [g_cap] second-select ping-pong buffer
   uint64_t* w;        // [k] winners (unsorted), later sorted
   uint64_t* w2;       // [k] sort ping-pong buffer
-  uint32_t* tcnt;     // [S] tie counts per subrange (bit 31: lower bound)
-  uint32_t* bsum;     // [4 * nblk] block sums for the tie scans
-  uint32_t* tieq;     // [2 * S] tie queues (subrange ids; emission prefixes)
+  uint64_t* tstat;    // tie path: tie_bytes(S, alpha) bytes (look-back words, then
+                      // per-tile lower bounds, their prefixes and the tile list)
   uint64_t* sort_status;  // [8 * tiles * 256] look-back words of the sort
   Ctl* ctl;
   int64_t n;

@@ -39,8 +39,10 @@ cudaError_t launch_sort_output(const Work& w, void* out_keys, int32_t* out_idx,
                                void* out_kth, int sms, cudaStream_t s);
 size_t sort_status_words(int64_t k);
 
-// Number of 2048-subrange blocks of the tie scans (select.cu).
-int64_t tie_blocks(int64_t S);
+// Tiles of the tie path for S subranges of 2^alpha keys, and the bytes of
+// its workspace (select.cu).
+int64_t tie_tiles(int64_t S, int alpha);
+size_t tie_bytes(int64_t S, int alpha);
 
 // Resolves exact delegate positions for drtopk_delegates (select.cu).
 cudaError_t launch_resolve_delegates(const Work& w, const void* keys, int32_t* d_idx,

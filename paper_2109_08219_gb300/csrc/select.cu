@@ -29,11 +29,6 @@ namespace drtopk {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr uint32_t kInexact = 0x80000000u;  // tie count is a lower bound
-constexpr uint32_t kScanned = 0x40000000u;  // tie count came from a scan
-constexpr uint32_t kCountMask = 0x3FFFFFFFu;
-constexpr int kTieSubPerThread = 8;
-constexpr int kTieSubPerBlock = kThreads * kTieSubPerThread;
 constexpr int kScanKPT = 16;  // virtual keys per thread per filter-scan step
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
@@ -519,374 +514,505 @@ __global__ void __launch_bounds__(kThreads) gstage_kernel(GSelParams p, int s) {
 }
 
 // ------------------------------------------------------------ tie path ----
+// Mode kModeTies (|G| < k, the k-th key is tau): the answer is G plus the
+// `need` smallest indices holding tau (reading R1). The subranges are cut
+// into tiles of consecutive subranges, and three kernels place the ties:
+//   A  per tile, a lower bound of its ties from the delegates alone (exact
+//      unless some subrange's beta delegates all reach tau: "inexact");
+//   B  one block: exclusive prefixes of the lower bounds, the last tile that
+//      can matter (the first whose lower-bound prefix reaches `need`), and
+//      the list, in index order, of the tiles up to it that hold ties or are
+//      inexact;
+//   C  the listed tiles in order (an atomic ticket): exact counts (inexact
+//      subranges read), the tile's prefix = its lower-bound prefix plus the
+//      corrections (exact - lower bound) of the earlier listed tiles, found
+//      by a decoupled look-back (warp-wide window, bounded waits) unless no
+//      inexact tile precedes it; then its ties go to W[|G| + prefix + rank]
+//      in index order. The first tile whose prefix reaches `need` is the
+//      cut; later tiles stop.
+// Sparse ties (one tie needed among distinct keys) touch one tile; dense
+// ties (all keys equal) read only the tiles before the cut plus those in
+// flight.
 struct TieParams {
   const uint32_t* keys;
   int64_t n, S, k;
   int alpha;
   const uint32_t* dkeys;
   const uint16_t* dsegs;
-  uint32_t* tcnt;
-  uint32_t* bsum1;   // block sums of the lower bounds, scanned in place
-  uint32_t* bsum2;   // block sums after exact counts, scanned in place
-  int64_t nblk;
-  uint32_t* q1;      // subranges needing an exact tie count
-  uint32_t* q2;      // subranges emitting ties
-  uint32_t* q2pre;   // their tie prefixes
+  uint64_t* tstat;   // per list entry: flag << 32 | correction (aggregate or inclusive)
+  uint32_t* tlb;     // per tile: lower bound | inexact << 31
+  uint32_t* lbpre;   // per tile: exclusive prefix of the lower bounds
+  uint32_t* list;    // tiles to visit, index order; bit 31: no inexact tile before
+  int64_t tsub;      // subranges per tile
+  int64_t ntiles;
   const uint64_t* g;
   uint64_t* w;
   Ctl* ctl;
 };
 
-// Block-wide exclusive scan of one value per thread (256 threads).
-__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total) {
-  __shared__ uint32_t wsum[kThreads / 32];
-  const uint32_t lane = lane_id();
-  const int warp = threadIdx.x >> 5;
-  uint32_t incl = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-    if (lane >= static_cast<uint32_t>(o)) incl += t;
-  }
-  if (lane == 31) wsum[warp] = incl;
-  __syncthreads();
-  uint32_t wpre = 0, tot = 0;
-  for (int q = 0; q < kThreads / 32; ++q) {
-    if (q < warp) wpre += wsum[q];
-    tot += wsum[q];
-  }
-  __syncthreads();
-  if (total) *total = tot;
-  return wpre + incl - v;
+constexpr int kTieTileKeys = 32768;     // keys per tile (at least one subrange)
+constexpr int kTieTileMaxSub = 1024;    // subranges per tile at most
+constexpr int kTieMaxSeg = 2048;        // 32-key segments per tile at most (alpha = 16)
+constexpr int kTiePlanChunk = 8192;     // tiles per shared-memory pass of the plan
+constexpr uint64_t kTieAgg = uint64_t(1) << 32;
+constexpr uint64_t kTieIncl = uint64_t(2) << 32;
+constexpr uint32_t kTieSpin = 1u << 22;
+constexpr uint32_t kTieInexact = 0x80000000u;
+
+__device__ __forceinline__ void st_relaxed_u64(uint64_t* p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
 }
 
+// Ties at tau a subrange holds by its delegates, and whether non-delegates
+// may hold more (all beta delegates reach tau and the subrange is longer).
+template <int B>
+__device__ __forceinline__ uint32_t tie_lb_of(const TieParams& p, int64_t i, uint32_t tau,
+                                              bool* inexact) {
+  uint32_t dk[B];
+  uint16_t ds[B];
+#pragma unroll
+  for (int j = 0; j < B; ++j) {
+    dk[j] = p.dkeys[i * B + j];
+    ds[j] = p.dsegs[i * B + j];
+  }
+  uint32_t c = 0;
+  *inexact = false;
+  if (dk[0] >= tau) {
+#pragma unroll
+    for (int j = 0; j < B; ++j) c += (dk[j] == tau && ds[j] != kNoSeg) ? 1u : 0u;
+    *inexact = dk[B - 1] >= tau && sub_len(i, p.alpha, p.n) > B;
+  }
+  return c;
+}
+
+// One thread per subrange, 4 subranges in flight per thread (grid-stride,
+// block-uniform trip count); the lanes of one tile (aligned groups of
+// min(tsub, 32)) are summed by shuffles and added to the tile's word (zeroed
+// before the launch).
 template <int B>
 __global__ void __launch_bounds__(kThreads) tie_lb_kernel(TieParams p) {
   Ctl* ctl = p.ctl;
   if (__ldcg(&ctl->mode) != kModeTies) return;
   const uint32_t tau = __ldcg(&ctl->tau);
-  for (int64_t b = blockIdx.x; b < p.nblk; b += gridDim.x) {
-  const int64_t i0 = b * kTieSubPerBlock + threadIdx.x * kTieSubPerThread;
-  uint32_t sum = 0;
-  uint32_t dka[kTieSubPerThread][B];
-  uint16_t dsa[kTieSubPerThread][B];
-#pragma unroll
-  for (int e = 0; e < kTieSubPerThread; ++e) {
-    const int64_t i = i0 + e;
-#pragma unroll
-    for (int j = 0; j < B; ++j) {
-      dka[e][j] = (i < p.S) ? p.dkeys[i * B + j] : 0u;
-      dsa[e][j] = (i < p.S) ? p.dsegs[i * B + j] : static_cast<uint16_t>(kNoSeg);
-    }
-  }
-#pragma unroll
-  for (int e = 0; e < kTieSubPerThread; ++e) {
-    const int64_t i = i0 + e;
-    if (i >= p.S) break;
-    const uint32_t* dk = dka[e];
-    const uint16_t* ds = dsa[e];
-    const int64_t len = sub_len(i, p.alpha, p.n);
-    uint32_t t;
-    if (dk[0] < tau) {
-      t = 0;
-    } else if (dk[B - 1] > tau && len > B) {
-      t = kInexact;  // scanned by the filter; its ties were not counted
-    } else {
-      uint32_t c = 0;
-#pragma unroll
-      for (int j = 0; j < B; ++j) c += (dk[j] == tau && ds[j] != kNoSeg) ? 1u : 0u;
-      t = c | ((dk[B - 1] == tau && len > B) ? kInexact : 0u);
-    }
-    p.tcnt[i] = t;
-    sum += t & kCountMask;
-  }
-  uint32_t tot;
-  block_excl_scan(sum, &tot);
-  if (threadIdx.x == 0) {
-    p.bsum1[b] = tot;
-    p.bsum2[b] = tot;
-  }
-  }
-}
-
-// Exclusive scan of nblk block sums in place, one block of 1024 threads.
-__global__ void __launch_bounds__(1024) scan_blocks_kernel(uint32_t* a, int64_t nblk, Ctl* ctl) {
-  if (__ldcg(&ctl->mode) != kModeTies) return;
-  __shared__ uint32_t part[1024];
-  const int64_t per = (nblk + 1023) / 1024;
-  const int64_t lo = threadIdx.x * per;
-  const int64_t hi = imin64(nblk, lo + per);
-  uint32_t s = 0;
-  for (int64_t i = lo; i < hi; ++i) s += a[i];
-  part[threadIdx.x] = s;
+  const int grp = p.tsub < 32 ? static_cast<int>(p.tsub) : 32;
+  const uint32_t lane = lane_id();
+  constexpr int kU = 4;
+  // the tiles one step of the block touches, summed in shared memory first
+  __shared__ uint32_t s_lb[kThreads * kU + 1];
+  for (int q = threadIdx.x; q <= kThreads * kU; q += kThreads) s_lb[q] = 0;
   __syncthreads();
-  for (int o = 1; o < 1024; o <<= 1) {
-    const uint32_t v = threadIdx.x >= static_cast<unsigned>(o) ? part[threadIdx.x - o] : 0u;
+  for (int64_t i0 = int64_t(blockIdx.x) * kThreads * kU; i0 < p.S;
+       i0 += int64_t(gridDim.x) * kThreads * kU) {
+    const int64_t t0 = i0 / p.tsub;
+    const int nt_blk = static_cast<int>(
+        (imin64(p.S, i0 + int64_t(kThreads) * kU) - 1) / p.tsub - t0 + 1);
+    uint32_t dk[kU][B];
+    uint16_t ds[kU][B];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int64_t i = i0 + int64_t(u) * kThreads + threadIdx.x;
+#pragma unroll
+      for (int q = 0; q < B; ++q) {
+        dk[u][q] = i < p.S ? p.dkeys[i * B + q] : 0u;
+        ds[u][q] = i < p.S ? p.dsegs[i * B + q] : static_cast<uint16_t>(kNoSeg);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int64_t i = i0 + int64_t(u) * kThreads + threadIdx.x;
+      uint32_t c = 0, x = 0;
+      if (i < p.S && dk[u][0] >= tau) {
+#pragma unroll
+        for (int q = 0; q < B; ++q) c += (dk[u][q] == tau && ds[u][q] != kNoSeg) ? 1u : 0u;
+        x = (dk[u][B - 1] >= tau && sub_len(i, p.alpha, p.n) > B) ? 1u : 0u;
+      }
+      for (int o = 1; o < grp; o <<= 1) {
+        c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+        x |= __shfl_xor_sync(0xFFFFFFFFu, x, o);
+      }
+      if ((lane & (grp - 1)) == 0 && i < p.S && (c | x)) {
+        const int t = static_cast<int>(i / p.tsub - t0);
+        if (c) atomicAdd(&s_lb[t], c);
+        if (x) atomicOr(&s_lb[t], kTieInexact);
+      }
+    }
     __syncthreads();
-    part[threadIdx.x] += v;
+    for (int q = threadIdx.x; q < nt_blk; q += kThreads) {
+      const uint32_t v = s_lb[q];
+      if (v) {
+        if (v & ~kTieInexact) atomicAdd(&p.tlb[t0 + q], v & ~kTieInexact);
+        if (v & kTieInexact) atomicOr(&p.tlb[t0 + q], kTieInexact);
+      }
+      s_lb[q] = 0;
+    }
     __syncthreads();
-  }
-  uint32_t run = part[threadIdx.x] - s;
-  for (int64_t i = lo; i < hi; ++i) {
-    const uint32_t v = a[i];
-    a[i] = run;
-    run += v;
   }
 }
 
-// Per-thread exclusive prefixes of the 8 tie counts it owns, offset by the
-// block's scanned sum: pre[e] = number of ties (as counted) before subrange e.
-__device__ __forceinline__ void tie_prefixes(const TieParams& p, const uint32_t* bscan, int64_t b,
-                                             uint32_t (&t)[kTieSubPerThread],
-                                             uint32_t (&pre)[kTieSubPerThread]) {
-  const int64_t i0 = b * kTieSubPerBlock + threadIdx.x * kTieSubPerThread;
-  uint32_t sum = 0;
-#pragma unroll
-  for (int e = 0; e < kTieSubPerThread; ++e) {
-    const int64_t i = i0 + e;
-    t[e] = (i < p.S) ? p.tcnt[i] : 0u;
-    pre[e] = sum;
-    sum += t[e] & kCountMask;
-  }
-  const uint32_t off = block_excl_scan(sum, nullptr) + bscan[b];
-#pragma unroll
-  for (int e = 0; e < kTieSubPerThread; ++e) pre[e] += off;
-}
-
-// Queue the subranges whose tie count is only a lower bound and whose
-// prefix is still below `need`: only they can hold a needed tie we cannot
-// place yet.
-__global__ void __launch_bounds__(kThreads) tie_enqueue_kernel(TieParams p) {
+// The tile words are staged through shared memory in chunks (coalesced
+// global reads and writes); each thread scans 8 consecutive tiles of a chunk.
+__global__ void __launch_bounds__(1024) tie_plan_kernel(TieParams p) {
   Ctl* ctl = p.ctl;
   if (__ldcg(&ctl->mode) != kModeTies) return;
   const uint32_t need = __ldcg(&ctl->need);
-  for (int64_t b = blockIdx.x; b < p.nblk; b += gridDim.x) {
-    uint32_t t[kTieSubPerThread], pre[kTieSubPerThread];
-    tie_prefixes(p, p.bsum1, b, t, pre);
-    const int64_t i0 = b * kTieSubPerBlock + threadIdx.x * kTieSubPerThread;
-    uint32_t c = 0;
+  constexpr int kPer = kTiePlanChunk / 1024;
+  __shared__ uint32_t buf[kTiePlanChunk + kTiePlanChunk / 32];  // padded: no bank conflicts
+  __shared__ int64_t s_last;
+  auto pad = [](int j) { return j + (j >> 5); };
+  const int64_t nt = p.ntiles;
+  const int tid = threadIdx.x;
+  if (tid == 0) s_last = nt - 1;
+  // pass 1: exclusive prefixes of the lower bounds; the first tile whose
+  // inclusive prefix reaches `need` is the last one that can matter
+  uint32_t base = 0;
+  for (int64_t c0 = 0; c0 < nt; c0 += kTiePlanChunk) {
+    const int cn = static_cast<int>(imin64(kTiePlanChunk, nt - c0));
 #pragma unroll
-    for (int e = 0; e < kTieSubPerThread; ++e) c += ((t[e] & kInexact) && pre[e] < need);
-    uint32_t slot = block_append<kThreads>(&ctl->tieq1_count, c);
-#pragma unroll
-    for (int e = 0; e < kTieSubPerThread; ++e)
-      if ((t[e] & kInexact) && pre[e] < need) p.q1[slot++] = static_cast<uint32_t>(i0 + e);
-  }
-}
-
-// Exact tie counts of the queued subranges, one warp per subrange over the
-// whole grid; the block sums used for the second scan are corrected in place.
-// Ties equal to tau among keys [lo, lo + len), read by one thread (len <= 64).
-template <int DT>
-__device__ __forceinline__ uint32_t count_eq_thread(const uint32_t* keys, int64_t lo, int64_t len,
-                                                    uint32_t tau) {
-  uint32_t c = 0;
-  if ((len & 3) == 0 && (reinterpret_cast<uintptr_t>(keys + lo) & 15u) == 0) {
-    const uint4* v4 = reinterpret_cast<const uint4*>(keys + lo);
-    for (int64_t w = 0; w < (len >> 2); ++w) {
-      const uint4 v = __ldg(v4 + w);
-      c += (map_key<DT>(v.x) == tau) + (map_key<DT>(v.y) == tau) + (map_key<DT>(v.z) == tau) +
-           (map_key<DT>(v.w) == tau);
+    for (int e = 0; e < kPer; ++e) {
+      const int j = e * 1024 + tid;
+      if (j < cn) buf[pad(j)] = p.tlb[c0 + j] & ~kTieInexact;
     }
-  } else {
-    for (int64_t t = 0; t < len; ++t) c += (map_key<DT>(__ldg(keys + lo + t)) == tau);
+    __syncthreads();
+    uint32_t v[kPer], sum = 0;
+#pragma unroll
+    for (int e = 0; e < kPer; ++e) {
+      const int j = tid * kPer + e;
+      v[e] = j < cn ? buf[pad(j)] : 0u;
+      sum += v[e];
+    }
+    uint32_t tot;
+    uint32_t run = base + block_scan_excl<1024>(sum, &tot);
+    int64_t first = -1;
+#pragma unroll
+    for (int e = 0; e < kPer; ++e) {
+      const int j = tid * kPer + e;
+      if (j < cn) {
+        buf[pad(j)] = run;
+        if (first < 0 && run + v[e] >= need) first = c0 + j;
+      }
+      run += v[e];
+    }
+    if (first >= 0)
+      atomicMin(reinterpret_cast<unsigned long long*>(&s_last), static_cast<unsigned long long>(first));
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < kPer; ++e) {
+      const int j = e * 1024 + tid;
+      if (j < cn) p.lbpre[c0 + j] = buf[pad(j)];
+    }
+    base += tot;
+    __syncthreads();
   }
-  return c;
+  const int64_t last = s_last;
+  // pass 2: the list of tiles up to `last` that hold ties or are inexact,
+  // each marked when no inexact tile precedes it
+  uint32_t lbase = 0, xbase = 0;
+  for (int64_t c0 = 0; c0 <= last; c0 += kTiePlanChunk) {
+    const int cn = static_cast<int>(imin64(kTiePlanChunk, last + 1 - c0));
+#pragma unroll
+    for (int e = 0; e < kPer; ++e) {
+      const int j = e * 1024 + tid;
+      if (j < cn) buf[pad(j)] = p.tlb[c0 + j];
+    }
+    __syncthreads();
+    uint32_t v[kPer], ci = 0, cx = 0;
+#pragma unroll
+    for (int e = 0; e < kPer; ++e) {
+      const int j = tid * kPer + e;
+      v[e] = j < cn ? buf[pad(j)] : 0u;
+      ci += v[e] != 0 ? 1u : 0u;  // holds ties or is inexact
+      cx += (v[e] & kTieInexact) ? 1u : 0u;
+    }
+    uint32_t ti, tx;
+    uint32_t bi = lbase + block_scan_excl<1024>(ci, &ti);
+    uint32_t bx = xbase + block_scan_excl<1024>(cx, &tx);
+#pragma unroll
+    for (int e = 0; e < kPer; ++e) {
+      const int j = tid * kPer + e;
+      if (j < cn && v[e] != 0)
+        p.list[bi++] = static_cast<uint32_t>(c0 + j) | (bx == 0 ? kTieInexact : 0u);
+      bx += (v[e] & kTieInexact) ? 1u : 0u;
+    }
+    lbase += ti;
+    xbase += tx;
+    __syncthreads();
+  }
+  if (tid == 0) ctl->tie_nlist = lbase;
 }
 
-constexpr int kTieThreadAlpha = 6;  // subranges of <= 64 keys: one thread each
+// The ties of a tile are ranked per 32-key segment. The tile's keys (when
+// some subrange must be read) come into shared memory by one bulk copy
+// (TMA, bounded wait) per chunk of kTieTileKeys; a warp vote per segment
+// gives its tie bitmask (subranges that may hold non-delegate ties, and for
+// alpha < 5 every subrange that may hold a tie at all). A subrange whose
+// ties are all delegates has its count at its first segment. Exclusive
+// prefixes over the segments rank every tie; the bitmasks place them
+// without reading the keys again.
+constexpr int kTieBufBytes = kTieTileKeys * 4 + 32;
 
-template <int DT>
-__global__ void __launch_bounds__(kThreads) tie_count_kernel(TieParams p) {
+__device__ __forceinline__ void tie_issue_copy(const uint32_t* keys, int64_t n, int64_t x0,
+                                               int64_t cnt, unsigned char* buf, uint64_t* bar,
+                                               uint64_t pol, int* shift) {
+  // keys [x0, x0 + cnt) -> buf at word `shift` (= the key's offset in its
+  // 16-byte block); the bulk copy starts at that block and stops at the last
+  // 16-byte boundary of the array, the rest by plain loads
+  const int64_t base = static_cast<int64_t>(reinterpret_cast<uintptr_t>(keys + x0));
+  const int s = static_cast<int>((base & 15) >> 2);
+  const int64_t a0 = base & ~int64_t(15);
+  const int64_t end16 = static_cast<int64_t>(reinterpret_cast<uintptr_t>(keys + n)) & ~int64_t(15);
+  const int64_t a1 = imin64((base + cnt * 4 + 15) & ~int64_t(15), end16);
+  const int64_t bytes = a1 > a0 ? a1 - a0 : 0;
+  uint32_t* dst = reinterpret_cast<uint32_t*>(buf);
+  const int64_t covered = bytes / 4 - s;  // keys [0, covered) come by the bulk copy
+  for (int64_t e = (covered > 0 ? covered : 0); e < cnt; ++e) dst[s + e] = keys[x0 + e];
+  if (bytes > 0) {
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(bar, static_cast<uint32_t>(bytes));
+    tma_load_1d(buf, reinterpret_cast<const void*>(a0), static_cast<uint32_t>(bytes), bar, pol);
+  } else {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+  }
+  *shift = s;
+}
+
+template <int DT, int B>
+__global__ void __launch_bounds__(kThreads, 1) tie_emit_kernel(TieParams p) {
   Ctl* ctl = p.ctl;
   if (__ldcg(&ctl->mode) != kModeTies) return;
   const uint32_t tau = __ldcg(&ctl->tau);
-  const int64_t nq = __ldcg(&ctl->tieq1_count);
-  const uint32_t lane = lane_id();
-  const int64_t warps = int64_t(gridDim.x) * (kThreads / 32);
-  uint32_t done = 0;
-  if (p.alpha <= kTieThreadAlpha) {
-    const int64_t nthr = int64_t(gridDim.x) * kThreads;
-    for (int64_t q0 = int64_t(blockIdx.x) * kThreads; q0 < nq; q0 += nthr) {
-      const int64_t q = q0 + threadIdx.x;
-      uint32_t delta = 0;
-      int64_t blk = -1;
-      if (q < nq) {
-        const int64_t i = p.q1[q];
-        const uint32_t c = count_eq_thread<DT>(p.keys, i << p.alpha, sub_len(i, p.alpha, p.n), tau);
-        delta = c - (p.tcnt[i] & kCountMask);
-        p.tcnt[i] = c | kScanned;
-        blk = i / kTieSubPerBlock;
-        ++done;
-      }
-      // consecutive queue entries mostly share a block sum: add once per group
-      const uint32_t am = __ballot_sync(0xFFFFFFFFu, q < nq);
-      if (q < nq) {
-        const uint32_t peers = __match_any_sync(am, static_cast<unsigned long long>(blk));
-        const uint32_t tot = __reduce_add_sync(peers, delta);
-        if ((peers & lanemask_lt()) == 0) atomicAdd(&p.bsum2[blk], tot);
-      }
-    }
-    done = __reduce_add_sync(0xFFFFFFFFu, done);
-    if (lane == 0 && done) atomicAdd(&ctl->tie_scanned, done);
-    return;
-  }
-  for (int64_t q = int64_t(blockIdx.x) * (kThreads / 32) + (threadIdx.x >> 5); q < nq;
-       q += warps) {
-    const int64_t i = p.q1[q];
-    const int64_t lo = i << p.alpha;
-    const int64_t len = sub_len(i, p.alpha, p.n);
-    uint32_t c = 0;
-    for (int64_t off = lane; off < len; off += 32)
-      c += (map_key<DT>(__ldg(p.keys + lo + off)) == tau);
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
-    if (lane == 0) {
-      const uint32_t old = p.tcnt[i] & kCountMask;
-      p.tcnt[i] = c | kScanned;
-      atomicAdd(&p.bsum2[i / kTieSubPerBlock], c - old);
-      ++done;
-    }
-  }
-  if (done) atomicAdd(&ctl->tie_scanned, done);
-}
-
-// Queue the subranges that hold needed ties (exact prefix below `need`) and
-// copy G, which is part of the answer, in front of the ties in W.
-__global__ void __launch_bounds__(kThreads) tie_emit_enqueue_kernel(TieParams p) {
-  Ctl* ctl = p.ctl;
-  if (__ldcg(&ctl->mode) != kModeTies) return;
   const uint32_t need = __ldcg(&ctl->need);
   const uint32_t g = __ldcg(&ctl->g_count);  // < k in this mode
+  const int64_t nl = __ldcg(&ctl->tie_nlist);
+  // G is part of the answer, in front of the ties
   for (int64_t j = int64_t(blockIdx.x) * kThreads + threadIdx.x; j < g;
        j += int64_t(gridDim.x) * kThreads)
     p.w[j] = p.g[j];
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&ctl->w_count, g);
-  for (int64_t b = blockIdx.x; b < p.nblk; b += gridDim.x) {
-    uint32_t t[kTieSubPerThread], pre[kTieSubPerThread];
-    tie_prefixes(p, p.bsum2, b, t, pre);
-    const int64_t i0 = b * kTieSubPerBlock + threadIdx.x * kTieSubPerThread;
-    uint32_t c = 0;
-#pragma unroll
-    for (int e = 0; e < kTieSubPerThread; ++e) c += ((t[e] & kCountMask) > 0 && pre[e] < need);
-    uint32_t slot = block_append<kThreads>(&ctl->tieq2_count, c);
-#pragma unroll
-    for (int e = 0; e < kTieSubPerThread; ++e) {
-      if ((t[e] & kCountMask) > 0 && pre[e] < need) {
-        p.q2[slot] = static_cast<uint32_t>(i0 + e);
-        p.q2pre[slot] = pre[e];
-        ++slot;
+
+  extern __shared__ __align__(128) unsigned char tbuf[];  // kTieBufBytes
+  __shared__ uint32_t s_seg[kTieMaxSeg];     // counts, then exclusive prefixes
+  __shared__ uint32_t s_bits[kTieMaxSeg];    // tie bitmask per segment
+  __shared__ uint32_t s_dc[kTieTileMaxSub];  // ties known from the delegates
+  __shared__ uint8_t s_read[kTieTileMaxSub];
+  __shared__ __align__(8) uint64_t s_bar;
+  __shared__ int64_t s_j, s_t;
+  __shared__ uint32_t s_clean, s_go, s_E, s_shift;
+  const int tid = threadIdx.x;
+  const uint32_t lane = lane_id();
+  const int warp = tid >> 5;
+  const int alpha = p.alpha;
+  const uint64_t pol = l2_evict_first_policy();
+  if (tid == 0) {
+    mbar_init(&s_bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  uint32_t phase = 0;  // copies completed on s_bar
+  uint32_t read_subs = 0;
+  uint32_t emitted = 0;  // ties written by this thread
+  for (;;) {
+    if (tid == 0) {
+      const int64_t j = atomicAdd(&ctl->tie_ticket, 1u);
+      s_j = j;
+      s_go = 0;
+      if (j < nl) {
+        const uint32_t e = p.list[j];
+        s_t = e & ~kTieInexact;
+        s_clean = (e & kTieInexact) ? 1u : 0u;
+        s_go = (s_t <= static_cast<int64_t>(~__ldcg(&ctl->tie_cut_inv))) ? 1u : 0u;
       }
     }
-  }
-}
-
-// Emit the ties of the queued subranges in index order, one warp each.
-template <int DT, int B>
-__global__ void __launch_bounds__(kThreads) tie_emit_kernel(TieParams p) {
-  Ctl* ctl = p.ctl;
-  if (__ldcg(&ctl->mode) != kModeTies) return;
-  const uint32_t tau = __ldcg(&ctl->tau);
-  const uint32_t need = __ldcg(&ctl->need);
-  const uint32_t g = __ldcg(&ctl->g_count);
-  const int64_t nq = __ldcg(&ctl->tieq2_count);
-  const uint32_t lane = lane_id();
-  const int64_t warps = int64_t(gridDim.x) * (kThreads / 32);
-  uint32_t emitted_total = 0;
-  if (p.alpha <= kTieThreadAlpha) {
-    // one thread per subrange, reading it in index order
-    for (int64_t q = int64_t(blockIdx.x) * kThreads + threadIdx.x; q < nq;
-         q += int64_t(gridDim.x) * kThreads) {
-      const int64_t i = p.q2[q];
-      uint32_t r = p.q2pre[q];
-      if (p.tcnt[i] & kScanned) {
-        const int64_t lo = i << p.alpha;
-        const int64_t len = sub_len(i, p.alpha, p.n);
-        for (int64_t t0 = 0; t0 < len && r < need; t0 += 16) {
-          uint32_t v[16];
+    __syncthreads();
+    if (!s_go) break;
+    const int64_t j = s_j, t = s_t;
+    const int64_t i_lo = t * p.tsub;
+    const int64_t nsub = imin64(p.tsub, p.S - i_lo);
+    const int64_t klo = i_lo << alpha;
+    const int64_t khi = imin64(p.n, (i_lo + nsub) << alpha);
+    const int nseg = static_cast<int>((khi - klo + 31) >> 5);
+    for (int q = tid; q < nseg; q += kThreads) {
+      s_seg[q] = 0;
+      s_bits[q] = 0;
+    }
+    __syncthreads();
+    uint32_t nread = 0;
+    for (int64_t ii = tid; ii < nsub; ii += kThreads) {
+      bool x;
+      const uint32_t c = tie_lb_of<B>(p, i_lo + ii, tau, &x);
+      const bool rd = alpha < 5 ? (c > 0 || x) : x;  // subrange read from its keys
+      s_read[ii] = rd ? 1 : 0;
+      s_dc[ii] = rd ? 0u : c;
+      if (!rd && c > 0) s_seg[static_cast<int>((ii << alpha) >> 5)] = c;  // alpha >= 5 here
+      nread += rd ? 1u : 0u;
+    }
+    read_subs += nread;
+    const int anyread = __syncthreads_or(nread > 0);
+    // tie bitmasks of the segments read, one chunk of the tile at a time
+    bool timed_out = false;
+    for (int64_t c0 = klo; anyread && c0 < khi; c0 += kTieTileKeys) {
+      const int64_t cn = imin64(kTieTileKeys, khi - c0);
+      if (tid == 0) {
+        int sh;
+        tie_issue_copy(p.keys, p.n, c0, cn, tbuf, &s_bar, pol, &sh);
+        s_shift = static_cast<uint32_t>(sh);
+      }
+      const bool ok = mbar_wait_bounded(&s_bar, phase & 1u);
+      ++phase;
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) {
+          atomicOr(&ctl->error, kErrTimeout);
+          mbar_wait_bounded(&s_bar, (phase - 1) & 1u);  // let the copy land (bounded)
+        }
+        timed_out = true;
+        break;
+      }
+      const uint32_t* kb = reinterpret_cast<const uint32_t*>(tbuf) + s_shift;
+      // 32 consecutive keys per warp step: one segment (block-uniform trip count)
+      for (int64_t xb = 0; xb < cn; xb += kThreads) {
+        const int64_t e = xb + tid;
+        const int64_t x = c0 + e;
+        const bool on = e < cn && s_read[(x >> alpha) - i_lo];
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, on && map_key<DT>(kb[e]) == tau);
+        if (lane == 0 && bal) {
+          const int seg = static_cast<int>((x - klo) >> 5);
+          s_seg[seg] = __popc(bal);
+          s_bits[seg] = bal;
+        }
+      }
+      __syncthreads();  // the buffer is reused by the next copy
+      fence_proxy_async_smem();
+    }
+    if (timed_out) break;
+    // exclusive prefixes over the segments (8 consecutive per thread)
+    uint32_t tot = 0;
+    {
+      constexpr int kPer = kTieMaxSeg / kThreads;
+      uint32_t c[kPer];
+      uint32_t sum = 0;
 #pragma unroll
-          for (int e = 0; e < 16; ++e) v[e] = (t0 + e < len) ? __ldg(p.keys + lo + t0 + e) : 0u;
+      for (int e = 0; e < kPer; ++e) {
+        const int q = tid * kPer + e;
+        c[e] = q < nseg ? s_seg[q] : 0u;
+        sum += c[e];
+      }
+      uint32_t run = block_scan_excl<kThreads>(sum, &tot);
 #pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            if (t0 + e < len && r < need && map_key<DT>(v[e]) == tau) {
-              p.w[g + r] = make_comp(tau, static_cast<uint32_t>(lo + t0 + e));
-              ++r;
-              ++emitted_total;
+      for (int e = 0; e < kPer; ++e) {
+        const int q = tid * kPer + e;
+        if (q < nseg) s_seg[q] = run;
+        run += c[e];
+      }
+    }
+    // corrections of the earlier listed tiles (warp 0)
+    if (warp == 0) {
+      const uint32_t corr = tot - (p.tlb[t] & ~kTieInexact);
+      uint32_t C = 0;
+      bool skip = false;
+      if (s_clean) {
+        if (lane == 0) st_relaxed_u64(&p.tstat[j], kTieIncl | corr);
+      } else {
+        if (lane == 0) st_relaxed_u64(&p.tstat[j], kTieAgg | corr);
+        int64_t base = j - 1;
+        uint32_t spins = 0;
+        for (;;) {
+          const int64_t idx = base - lane;
+          const uint64_t v = idx >= 0 ? ld_relaxed_u64(&p.tstat[idx]) : kTieIncl;
+          const uint64_t f = v & ~uint64_t(0xFFFFFFFFu);
+          const uint32_t ready = __ballot_sync(0xFFFFFFFFu, f != 0);
+          const uint32_t incl = __ballot_sync(0xFFFFFFFFu, f == kTieIncl);
+          if (incl) {
+            const int L = __ffs(incl) - 1;  // nearest inclusive word
+            const uint32_t upto = (L == 31) ? 0xFFFFFFFFu : ((2u << L) - 1u);
+            if ((ready & upto) == upto) {
+              C += __reduce_add_sync(0xFFFFFFFFu,
+                                     static_cast<int>(lane) <= L ? static_cast<uint32_t>(v) : 0u);
+              break;
             }
+          } else if (ready == 0xFFFFFFFFu) {
+            C += __reduce_add_sync(0xFFFFFFFFu, static_cast<uint32_t>(v));
+            base -= 32;
+            continue;
+          }
+          // a word not yet published: a tile past the cut may never publish
+          // (the decision is warp-uniform: any lane that sees the cut)
+          const bool past =
+              __any_sync(0xFFFFFFFFu, t > static_cast<int64_t>(~__ldcg(&ctl->tie_cut_inv)));
+          if (past || ++spins > kTieSpin) {
+            if (spins > kTieSpin && lane == 0) atomicOr(&ctl->error, kErrTimeout);
+            skip = true;
+            break;
           }
         }
-      } else {
+        if (!skip && lane == 0) st_relaxed_u64(&p.tstat[j], kTieIncl | (C + corr));
+      }
+      if (lane == 0) {
+        const uint32_t E = p.lbpre[t] + C;
+        if (!skip && E >= need) atomicMax(&ctl->tie_cut_inv, ~static_cast<uint32_t>(t));
+        s_E = skip ? need : E;
+      }
+    }
+    __syncthreads();
+    const uint32_t E = s_E;
+    if (E < need) {
+      // ties from the bitmasks: a warp per segment, coalesced writes
+      for (int q = warp; q < nseg; q += kThreads / 32) {
+        const uint32_t bits = s_bits[q];
+        const uint32_t r0 = E + s_seg[q];
+        if (bits == 0 || r0 >= need) continue;
+        if ((bits >> lane) & 1u) {
+          const uint32_t r = r0 + __popc(bits & lanemask_lt());
+          if (r < need) {
+            p.w[g + r] = make_comp(tau, static_cast<uint32_t>(klo + int64_t(q) * 32 + lane));
+            ++emitted;
+          }
+        }
+      }
+      // subranges whose ties are all delegates (alpha >= 5), a warp each:
+      // D lists equal keys in index order (segment, then occurrence); the
+      // position is the occurrence-th key equal to tau in the 32-key
+      // segment, found by one coalesced read and a vote
+      for (int64_t ii = warp; ii < nsub; ii += kThreads / 32) {
+        if (s_read[ii] || s_dc[ii] == 0) continue;
+        uint32_t r = E + s_seg[static_cast<int>((ii << alpha) >> 5)];
+        if (r >= need) continue;
+        const int64_t i = i_lo + ii;
         uint32_t dk[B];
         uint16_t ds[B];
 #pragma unroll
-        for (int j = 0; j < B; ++j) {
-          dk[j] = p.dkeys[i * B + j];
-          ds[j] = p.dsegs[i * B + j];
+        for (int q = 0; q < B; ++q) {
+          dk[q] = p.dkeys[i * B + q];
+          ds[q] = p.dsegs[i * B + q];
         }
 #pragma unroll
-        for (int j = 0; j < B; ++j) {
-          if (dk[j] == tau && ds[j] != kNoSeg && r < need) {
-            const int o = occ_rank<B>(dk, ds, j);
-            const int64_t pos = resolve_pos<DT>(p.keys, p.n, p.alpha, i, ds[j], tau, o);
-            if (pos < 0) atomicOr(&ctl->error, kErrTieRank);
-            p.w[g + r] = make_comp(tau, static_cast<uint32_t>(pos));
+        for (int q = 0; q < B; ++q) {
+          if (dk[q] == tau && ds[q] != kNoSeg && r < need) {
+            const int o = occ_rank<B>(dk, ds, q);
+            const int64_t lo = (i << alpha) + int64_t(ds[q]) * 32;
+            const int64_t hi = imin64(imin64(p.n, lo + 32), (i + 1) << alpha);
+            const bool m = lo + lane < hi && map_key<DT>(__ldg(p.keys + lo + lane)) == tau;
+            uint32_t bal = __ballot_sync(0xFFFFFFFFu, m);
+            for (int z = 0; z < o; ++z) bal &= bal - 1;
+            if (lane == 0) {
+              if (bal == 0) atomicOr(&ctl->error, kErrTieRank);
+              p.w[g + r] = make_comp(tau, static_cast<uint32_t>(lo + (bal ? __ffs(bal) - 1 : 0)));
+              ++emitted;
+            }
             ++r;
-            ++emitted_total;
           }
         }
       }
     }
+    __syncthreads();
   }
-  for (int64_t q = int64_t(blockIdx.x) * (kThreads / 32) + (threadIdx.x >> 5);
-       p.alpha > kTieThreadAlpha && q < nq; q += warps) {
-    const int64_t i = p.q2[q];
-    const uint32_t base = p.q2pre[q];
-    const uint32_t tt = p.tcnt[i];
-    uint32_t emitted = 0;
-    if (tt & kScanned) {
-      // read the subrange in index order and rank its ties
-      const int64_t lo = i << p.alpha;
-      const int64_t len = sub_len(i, p.alpha, p.n);
-      uint32_t run = 0;
-      for (int64_t off = 0; off < len && base + run < need; off += 32) {
-        const int64_t tix = off + lane;
-        const bool is_t = (tix < len) && (map_key<DT>(__ldg(p.keys + lo + tix)) == tau);
-        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, is_t);
-        const uint32_t r = base + run + __popc(bal & lanemask_lt());
-        if (is_t && r < need) {
-          p.w[g + r] = make_comp(tau, static_cast<uint32_t>(lo + tix));
-          ++emitted;
-        }
-        run += __popc(bal);
-      }
-    } else if (lane == 0) {
-      // every tie of this subrange is a delegate; D lists equal keys in
-      // index order (segment, then occurrence)
-      uint32_t dk[B];
-      uint16_t ds[B];
-#pragma unroll
-      for (int j = 0; j < B; ++j) {
-        dk[j] = p.dkeys[i * B + j];
-        ds[j] = p.dsegs[i * B + j];
-      }
-      uint32_t r = base;
-#pragma unroll
-      for (int j = 0; j < B; ++j) {
-        if (dk[j] == tau && ds[j] != kNoSeg && r < need) {
-          const int o = occ_rank<B>(dk, ds, j);
-          const int64_t pos = resolve_pos<DT>(p.keys, p.n, p.alpha, i, ds[j], tau, o);
-          if (pos < 0) atomicOr(&ctl->error, kErrTieRank);
-          p.w[g + r] = make_comp(tau, static_cast<uint32_t>(pos));
-          ++r;
-          ++emitted;
-        }
-      }
-    }
-    emitted_total += emitted;
-  }
-#pragma unroll
-  for (int o = 16; o >= 1; o >>= 1) emitted_total += __shfl_xor_sync(0xFFFFFFFFu, emitted_total, o);
-  if (lane == 0 && emitted_total) atomicAdd(&ctl->w_count, emitted_total);
+  read_subs = __reduce_add_sync(0xFFFFFFFFu, read_subs);
+  if (lane == 0 && read_subs) atomicAdd(&ctl->tie_scanned, read_subs);
+  emitted = __reduce_add_sync(0xFFFFFFFFu, emitted);
+  if (lane == 0 && emitted) atomicAdd(&ctl->w_count, emitted);
 }
 
 // ----------------------------------------------------------- k-th output ---
@@ -924,7 +1050,6 @@ __global__ void resolve_kernel(const uint32_t* keys, int64_t n, int64_t S, int a
 
 }  // namespace
 
-int64_t tie_blocks(int64_t S) { return (S + kTieSubPerBlock - 1) / kTieSubPerBlock; }
 
 cudaError_t launch_threshold(const Work& w, int sms, cudaStream_t s) {
   const int64_t count = w.S * w.beta;
@@ -978,6 +1103,16 @@ cudaError_t launch_filter(const Work& w, const void* keys, bool kth_only, int sm
   return cudaGetLastError();
 }
 
+int64_t tie_tile_subs(int alpha) {
+  const int64_t t = kTieTileKeys >> alpha;
+  return t < 1 ? 1 : (t > kTieTileMaxSub ? kTieTileMaxSub : t);
+}
+int64_t tie_tiles(int64_t S, int alpha) {
+  const int64_t t = tie_tile_subs(alpha);
+  return (S + t - 1) / t;
+}
+size_t tie_bytes(int64_t S, int alpha) { return static_cast<size_t>(tie_tiles(S, alpha)) * 20; }
+
 cudaError_t launch_ties(const Work& w, const void* keys, int sms, cudaStream_t s) {
   TieParams p;
   p.keys = static_cast<const uint32_t*>(keys);
@@ -987,43 +1122,41 @@ cudaError_t launch_ties(const Work& w, const void* keys, int sms, cudaStream_t s
   p.alpha = w.alpha;
   p.dkeys = w.dkeys;
   p.dsegs = w.dsegs;
-  p.tcnt = w.tcnt;
-  p.nblk = tie_blocks(w.S);
-  p.bsum1 = w.bsum;
-  p.bsum2 = w.bsum + p.nblk;
-  p.q1 = w.tieq;
-  p.q2 = w.tieq + w.S;
-  p.q2pre = w.scanq;  // the filter's queue is no longer needed
+  p.tsub = tie_tile_subs(w.alpha);
+  p.ntiles = tie_tiles(w.S, w.alpha);
+  p.tstat = w.tstat;
+  p.tlb = reinterpret_cast<uint32_t*>(w.tstat + p.ntiles);
+  p.lbpre = p.tlb + p.ntiles;
+  p.list = p.lbpre + p.ntiles;
   p.g = w.g;
   p.w = w.w;
   p.ctl = w.ctl;
-  const int grid = static_cast<int>(std::min<int64_t>(p.nblk, int64_t(sms) * 4));
-  const int gq = grid_for(w.S, kThreads / 32, sms, 4);
-#define DRTOPK_TIE_CASE(DTV)                                                        \
-  switch (w.beta) {                                                                 \
-    case 1: tie_lb_kernel<1><<<grid, kThreads, 0, s>>>(p); break;                   \
-    case 2: tie_lb_kernel<2><<<grid, kThreads, 0, s>>>(p); break;                   \
-    case 3: tie_lb_kernel<3><<<grid, kThreads, 0, s>>>(p); break;                   \
-    default: tie_lb_kernel<4><<<grid, kThreads, 0, s>>>(p); break;                  \
-  }                                                                                 \
-  scan_blocks_kernel<<<1, 1024, 0, s>>>(p.bsum1, p.nblk, p.ctl);                    \
-  tie_enqueue_kernel<<<grid, kThreads, 0, s>>>(p);                                  \
-  tie_count_kernel<DTV><<<gq, kThreads, 0, s>>>(p);                                 \
-  scan_blocks_kernel<<<1, 1024, 0, s>>>(p.bsum2, p.nblk, p.ctl);                    \
-  tie_emit_enqueue_kernel<<<grid, kThreads, 0, s>>>(p);                             \
-  switch (w.beta) {                                                                 \
-    case 1: tie_emit_kernel<DTV, 1><<<gq, kThreads, 0, s>>>(p); break;              \
-    case 2: tie_emit_kernel<DTV, 2><<<gq, kThreads, 0, s>>>(p); break;              \
-    case 3: tie_emit_kernel<DTV, 3><<<gq, kThreads, 0, s>>>(p); break;              \
-    default: tie_emit_kernel<DTV, 4><<<gq, kThreads, 0, s>>>(p); break;             \
+  // look-back words and tile lower bounds start at zero
+  cudaError_t e = cudaMemsetAsync(w.tstat, 0, static_cast<size_t>(p.ntiles) * 12, s);
+  if (e != cudaSuccess) return e;
+  const int ga = static_cast<int>(std::min<int64_t>((p.S + kThreads * 4 - 1) / (kThreads * 4), int64_t(sms) * 8));
+  const int gc = static_cast<int>(std::min<int64_t>(p.ntiles, int64_t(sms)));
+#define DRTOPK_TIE_CASE(DTV, BV)                                                          \
+  tie_lb_kernel<BV><<<ga, kThreads, 0, s>>>(p);                                           \
+  tie_plan_kernel<<<1, 1024, 0, s>>>(p);                                                  \
+  cudaFuncSetAttribute(tie_emit_kernel<DTV, BV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                       kTieBufBytes);                                                     \
+  tie_emit_kernel<DTV, BV><<<gc, kThreads, kTieBufBytes, s>>>(p);
+#define DRTOPK_TIE_BETA(DTV)                    \
+  switch (w.beta) {                             \
+    case 1: DRTOPK_TIE_CASE(DTV, 1) break;      \
+    case 2: DRTOPK_TIE_CASE(DTV, 2) break;      \
+    case 3: DRTOPK_TIE_CASE(DTV, 3) break;      \
+    default: DRTOPK_TIE_CASE(DTV, 4) break;     \
   }
   switch (w.dtype) {
-    case DRTOPK_U32: DRTOPK_TIE_CASE(DRTOPK_U32); break;
-    case DRTOPK_I32: DRTOPK_TIE_CASE(DRTOPK_I32); break;
-    default: DRTOPK_TIE_CASE(DRTOPK_F32); break;
+    case DRTOPK_U32: DRTOPK_TIE_BETA(DRTOPK_U32); break;
+    case DRTOPK_I32: DRTOPK_TIE_BETA(DRTOPK_I32); break;
+    default: DRTOPK_TIE_BETA(DRTOPK_F32); break;
   }
+#undef DRTOPK_TIE_BETA
 #undef DRTOPK_TIE_CASE
-  note_launch(7);
+  note_launch(3);
   return cudaGetLastError();
 }
 

@@ -2,6 +2,9 @@
 // sorted descending, i.e. by key descending then index ascending (the
 // output order of top-k; the paper leaves it unstated), and written as the
 // input dtype's key bits plus int32 indices.
+// When the k-th key is tau (tie mode), W holds G (all keys > tau, unsorted)
+// followed by the ties at tau in index order, which are already in output
+// order: only the first |G| entries are sorted (m below).
 //   * k <= 4096: one CTA bitonic-sorts W in shared memory;
 //   * larger k: a stable LSD radix sort of the complemented composites
 //     (ascending) with 8-bit digits. One kernel histograms all 8 digits at
@@ -52,13 +55,20 @@ __device__ __forceinline__ void write_out(uint64_t c, int64_t j, int64_t k, int 
   }
 }
 
+// Entries of W that need sorting: all k, or |G| when the tail of W holds
+// the ties at tau in index order.
+__device__ __forceinline__ int64_t sort_count(const Ctl* ctl, int64_t k) {
+  return __ldcg(&ctl->mode) == kModeTies ? static_cast<int64_t>(__ldcg(&ctl->g_count)) : k;
+}
+
 __global__ void __launch_bounds__(1024) small_sort_kernel(const uint64_t* w, int k, int dtype,
                                                           uint32_t* out_keys, int32_t* out_idx,
                                                           uint32_t* out_kth, Ctl* ctl) {
   __shared__ uint64_t s[kSmallSort];
+  const int m = static_cast<int>(sort_count(ctl, k));
   int P = 1;
-  while (P < k) P <<= 1;
-  for (int i = threadIdx.x; i < P; i += blockDim.x) s[i] = (i < k) ? w[i] : 0ull;
+  while (P < m) P <<= 1;
+  for (int i = threadIdx.x; i < P; i += blockDim.x) s[i] = (i < m) ? w[i] : 0ull;
   __syncthreads();
   // bitonic sort, descending
   for (int size = 2; size <= P; size <<= 1) {
@@ -78,7 +88,7 @@ __global__ void __launch_bounds__(1024) small_sort_kernel(const uint64_t* w, int
     }
   }
   for (int i = threadIdx.x; i < k; i += blockDim.x)
-    write_out(s[i], i, k, dtype, out_keys, out_idx, out_kth, ctl);
+    write_out(i < m ? s[i] : w[i], i, k, dtype, out_keys, out_idx, out_kth, ctl);
 }
 
 struct SortParams {
@@ -100,10 +110,11 @@ __global__ void __launch_bounds__(kHistThreads) sort_hist_all_kernel(SortParams 
   __syncthreads();
   const uint64_t* src = p.buf[0];
   const uint32_t lane = lane_id();
-  for (int64_t b = int64_t(blockIdx.x) * kHistThreads; b < p.k;
+  const int64_t m = sort_count(p.ctl, p.k);
+  for (int64_t b = int64_t(blockIdx.x) * kHistThreads; b < m;
        b += int64_t(gridDim.x) * kHistThreads) {
     const int64_t i = b + threadIdx.x;
-    const bool act = i < p.k;
+    const bool act = i < m;
     const uint32_t am = __ballot_sync(0xFFFFFFFFu, act);
     if (act) {
       const uint64_t c = src[i];
@@ -136,7 +147,7 @@ __global__ void __launch_bounds__(kHistThreads) sort_hist_all_kernel(SortParams 
     for (int q = 0; q < 8; ++q) {
       const uint32_t e = block_scan_excl<kHistThreads>(v[q], nullptr);
       p.ctl->sort_hist[q][threadIdx.x] = e;
-      const int full = __syncthreads_or(v[q] == static_cast<uint32_t>(p.k));
+      const int full = __syncthreads_or(v[q] == static_cast<uint32_t>(m));
       if (threadIdx.x == 0) p.ctl->sort_skip[q] = full ? 1u : 0u;
     }
   }
@@ -162,10 +173,12 @@ __global__ void __launch_bounds__(kSortThreads, 1) sort_pass_kernel(SortParams p
   __shared__ uint32_t s_start[256];
   extern __shared__ __align__(16) uint64_t s_el[];  // kTile entries, then kTile u16 ranks
   uint16_t* s_rank = reinterpret_cast<uint16_t*>(s_el + kTile);
+  const int64_t m = sort_count(ctl, p.k);
   if (threadIdx.x == 0) s_tile = atomicAdd(&ctl->sort_tiles[pass], 1u);
   for (int q = threadIdx.x; q < kWarpsS * 256; q += kSortThreads) (&wcnt[0][0])[q] = 0;
   __syncthreads();
   const int64_t tile = s_tile;
+  if (tile * kTile >= m) return;  // beyond the entries to sort (nobody waits on it)
   const int warp = threadIdx.x >> 5;
   const uint32_t lane = lane_id();
   const int64_t w0 = tile * kTile + int64_t(warp) * kPerWarp;
@@ -178,12 +191,12 @@ __global__ void __launch_bounds__(kSortThreads, 1) sort_pass_kernel(SortParams p
 #pragma unroll
   for (int r = 0; r < kItems; ++r) {
     const int64_t i = w0 + r * 32 + lane;
-    c[r] = (i < p.k) ? src[i] : 0ull;
+    c[r] = (i < m) ? src[i] : 0ull;
   }
 #pragma unroll
   for (int r = 0; r < kItems; ++r) {
     const int64_t i = w0 + r * 32 + lane;
-    const bool act = i < p.k;
+    const bool act = i < m;
     const uint32_t am = __ballot_sync(0xFFFFFFFFu, act);
     if (act) {
       const uint32_t d = sdigit(c[r], pass);
@@ -263,13 +276,13 @@ __global__ void __launch_bounds__(kSortThreads, 1) sort_pass_kernel(SortParams p
 #pragma unroll
   for (int r = 0; r < kItems; ++r) {
     const int64_t i = w0 + r * 32 + lane;
-    if (i < p.k) {
+    if (i < m) {
       const uint32_t d = sdigit(c[r], pass);
       s_el[s_start[d] + wcnt[warp][d] + s_rank[warp * kPerWarp + r * 32 + lane]] = c[r];
     }
   }
   __syncthreads();
-  const int64_t tcount = imin64(kTile, p.k - tile * kTile);
+  const int64_t tcount = imin64(kTile, m - tile * kTile);
   for (int j = threadIdx.x; j < tcount; j += kSortThreads) {
     const uint64_t e = s_el[j];
     const uint32_t d = sdigit(e, pass);
@@ -286,9 +299,10 @@ __global__ void finalize_kernel(SortParams p, int dtype, uint32_t* out_keys, int
 #pragma unroll
   for (int q = 0; q < 8; ++q) par ^= (skip[q] == 0) ? 1u : 0u;
   const uint64_t* src = p.buf[par];
+  const int64_t m = sort_count(p.ctl, p.k);
   for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < p.k;
        j += int64_t(gridDim.x) * blockDim.x)
-    write_out(src[j], j, p.k, dtype, out_keys, out_idx, out_kth, p.ctl);
+    write_out(j < m ? src[j] : p.buf[0][j], j, p.k, dtype, out_keys, out_idx, out_kth, p.ctl);
 }
 
 }  // namespace
