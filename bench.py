@@ -21,6 +21,10 @@ Extra measurements in the same line:
                 persistent launch, default and autotuned parameters, against the
                 same rows as 4096 plain per-row calls (and those calls captured in
                 one CUDA graph);
+  ablations     candidate-ratio curves on UD (n in 2^24..2^30, k in 2^4..2^20)
+                and, at n = 2^30 on UD and ND, the method against beta = 1
+                (Rules 1+2 alone), Rule 2's filtering off, and the first select
+                stopped one digit early (all exact);
   served        Poisson arrivals of float32 requests (n log-uniform in
                 [2^12, 2^28], k log-uniform in [1, 2^14], N(0,1) or U[-1,1)
                 by coin flip) at offered loads {0.25 .. 1.2} x the plain mode's
@@ -70,6 +74,8 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="skip breakdown/context runs")
     ap.add_argument("--no-batched", action="store_true", help="skip the ragged batch")
     ap.add_argument("--no-served", action="store_true", help="skip the served workload")
+    ap.add_argument("--no-ablations", action="store_true",
+                    help="skip the candidate-ratio curves and the ablations")
     ap.add_argument("--batched-rows", type=int, default=4096,
                     help="rows of the ragged batch (the first rows of the 4096-row recipe)")
     ap.add_argument("--served-requests", type=int, default=2000,
@@ -341,6 +347,62 @@ def batched_measure(drtopk, inputs, dev, peak, rows=4096, reps=10):
     return out
 
 
+# ------------------------------------------------------------ ablations ----
+def ablations_measure(drtopk, inputs, dev, reps=3):
+    import torch
+    out = {"curves_workload": "UD u32 (seed 1), prefixes of one 2^30 array", "curves": [],
+           "ablations_workload": "n = 2^30 u32, UD (seed 1) and ND = round(N(1e8, 10)) (seed 1)",
+           "ablations": []}
+    ud = inputs.uniform_u32(1 << 30, 1, device=dev)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, r
+
+    for ln in (24, 26, 28, 30):
+        n = 1 << ln
+        x = ud[:n]
+        for lk in (4, 10, 16, 20):
+            k = 1 << lk
+            ok = torch.empty(k, dtype=torch.int32, device=dev)
+            oi = torch.empty(k, dtype=torch.int32, device=dev)
+            ms, _ = timed(lambda: drtopk.drtopk_topk(x, k, out_keys=ok, out_idx=oi, dtype="u32"))
+            _, _, _, st = drtopk.drtopk_topk_ex(x, k, want_kth=False, dtype="u32")
+            cand = st["greater"] + st["ties_needed"]
+            out["curves"].append({
+                "log2n": ln, "log2k": lk, "ms": ms, "gkeys_s": n / ms / 1e6,
+                "alpha": st["alpha"], "beta": st["beta"], "candidate_fraction": cand / n,
+                "workload_fraction": (st["beta"] * st["subranges"] + cand) / n,
+                "scanned_subranges": st["scanned"]})
+    nd = inputs.nd_u32(1 << 30, 1, device=dev)
+    variants = [("method", {}), ("beta1_rules_1_2", {"beta": 1}),
+                ("rule2_filter_off", {"no_filter": True}),
+                ("first_select_skips_last_digit", {"skip_last_digit": True})]
+    for name, x in (("UD", ud), ("ND", nd)):
+        for k in (1024, 1 << 20):
+            for vname, kw in variants:
+                ms, r = timed(lambda: drtopk.drtopk_topk_ablate(x, k, dtype="u32", **kw))
+                st = r[2]
+                cand = st["greater"] + st["ties_needed"]
+                out["ablations"].append({
+                    "input": name, "k": k, "variant": vname, "ms": ms,
+                    "alpha": st["alpha"], "beta": st["beta"], "tau": st["tau"],
+                    "candidate_fraction": cand / x.numel(),
+                    "scanned_subranges": st["scanned"], "note": "each call synchronizes "
+                    "(statistics read back); times include that"})
+    del ud, nd
+    torch.cuda.empty_cache()
+    return out
+
+
 # --------------------------------------------------------------- served ----
 def served_measure(drtopk, dev, arrivals, budget=64 << 30, pool=192, seed=5):
     import numpy as np
@@ -572,6 +634,8 @@ def main():
             "note": "paper number is V100S (1134 GB/s), context only"}
         del ud
 
+    if not args.no_ablations and world == 1:
+        out["ablations"] = ablations_measure(drtopk, inputs, dev)
     if not args.no_batched and world == 1:
         out["batched"] = batched_measure(drtopk, inputs, dev, peak, rows=args.batched_rows)
     if not args.no_served and world == 1:

@@ -138,6 +138,24 @@ drtopk_status drtopk_topk_ex(const void* keys, drtopk_dtype dtype, int64_t n,
                              drtopk_stats* stats, void* stream);
 
 /*
+ * Ablations of the method (Sec. 5's ablation study; results stay exact):
+ *   DRTOPK_ABLATE_NO_FILTER: Rule 2's filtering off: every subrange whose
+ *     maximum delegate reaches tau (Rule 1) is concatenated whole, not only
+ *     its keys above tau; the candidate workspace grows to n.
+ *   DRTOPK_ABLATE_SKIP_LAST_DIGIT: the first top-k stops one 8-bit digit
+ *     early (Sec. 3.3): tau = the k-th largest delegate with its low byte
+ *     cleared, a lower threshold; the candidate workspace grows to n.
+ * beta = 1 is Rules 1 + 2 alone (no Rule 3). alpha / beta as for
+ * drtopk_topk_ex; stats optional (HOST; synchronizes `stream` when given).
+ * Never served from the graph cache.
+ */
+#define DRTOPK_ABLATE_NO_FILTER 1
+#define DRTOPK_ABLATE_SKIP_LAST_DIGIT 2
+drtopk_status drtopk_topk_ablate(const void* keys, drtopk_dtype dtype, int64_t n, int64_t k,
+                                 int alpha, int beta, int flags, void* out_keys,
+                                 int32_t* out_idx, drtopk_stats* stats, void* stream);
+
+/*
  * The delegate pass alone (Sec. 3.1, 3.3, 4.1), exposed as a stage. For
  * each subrange i of 2^alpha keys (the last may be shorter) writes its beta
  * largest keys, order-mapped, to d_keys[i*beta + j] (descending, ties by

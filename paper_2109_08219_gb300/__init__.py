@@ -85,6 +85,8 @@ def lib():
         L.drtopk_topk_ex.argtypes = [p, i32, i64, i64, i32, i32, p, p, p,
                                      ctypes.POINTER(Stats), p]
         L.drtopk_delegates.argtypes = [p, i32, i64, i32, i32, p, p, p]
+        L.drtopk_topk_ablate.argtypes = [p, i32, i64, i64, i32, i32, i32, p, p,
+                                         ctypes.POINTER(Stats), p]
         L.drtopk_topk_host.argtypes = [p, i32, i64, i64, p, p, p]
         L.drtopk_kth_noalloc.argtypes = [p, i32, i64, i64, p, p]
         L.drtopk_kth_noalloc.restype = i32
@@ -115,7 +117,7 @@ def lib():
         L.drtopk_tune_get.argtypes = [i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
         L.drtopk_tune_set.argtypes = [i32, i32, i32, i32]
         L.drtopk_autotune_batched.argtypes = [i32, i32, i32, i32, p]
-        for fn in ("drtopk_plan", "drtopk_kth", "drtopk_topk", "drtopk_topk_ex",
+        for fn in ("drtopk_plan", "drtopk_kth", "drtopk_topk", "drtopk_topk_ex", "drtopk_topk_ablate",
                    "drtopk_delegates", "drtopk_topk_host", "drtopk_profile_begin",
                    "drtopk_profile_end", "drtopk_batch_plan_create", "drtopk_batch_plan_run",
                    "drtopk_batch_plan_status", "drtopk_batch_plan_params",
@@ -240,6 +242,27 @@ def drtopk_topk_ex(keys, k, alpha=0, beta=0, want_topk=True, want_kth=True, dtyp
                               ctypes.byref(st) if st is not None else None, _stream(stream))
     _check(rc, "drtopk_topk_ex")
     return ok, oi, ot, (st.as_dict() if st is not None else None)
+
+
+ABLATE_NO_FILTER = 1
+ABLATE_SKIP_LAST_DIGIT = 2
+
+
+def drtopk_topk_ablate(keys, k, alpha=0, beta=0, no_filter=False, skip_last_digit=False,
+                       dtype=None, stream=None):
+    """Top-k with an ablation of the method (drtopk_topk_ablate): Rule 2's
+    filtering off and/or the first select stopped one digit early. Returns
+    (out_keys, out_idx, stats dict); synchronizes the stream."""
+    import torch
+    code = _dtype_code(keys, dtype)
+    out_keys = torch.empty(k, dtype=keys.dtype, device=keys.device)
+    out_idx = torch.empty(k, dtype=torch.int32, device=keys.device)
+    st = Stats()
+    flags = (ABLATE_NO_FILTER if no_filter else 0) | (ABLATE_SKIP_LAST_DIGIT if skip_last_digit else 0)
+    _check(lib().drtopk_topk_ablate(_dev(keys), code, keys.numel(), k, alpha, beta, flags,
+                                    _dev(out_keys), _dev(out_idx), ctypes.byref(st),
+                                    _stream(stream)), "drtopk_topk_ablate")
+    return out_keys, out_idx, st.as_dict()
 
 
 def drtopk_delegates(keys, alpha, beta, dtype=None, stream=None):

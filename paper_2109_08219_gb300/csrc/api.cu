@@ -24,6 +24,7 @@ struct Plan {
   int64_t S;
   int64_t g_cap;
   bool fuse_hist;  // beta * S >= k: tau from the delegates, else tau = 0
+  int ablate = 0;
 };
 
 int alpha_rule4(int64_t n, int64_t k) {
@@ -32,7 +33,7 @@ int alpha_rule4(int64_t n, int64_t k) {
   return static_cast<int>(std::floor(a));
 }
 
-bool make_plan(int64_t n, int64_t k, int alpha, int beta, Plan* p) {
+bool make_plan(int64_t n, int64_t k, int alpha, int beta, Plan* p, int ablate = 0) {
   if (beta <= 0) beta = 2;  // Sec. 3.3: beta = 2 performs best
   if (beta < 1 || beta > kMaxBeta) return false;
   if (alpha <= 0) {
@@ -53,7 +54,11 @@ bool make_plan(int64_t n, int64_t k, int alpha, int beta, Plan* p) {
   } else {
     p->g_cap = n;
   }
+  // the candidate bound assumes both Rule 2's filtering and tau = the exact
+  // k-th delegate: without either, candidates are bounded by n only
+  if (ablate & (kAblateNoFilter | kAblateSkipLastDigit)) p->g_cap = n;
   if (p->g_cap < 1) p->g_cap = 1;
+  p->ablate = ablate;
   return true;
 }
 
@@ -190,6 +195,7 @@ void bind_work(Work& w, char* ws, const Layout& L, const Plan& P, int64_t n, int
   w.alpha = P.alpha;
   w.beta = P.beta;
   w.dtype = dtype;
+  w.ablate = P.ablate;
 }
 
 // Every launch of one query, in order, on stream s (no allocation, no sync).
@@ -390,7 +396,7 @@ bool run_graph(const Plan& P, const void* keys, int dtype, int64_t n, int64_t k,
 
 drtopk_status run_query(const void* keys, int dtype, int64_t n, int64_t k, int alpha, int beta,
                         void* out_keys, int32_t* out_idx, void* out_kth, drtopk_stats* stats,
-                        cudaStream_t s, bool allow_graph) {
+                        cudaStream_t s, bool allow_graph, int ablate = 0) {
   drtopk_status st = check_args(keys, dtype, n, k);
   if (st != DRTOPK_OK) return st;
   const bool topk = out_keys != nullptr || out_idx != nullptr;
@@ -398,11 +404,12 @@ drtopk_status run_query(const void* keys, int dtype, int64_t n, int64_t k, int a
   if (alpha > 0 && (alpha < kMinAlpha || alpha > kMaxAlpha)) return DRTOPK_ERR_INVALID;
   if (beta > kMaxBeta) return DRTOPK_ERR_INVALID;
   Plan P;
-  if (!make_plan(n, k, alpha, beta, &P)) return DRTOPK_ERR_INVALID;
+  if (!make_plan(n, k, alpha, beta, &P, ablate)) return DRTOPK_ERR_INVALID;
   int sms = 0;
   st = dev_info(&sms);
   if (st != DRTOPK_OK) return st;
   const bool prof = profiling_on();
+  if (ablate) allow_graph = false;  // the graph cache keys on the method as stated
 
   // profiled calls run the direct path: its stage events sit between launches
   if (allow_graph && !stats && !prof && graph_cache_enabled() &&
@@ -506,6 +513,16 @@ drtopk_status drtopk_topk_ex(const void* keys, drtopk_dtype dtype, int64_t n, in
   if (alpha < 0 || beta < 0) return DRTOPK_ERR_INVALID;
   return run_query(keys, dtype, n, k, alpha, beta, out_keys, out_idx, out_kth, stats,
                    static_cast<cudaStream_t>(stream), true);
+}
+
+drtopk_status drtopk_topk_ablate(const void* keys, drtopk_dtype dtype, int64_t n, int64_t k,
+                                 int alpha, int beta, int flags, void* out_keys, int32_t* out_idx,
+                                 drtopk_stats* stats, void* stream) {
+  if (!out_keys || !out_idx) return DRTOPK_ERR_INVALID;
+  if (alpha < 0 || beta < 0 || (flags & ~(DRTOPK_ABLATE_NO_FILTER | DRTOPK_ABLATE_SKIP_LAST_DIGIT)))
+    return DRTOPK_ERR_INVALID;
+  return run_query(keys, dtype, n, k, alpha, beta, out_keys, out_idx, nullptr, stats,
+                   static_cast<cudaStream_t>(stream), false, flags);
 }
 
 drtopk_status drtopk_delegates(const void* keys, drtopk_dtype dtype, int64_t n, int alpha,

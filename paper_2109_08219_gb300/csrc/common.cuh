@@ -110,6 +110,13 @@ struct Ctl {
   uint32_t pad_;
 };
 
+// Ablations of the method (drtopk_topk_ablate): Rule 2's filtering off
+// (every subrange whose maximum delegate reaches tau is concatenated whole),
+// and the first top-k stopped one digit early (Sec. 3.3's shortcut: tau is
+// the k-th delegate with its low 8 bits cleared, a lower threshold).
+constexpr int kAblateNoFilter = 1;
+constexpr int kAblateSkipLastDigit = 2;
+
 // Device views of the workspace of one query.
 struct Work {
   uint32_t* dkeys;    // [S * beta] delegate keys (mapped), descending
@@ -131,6 +138,7 @@ struct Work {
   int alpha;
   int beta;
   int dtype;
+  int ablate;         // kAblate* flags, 0 for the method as stated
 };
 
 // -------------------------------------------------------- small helpers ---

@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(kThreads) thr_compact_kernel(const uint32_t* d
 __global__ void __launch_bounds__(kThreads) thr_pass_kernel(const uint32_t* dsv,
                                                             const uint32_t* dkeys,
                                                             int64_t dcount, Ctl* ctl,
-                                                            int pass) {
+                                                            int pass, int last_pass) {
   __shared__ uint32_t sh[256];
   zero_hist(sh);
   __syncthreads();
@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(kThreads) thr_pass_kernel(const uint32_t* dsv,
   if (last_block_of(&st->ticket[pass], nact)) {
     if (threadIdx.x < 32) {
       select_digit<4>(st, pass, 32, false);
-      if (pass == 3 && threadIdx.x == 0) {
+      if (pass == last_pass && threadIdx.x == 0) {
         __threadfence();
         ctl->tau = static_cast<uint32_t>(__ldcg(&st->prefix));
         ctl->tau_ready = 1;
@@ -247,6 +247,7 @@ struct FilterParams {
   uint64_t* g;
   Ctl* ctl;
   int kth_only;
+  int no_filter;  // ablation: Rule 2 off
 };
 
 // Each thread classifies 4 subranges per step: skip (m^0 <= tau), queue
@@ -291,7 +292,10 @@ __global__ void __launch_bounds__(kThreads) filter_classify_kernel(FilterParams 
 #pragma unroll
     for (int u = 0; u < kClsSub; ++u) {
       const int64_t i = base + int64_t(u) * kThreads + threadIdx.x;
-      if (i < p.S && dk[u][0] > tau) {
+      if (p.no_filter) {
+        // Rule 1 alone: a subrange whose maximum delegate reaches tau is kept whole
+        if (i < p.S && dk[u][0] >= tau) scanm |= 1u << u;
+      } else if (i < p.S && dk[u][0] > tau) {
         if (dk[u][B - 1] > tau && sub_len(i, alpha, p.n) > B) {
           scanm |= 1u << u;
         } else {
@@ -363,7 +367,7 @@ __global__ void __launch_bounds__(kThreads) filter_scan_kernel(FilterParams p) {
       const int64_t gi = (int64_t(sq[u]) << alpha) + (v & mask);
       const bool ok = v < total && gi < p.n;
       x[u] = map_key<DT>(__ldg(p.keys + (ok ? gi : 0)));
-      if (ok && x[u] > tau) hit |= 1u << u;
+      if (ok && (x[u] > tau || p.no_filter)) hit |= 1u << u;
     }
     const uint32_t wt = __reduce_add_sync(0xFFFFFFFFu, __popc(hit));
     uint32_t wb, unused;
@@ -1056,9 +1060,13 @@ cudaError_t launch_threshold(const Work& w, int sms, cudaStream_t s) {
   const int g1 = grid_for(count, kThreads * 16, sms, 4);
   thr_compact_kernel<<<g1, kThreads, 0, s>>>(w.dkeys, count, w.ds, w.ctl);
   const int g2 = grid_for(count, kThreads * 8, sms, 4);
-  thr_pass_kernel<<<g2, kThreads, 0, s>>>(w.ds, w.dkeys, count, w.ctl, 2);
-  thr_pass_kernel<<<g2, kThreads, 0, s>>>(w.ds, w.dkeys, count, w.ctl, 3);
-  note_launch(3);
+  // the shortcut stops after digit 2: tau = the k-th delegate's top 24 bits
+  // (low byte 0), a lower threshold, still exact (the tie reading holds for
+  // any tau with at least k keys >= tau)
+  const bool skip_last = (w.ablate & kAblateSkipLastDigit) != 0;
+  thr_pass_kernel<<<g2, kThreads, 0, s>>>(w.ds, w.dkeys, count, w.ctl, 2, skip_last ? 2 : 3);
+  if (!skip_last) thr_pass_kernel<<<g2, kThreads, 0, s>>>(w.ds, w.dkeys, count, w.ctl, 3, 3);
+  note_launch(skip_last ? 2 : 3);
   return cudaGetLastError();
 }
 
@@ -1083,6 +1091,7 @@ cudaError_t launch_filter(const Work& w, const void* keys, bool kth_only, int sm
   p.g = w.g;
   p.ctl = w.ctl;
   p.kth_only = kth_only ? 1 : 0;
+  p.no_filter = (w.ablate & kAblateNoFilter) ? 1 : 0;
   const int g1 = grid_for(w.S, kThreads, sms, 8);
   // scanned keys are bounded by the G capacity (or n when tau = 0)
   const int g2 = grid_for(w.g_cap, kThreads * kScanKPT, sms, 8);

@@ -100,3 +100,12 @@ def test_plan_rejects_bad_sizes(L):
         drtopk.drtopk_plan(10, 11)
     with pytest.raises(drtopk.DrTopkError):
         drtopk.drtopk_plan(0, 1)
+
+
+def test_ablation_argument_checks(L):
+    p = ctypes.c_void_p(0x1000)
+    out = ctypes.c_void_p(0x2000)
+    assert L.drtopk_topk_ablate(p, 0, 100, 1, 0, 0, 4, out, out, None, None) == 1   # flag
+    assert L.drtopk_topk_ablate(p, 0, 100, 1, -1, 0, 1, out, out, None, None) == 1  # alpha
+    assert L.drtopk_topk_ablate(p, 0, 100, 0, 0, 0, 1, out, out, None, None) == 2   # k = 0
+    assert L.drtopk_topk_ablate(p, 0, 100, 1, 0, 0, 1, None, out, None, None) == 1  # outputs

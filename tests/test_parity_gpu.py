@@ -273,3 +273,28 @@ def test_queries_inside_a_user_graph():
         rk, ri = oracle.topk(bits, oracle.U32, k)
         assert np.array_equal(host_bits(ok), rk) and np.array_equal(oi.cpu().numpy(), ri), kind
         assert int(host_bits(kt)[0]) == oracle.kth(bits, oracle.U32, 7)
+
+
+@pytest.mark.parametrize("flags", [(True, False), (False, True), (True, True)])
+def test_ablations_stay_exact(flags):
+    """Rule 2 off and / or the first select stopped one digit early change
+    the candidate set, never the answer (Sec. 5 ablations)."""
+    no_filter, skip_last = flags
+    for kind in ("uniform", "few", "equal", "asc", "zipf", "normal"):
+        n = 200003
+        dt = "f32" if kind == "normal" else "u32"
+        bits = make(kind, n, 31, dt)
+        x = to_dev(bits, dt)
+        for beta in (1, 2):
+            for k in (1, 100, 5000, 70000):
+                ok, oi, st = drtopk.drtopk_topk_ablate(x, k, beta=beta, no_filter=no_filter,
+                                                       skip_last_digit=skip_last, dtype=dt)
+                _, _, _, base = drtopk.drtopk_topk_ex(x, k, beta=beta, dtype=dt)
+                rk, ri = oracle.topk(bits, DT[dt], k)
+                assert st["error"] == 0, st
+                assert np.array_equal(host_bits(ok), rk) and np.array_equal(oi.cpu().numpy(), ri), \
+                    (kind, beta, k, flags)
+                if skip_last:
+                    assert st["tau"] <= base["tau"] and (st["tau"] & 0xFF) == 0 or st["tau"] == 0
+                if no_filter and not skip_last:
+                    assert st["greater"] >= base["greater"]  # whole subranges kept
