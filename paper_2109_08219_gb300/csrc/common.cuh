@@ -107,7 +107,7 @@ struct Ctl {
   uint32_t sort_hist[8][256];  // digit counts of the output composites
   uint32_t sort_skip[8];
   uint32_t tie_nlist;        // tiles listed for the tie emission
-  uint32_t pad_;
+  uint32_t tie_dense;        // the listed tiles are read whole (bulk copies)
 };
 
 // Ablations of the method (drtopk_topk_ablate): Rule 2's filtering off

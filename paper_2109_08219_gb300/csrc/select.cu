@@ -562,6 +562,9 @@ constexpr uint64_t kTieAgg = uint64_t(1) << 32;
 constexpr uint64_t kTieIncl = uint64_t(2) << 32;
 constexpr uint32_t kTieSpin = 1u << 22;
 constexpr uint32_t kTieInexact = 0x80000000u;
+// tile word: bits 0-15 lower bound, 16-29 inexact subranges, 31 inexact flag
+__device__ __forceinline__ uint32_t tlb_lb(uint32_t v) { return v & 0xFFFFu; }
+__device__ __forceinline__ uint32_t tlb_ninex(uint32_t v) { return (v >> 16) & 0x3FFFu; }
 
 __device__ __forceinline__ void st_relaxed_u64(uint64_t* p, uint64_t v) {
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
@@ -637,11 +640,11 @@ __global__ void __launch_bounds__(kThreads) tie_lb_kernel(TieParams p) {
       }
       for (int o = 1; o < grp; o <<= 1) {
         c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
-        x |= __shfl_xor_sync(0xFFFFFFFFu, x, o);
+        x += __shfl_xor_sync(0xFFFFFFFFu, x, o);  // inexact subranges of the group
       }
       if ((lane & (grp - 1)) == 0 && i < p.S && (c | x)) {
         const int t = static_cast<int>(i / p.tsub - t0);
-        if (c) atomicAdd(&s_lb[t], c);
+        atomicAdd(&s_lb[t], c | (x << 16));
         if (x) atomicOr(&s_lb[t], kTieInexact);
       }
     }
@@ -679,7 +682,7 @@ __global__ void __launch_bounds__(1024) tie_plan_kernel(TieParams p) {
 #pragma unroll
     for (int e = 0; e < kPer; ++e) {
       const int j = e * 1024 + tid;
-      if (j < cn) buf[pad(j)] = p.tlb[c0 + j] & ~kTieInexact;
+      if (j < cn) buf[pad(j)] = tlb_lb(p.tlb[c0 + j]);
     }
     __syncthreads();
     uint32_t v[kPer], sum = 0;
@@ -716,6 +719,7 @@ __global__ void __launch_bounds__(1024) tie_plan_kernel(TieParams p) {
   // pass 2: the list of tiles up to `last` that hold ties or are inexact,
   // each marked when no inexact tile precedes it
   uint32_t lbase = 0, xbase = 0;
+  uint64_t nin = 0;  // inexact subranges up to `last` (this thread's share)
   for (int64_t c0 = 0; c0 <= last; c0 += kTiePlanChunk) {
     const int cn = static_cast<int>(imin64(kTiePlanChunk, last + 1 - c0));
 #pragma unroll
@@ -731,6 +735,7 @@ __global__ void __launch_bounds__(1024) tie_plan_kernel(TieParams p) {
       v[e] = j < cn ? buf[pad(j)] : 0u;
       ci += v[e] != 0 ? 1u : 0u;  // holds ties or is inexact
       cx += (v[e] & kTieInexact) ? 1u : 0u;
+      nin += tlb_ninex(v[e]);
     }
     uint32_t ti, tx;
     uint32_t bi = lbase + block_scan_excl<1024>(ci, &ti);
@@ -746,7 +751,18 @@ __global__ void __launch_bounds__(1024) tie_plan_kernel(TieParams p) {
     xbase += tx;
     __syncthreads();
   }
-  if (tid == 0) ctl->tie_nlist = lbase;
+  // dense when most subranges up to `last` must be read: their tiles come
+  // whole by bulk copies; else a few subranges per tile, read directly
+  __shared__ unsigned long long s_nin;
+  if (tid == 0) s_nin = 0;
+  __syncthreads();
+  if (nin) atomicAdd(&s_nin, static_cast<unsigned long long>(nin));
+  __syncthreads();
+  if (tid == 0) {
+    ctl->tie_nlist = lbase;
+    const int64_t subs = imin64(p.S, (last + 1) * p.tsub);
+    ctl->tie_dense = (2 * static_cast<int64_t>(s_nin) > subs) ? 1u : 0u;
+  }
 }
 
 // The ties of a tile are ranked per 32-key segment. The tile's keys (when
@@ -784,41 +800,236 @@ __device__ __forceinline__ void tie_issue_copy(const uint32_t* keys, int64_t n, 
   *shift = s;
 }
 
+// Shared memory of one tile's tie work.
+struct TieTileSmem {
+  uint32_t seg[kTieMaxSeg];     // counts, then exclusive prefixes
+  uint32_t bits[kTieMaxSeg];    // tie bitmask per segment
+  uint32_t dc[kTieTileMaxSub];  // ties known from the delegates
+  uint8_t rd[kTieTileMaxSub];   // subrange read from its keys
+};
+
+// Counts the ties of tile t per 32-key segment and turns the counts into
+// exclusive prefixes; returns the tile's total (block-wide, all threads).
+// kTma: the tile comes whole by bulk copies (bounded waits; *timed_out set
+// on failure), else only the keys of the subranges read are loaded.
+template <int DT, int B, bool kTma>
+__device__ uint32_t tie_tile_count(const TieParams& p, int64_t t, uint32_t tau, TieTileSmem& sm,
+                                   unsigned char* tbuf, uint64_t* bar, uint32_t& phase,
+                                   uint64_t pol, uint32_t* s_shift, uint32_t& read_subs,
+                                   bool* timed_out) {
+  const int tid = threadIdx.x;
+  const uint32_t lane = lane_id();
+  const int alpha = p.alpha;
+  const int64_t i_lo = t * p.tsub;
+  const int64_t nsub = imin64(p.tsub, p.S - i_lo);
+  const int64_t klo = i_lo << alpha;
+  const int64_t khi = imin64(p.n, (i_lo + nsub) << alpha);
+  const int nseg = static_cast<int>((khi - klo + 31) >> 5);
+  *timed_out = false;
+  for (int q = tid; q < nseg; q += kThreads) {
+    sm.seg[q] = 0;
+    sm.bits[q] = 0;
+  }
+  __syncthreads();
+  uint32_t nread = 0;
+  for (int64_t ii = tid; ii < nsub; ii += kThreads) {
+    bool x;
+    const uint32_t c = tie_lb_of<B>(p, i_lo + ii, tau, &x);
+    const bool rd = alpha < 5 ? (c > 0 || x) : x;
+    sm.rd[ii] = rd ? 1 : 0;
+    sm.dc[ii] = rd ? 0u : c;
+    if (!rd && c > 0) sm.seg[static_cast<int>((ii << alpha) >> 5)] = c;  // alpha >= 5 here
+    nread += rd ? 1u : 0u;
+  }
+  read_subs += nread;
+  const int anyread = __syncthreads_or(nread > 0);
+  if (!kTma && anyread) {
+    // direct loads over the tile as one array, 4 in flight per thread, only
+    // the keys of subranges read (block-uniform trip count; a segment is one
+    // warp step)
+    for (int64_t xb = klo; xb < khi; xb += int64_t(kThreads) * 4) {
+      uint32_t v[4];
+      bool on[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t x = xb + tid + int64_t(u) * kThreads;
+        on[u] = x < khi && sm.rd[(x >> alpha) - i_lo];
+        v[u] = on[u] ? __ldg(p.keys + x) : 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t x = xb + tid + int64_t(u) * kThreads;
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, on[u] && map_key<DT>(v[u]) == tau);
+        if (lane == 0 && bal) {
+          const int seg = static_cast<int>((x - klo) >> 5);
+          sm.seg[seg] = __popc(bal);
+          sm.bits[seg] = bal;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  for (int64_t c0 = klo; kTma && anyread && c0 < khi; c0 += kTieTileKeys) {
+    const int64_t cn = imin64(kTieTileKeys, khi - c0);
+    if (tid == 0) {
+      int sh;
+      tie_issue_copy(p.keys, p.n, c0, cn, tbuf, bar, pol, &sh);
+      *s_shift = static_cast<uint32_t>(sh);
+    }
+    const bool ok = mbar_wait_bounded(bar, phase & 1u);
+    ++phase;
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicOr(&p.ctl->error, kErrTimeout);
+        mbar_wait_bounded(bar, (phase - 1) & 1u);  // let the copy land (bounded)
+      }
+      *timed_out = true;
+      return 0;
+    }
+    const uint32_t* kb = reinterpret_cast<const uint32_t*>(tbuf) + *s_shift;
+    for (int64_t xb = 0; xb < cn; xb += kThreads) {
+      const int64_t e = xb + tid;
+      const int64_t x = c0 + e;
+      const bool on = e < cn && sm.rd[(x >> alpha) - i_lo];
+      const uint32_t bal = __ballot_sync(0xFFFFFFFFu, on && map_key<DT>(kb[e]) == tau);
+      if (lane == 0 && bal) {
+        const int seg = static_cast<int>((x - klo) >> 5);
+        sm.seg[seg] = __popc(bal);
+        sm.bits[seg] = bal;
+      }
+    }
+    __syncthreads();  // the buffer is reused by the next copy
+    fence_proxy_async_smem();
+  }
+  // exclusive prefixes over the segments (8 consecutive per thread)
+  uint32_t tot = 0;
+  constexpr int kPer = kTieMaxSeg / kThreads;
+  uint32_t c[kPer];
+  uint32_t sum = 0;
+#pragma unroll
+  for (int e = 0; e < kPer; ++e) {
+    const int q = tid * kPer + e;
+    c[e] = q < nseg ? sm.seg[q] : 0u;
+    sum += c[e];
+  }
+  uint32_t run = block_scan_excl<kThreads>(sum, &tot);
+#pragma unroll
+  for (int e = 0; e < kPer; ++e) {
+    const int q = tid * kPer + e;
+    if (q < nseg) sm.seg[q] = run;
+    run += c[e];
+  }
+  __syncthreads();
+  return tot;
+}
+
+// Writes the ties of tile t whose ranks E + (prefix in the tile) are below
+// `need`, from the segment bitmasks and the delegates (block-wide).
 template <int DT, int B>
-__global__ void __launch_bounds__(kThreads, 1) tie_emit_kernel(TieParams p) {
-  Ctl* ctl = p.ctl;
-  if (__ldcg(&ctl->mode) != kModeTies) return;
-  const uint32_t tau = __ldcg(&ctl->tau);
-  const uint32_t need = __ldcg(&ctl->need);
-  const uint32_t g = __ldcg(&ctl->g_count);  // < k in this mode
-  const int64_t nl = __ldcg(&ctl->tie_nlist);
+__device__ void tie_tile_emit(const TieParams& p, int64_t t, uint32_t tau, uint32_t need,
+                              uint32_t g, uint32_t E, const TieTileSmem& sm, uint32_t& emitted) {
+  const int tid = threadIdx.x;
+  const uint32_t lane = lane_id();
+  const int warp = tid >> 5;
+  const int alpha = p.alpha;
+  const int64_t i_lo = t * p.tsub;
+  const int64_t nsub = imin64(p.tsub, p.S - i_lo);
+  const int64_t klo = i_lo << alpha;
+  const int64_t khi = imin64(p.n, (i_lo + nsub) << alpha);
+  const int nseg = static_cast<int>((khi - klo + 31) >> 5);
+  // from the bitmasks: a warp per segment, coalesced writes
+  for (int q = warp; q < nseg; q += kThreads / 32) {
+    const uint32_t bits = sm.bits[q];
+    const uint32_t r0 = E + sm.seg[q];
+    if (bits == 0 || r0 >= need) continue;
+    if ((bits >> lane) & 1u) {
+      const uint32_t r = r0 + __popc(bits & lanemask_lt());
+      if (r < need) {
+        p.w[g + r] = make_comp(tau, static_cast<uint32_t>(klo + int64_t(q) * 32 + lane));
+        ++emitted;
+      }
+    }
+  }
+  // subranges whose ties are all delegates (alpha >= 5), a warp each: D
+  // lists equal keys in index order (segment, then occurrence); the position
+  // is the occurrence-th key equal to tau in the 32-key segment, found by
+  // one coalesced read and a vote
+  for (int64_t ii = warp; ii < nsub; ii += kThreads / 32) {
+    if (sm.rd[ii] || sm.dc[ii] == 0) continue;
+    uint32_t r = E + sm.seg[static_cast<int>((ii << alpha) >> 5)];
+    if (r >= need) continue;
+    const int64_t i = i_lo + ii;
+    uint32_t dk[B];
+    uint16_t ds[B];
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+      dk[q] = p.dkeys[i * B + q];
+      ds[q] = p.dsegs[i * B + q];
+    }
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+      if (dk[q] == tau && ds[q] != kNoSeg && r < need) {
+        const int o = occ_rank<B>(dk, ds, q);
+        const int64_t lo = (i << alpha) + int64_t(ds[q]) * 32;
+        const int64_t hi = imin64(imin64(p.n, lo + 32), (i + 1) << alpha);
+        const bool m = lo + lane < hi && map_key<DT>(__ldg(p.keys + lo + lane)) == tau;
+        uint32_t bal = __ballot_sync(0xFFFFFFFFu, m);
+        for (int z = 0; z < o; ++z) bal &= bal - 1;
+        if (lane == 0) {
+          if (bal == 0) atomicOr(&p.ctl->error, kErrTieRank);
+          p.w[g + r] = make_comp(tau, static_cast<uint32_t>(lo + (bal ? __ffs(bal) - 1 : 0)));
+          ++emitted;
+        }
+        ++r;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void tie_copy_g(const TieParams& p, uint32_t g) {
   // G is part of the answer, in front of the ties
   for (int64_t j = int64_t(blockIdx.x) * kThreads + threadIdx.x; j < g;
        j += int64_t(gridDim.x) * kThreads)
     p.w[j] = p.g[j];
-  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&ctl->w_count, g);
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&p.ctl->w_count, g);
+}
 
+__device__ __forceinline__ void tie_finish(const TieParams& p, uint32_t read_subs,
+                                           uint32_t emitted) {
+  const uint32_t lane = lane_id();
+  read_subs = __reduce_add_sync(0xFFFFFFFFu, read_subs);
+  if (lane == 0 && read_subs) atomicAdd(&p.ctl->tie_scanned, read_subs);
+  emitted = __reduce_add_sync(0xFFFFFFFFu, emitted);
+  if (lane == 0 && emitted) atomicAdd(&p.ctl->w_count, emitted);
+}
+
+// Dense ties: the listed tiles walked in order (ticket), each read whole by
+// bulk copies; its prefix = lower-bound prefix + corrections of the earlier
+// listed tiles (decoupled look-back); the first tile reaching `need` cuts.
+template <int DT, int B>
+__global__ void __launch_bounds__(kThreads, 1) tie_walk_kernel(TieParams p) {
+  Ctl* ctl = p.ctl;
+  if (__ldcg(&ctl->mode) != kModeTies || __ldcg(&ctl->tie_dense) == 0) return;
+  const uint32_t tau = __ldcg(&ctl->tau);
+  const uint32_t need = __ldcg(&ctl->need);
+  const uint32_t g = __ldcg(&ctl->g_count);
+  const int64_t nl = __ldcg(&ctl->tie_nlist);
+  tie_copy_g(p, g);
   extern __shared__ __align__(128) unsigned char tbuf[];  // kTieBufBytes
-  __shared__ uint32_t s_seg[kTieMaxSeg];     // counts, then exclusive prefixes
-  __shared__ uint32_t s_bits[kTieMaxSeg];    // tie bitmask per segment
-  __shared__ uint32_t s_dc[kTieTileMaxSub];  // ties known from the delegates
-  __shared__ uint8_t s_read[kTieTileMaxSub];
+  __shared__ TieTileSmem sm;
   __shared__ __align__(8) uint64_t s_bar;
   __shared__ int64_t s_j, s_t;
   __shared__ uint32_t s_clean, s_go, s_E, s_shift;
   const int tid = threadIdx.x;
   const uint32_t lane = lane_id();
   const int warp = tid >> 5;
-  const int alpha = p.alpha;
   const uint64_t pol = l2_evict_first_policy();
   if (tid == 0) {
     mbar_init(&s_bar, 1);
     fence_mbar_init();
   }
   __syncthreads();
-  uint32_t phase = 0;  // copies completed on s_bar
-  uint32_t read_subs = 0;
-  uint32_t emitted = 0;  // ties written by this thread
+  uint32_t phase = 0, read_subs = 0, emitted = 0;
   for (;;) {
     if (tid == 0) {
       const int64_t j = atomicAdd(&ctl->tie_ticket, 1u);
@@ -834,87 +1045,12 @@ __global__ void __launch_bounds__(kThreads, 1) tie_emit_kernel(TieParams p) {
     __syncthreads();
     if (!s_go) break;
     const int64_t j = s_j, t = s_t;
-    const int64_t i_lo = t * p.tsub;
-    const int64_t nsub = imin64(p.tsub, p.S - i_lo);
-    const int64_t klo = i_lo << alpha;
-    const int64_t khi = imin64(p.n, (i_lo + nsub) << alpha);
-    const int nseg = static_cast<int>((khi - klo + 31) >> 5);
-    for (int q = tid; q < nseg; q += kThreads) {
-      s_seg[q] = 0;
-      s_bits[q] = 0;
-    }
-    __syncthreads();
-    uint32_t nread = 0;
-    for (int64_t ii = tid; ii < nsub; ii += kThreads) {
-      bool x;
-      const uint32_t c = tie_lb_of<B>(p, i_lo + ii, tau, &x);
-      const bool rd = alpha < 5 ? (c > 0 || x) : x;  // subrange read from its keys
-      s_read[ii] = rd ? 1 : 0;
-      s_dc[ii] = rd ? 0u : c;
-      if (!rd && c > 0) s_seg[static_cast<int>((ii << alpha) >> 5)] = c;  // alpha >= 5 here
-      nread += rd ? 1u : 0u;
-    }
-    read_subs += nread;
-    const int anyread = __syncthreads_or(nread > 0);
-    // tie bitmasks of the segments read, one chunk of the tile at a time
-    bool timed_out = false;
-    for (int64_t c0 = klo; anyread && c0 < khi; c0 += kTieTileKeys) {
-      const int64_t cn = imin64(kTieTileKeys, khi - c0);
-      if (tid == 0) {
-        int sh;
-        tie_issue_copy(p.keys, p.n, c0, cn, tbuf, &s_bar, pol, &sh);
-        s_shift = static_cast<uint32_t>(sh);
-      }
-      const bool ok = mbar_wait_bounded(&s_bar, phase & 1u);
-      ++phase;
-      if (__syncthreads_or(!ok)) {
-        if (tid == 0) {
-          atomicOr(&ctl->error, kErrTimeout);
-          mbar_wait_bounded(&s_bar, (phase - 1) & 1u);  // let the copy land (bounded)
-        }
-        timed_out = true;
-        break;
-      }
-      const uint32_t* kb = reinterpret_cast<const uint32_t*>(tbuf) + s_shift;
-      // 32 consecutive keys per warp step: one segment (block-uniform trip count)
-      for (int64_t xb = 0; xb < cn; xb += kThreads) {
-        const int64_t e = xb + tid;
-        const int64_t x = c0 + e;
-        const bool on = e < cn && s_read[(x >> alpha) - i_lo];
-        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, on && map_key<DT>(kb[e]) == tau);
-        if (lane == 0 && bal) {
-          const int seg = static_cast<int>((x - klo) >> 5);
-          s_seg[seg] = __popc(bal);
-          s_bits[seg] = bal;
-        }
-      }
-      __syncthreads();  // the buffer is reused by the next copy
-      fence_proxy_async_smem();
-    }
+    bool timed_out;
+    const uint32_t tot = tie_tile_count<DT, B, true>(p, t, tau, sm, tbuf, &s_bar, phase, pol,
+                                                     &s_shift, read_subs, &timed_out);
     if (timed_out) break;
-    // exclusive prefixes over the segments (8 consecutive per thread)
-    uint32_t tot = 0;
-    {
-      constexpr int kPer = kTieMaxSeg / kThreads;
-      uint32_t c[kPer];
-      uint32_t sum = 0;
-#pragma unroll
-      for (int e = 0; e < kPer; ++e) {
-        const int q = tid * kPer + e;
-        c[e] = q < nseg ? s_seg[q] : 0u;
-        sum += c[e];
-      }
-      uint32_t run = block_scan_excl<kThreads>(sum, &tot);
-#pragma unroll
-      for (int e = 0; e < kPer; ++e) {
-        const int q = tid * kPer + e;
-        if (q < nseg) s_seg[q] = run;
-        run += c[e];
-      }
-    }
-    // corrections of the earlier listed tiles (warp 0)
     if (warp == 0) {
-      const uint32_t corr = tot - (p.tlb[t] & ~kTieInexact);
+      const uint32_t corr = tot - tlb_lb(p.tlb[t]);
       uint32_t C = 0;
       bool skip = false;
       if (s_clean) {
@@ -962,45 +1098,239 @@ __global__ void __launch_bounds__(kThreads, 1) tie_emit_kernel(TieParams p) {
     }
     __syncthreads();
     const uint32_t E = s_E;
-    if (E < need) {
-      // ties from the bitmasks: a warp per segment, coalesced writes
-      for (int q = warp; q < nseg; q += kThreads / 32) {
-        const uint32_t bits = s_bits[q];
-        const uint32_t r0 = E + s_seg[q];
-        if (bits == 0 || r0 >= need) continue;
-        if ((bits >> lane) & 1u) {
-          const uint32_t r = r0 + __popc(bits & lanemask_lt());
-          if (r < need) {
-            p.w[g + r] = make_comp(tau, static_cast<uint32_t>(klo + int64_t(q) * 32 + lane));
+    if (E < need) tie_tile_emit<DT, B>(p, t, tau, need, g, E, sm, emitted);
+    __syncthreads();
+  }
+  tie_finish(p, read_subs, emitted);
+}
+
+// Sparse ties work per tile on its few "interesting" subranges (ties among
+// the delegates, or a subrange that must be read): they are listed in index
+// order, counted (a warp per subrange read, coalesced 32-key votes),
+// prefixed, and in step 3 written, a warp each.
+struct TieSparseSmem {
+  uint16_t sub[kTieTileMaxSub];  // interesting subranges, index order; bit 15: read
+  uint32_t cnt[kTieTileMaxSub];  // their tie counts, then exclusive prefixes
+  uint32_t n;                    // how many
+};
+
+template <int DT, int B>
+__device__ uint32_t tie_sparse_tile(const TieParams& p, int64_t t, uint32_t tau,
+                                    TieSparseSmem& sm, uint32_t& read_subs) {
+  const int tid = threadIdx.x;
+  const uint32_t lane = lane_id();
+  const int warp = tid >> 5;
+  const int alpha = p.alpha;
+  const int64_t i_lo = t * p.tsub;
+  const int nsub = static_cast<int>(imin64(p.tsub, p.S - i_lo));
+  constexpr int kPerT = kTieTileMaxSub / kThreads;
+  // classify kPerT consecutive subranges per thread, list them in order
+  uint32_t c[kPerT];
+  uint8_t flag[kPerT];  // 0 none, 1 delegates, 2 read
+  uint32_t mine = 0;
+#pragma unroll
+  for (int e = 0; e < kPerT; ++e) {
+    const int ii = tid * kPerT + e;
+    c[e] = 0;
+    flag[e] = 0;
+    if (ii < nsub) {
+      bool x;
+      c[e] = tie_lb_of<B>(p, i_lo + ii, tau, &x);
+      const bool rd = alpha < 5 ? (c[e] > 0 || x) : x;
+      flag[e] = rd ? 2 : (c[e] > 0 ? 1 : 0);
+    }
+    mine += flag[e] ? 1u : 0u;
+  }
+  uint32_t ni;
+  uint32_t pos = block_scan_excl<kThreads>(mine, &ni);
+#pragma unroll
+  for (int e = 0; e < kPerT; ++e) {
+    if (flag[e]) {
+      sm.sub[pos] = static_cast<uint16_t>((tid * kPerT + e) | (flag[e] == 2 ? 0x8000 : 0));
+      sm.cnt[pos] = flag[e] == 2 ? 0u : c[e];
+      ++pos;
+      if (flag[e] == 2) ++read_subs;
+    }
+  }
+  __syncthreads();
+  // exact counts of the subranges read: a warp each, 4 segments in flight
+  for (uint32_t q = warp; q < ni; q += kThreads / 32) {
+    const uint32_t e = sm.sub[q];
+    if (!(e & 0x8000)) continue;
+    const int64_t i = i_lo + (e & 0x7FFF);
+    const int64_t lo = i << alpha;
+    const int64_t len = sub_len(i, alpha, p.n);
+    uint32_t cntq = 0;
+    for (int64_t off = 0; off < len; off += 128) {
+      uint32_t v[4];
+      bool on[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t x = off + u * 32 + lane;
+        on[u] = x < len;
+        v[u] = on[u] ? __ldg(p.keys + lo + x) : 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        cntq += __popc(__ballot_sync(0xFFFFFFFFu, on[u] && map_key<DT>(v[u]) == tau));
+    }
+    if (lane == 0) sm.cnt[q] = cntq;
+  }
+  __syncthreads();
+  // exclusive prefixes (kPerT consecutive entries per thread)
+  uint32_t v[kPerT], sum = 0;
+#pragma unroll
+  for (int e = 0; e < kPerT; ++e) {
+    const uint32_t q = tid * kPerT + e;
+    v[e] = q < ni ? sm.cnt[q] : 0u;
+    sum += v[e];
+  }
+  uint32_t tot;
+  uint32_t run = block_scan_excl<kThreads>(sum, &tot);
+#pragma unroll
+  for (int e = 0; e < kPerT; ++e) {
+    const uint32_t q = tid * kPerT + e;
+    if (q < ni) sm.cnt[q] = run;  // prefix; the count is recomputed where needed
+    run += v[e];
+  }
+  if (tid == 0) sm.n = ni;
+  __syncthreads();
+  return tot;
+}
+
+// Sparse ties, step 1: exact tie count of every listed tile, in parallel.
+template <int DT, int B>
+__global__ void __launch_bounds__(kThreads, 4) tie_count_kernel(TieParams p) {
+  Ctl* ctl = p.ctl;
+  if (__ldcg(&ctl->mode) != kModeTies || __ldcg(&ctl->tie_dense) != 0) return;
+  const uint32_t tau = __ldcg(&ctl->tau);
+  const int64_t nl = __ldcg(&ctl->tie_nlist);
+  __shared__ TieSparseSmem sm;
+  uint32_t read_subs = 0;
+  for (int64_t j = blockIdx.x; j < nl; j += gridDim.x) {
+    const int64_t t = p.list[j] & ~kTieInexact;
+    const uint32_t tot = tie_sparse_tile<DT, B>(p, t, tau, sm, read_subs);
+    if (threadIdx.x == 0) p.tstat[j] = tot;
+  }
+}
+
+// Sparse ties, step 2 (one block): exclusive prefixes of the tiles' exact
+// counts in list order (in place), and the cut.
+__global__ void __launch_bounds__(1024) tie_scan_kernel(TieParams p) {
+  Ctl* ctl = p.ctl;
+  if (__ldcg(&ctl->mode) != kModeTies || __ldcg(&ctl->tie_dense) != 0) return;
+  const uint32_t need = __ldcg(&ctl->need);
+  const int64_t nl = __ldcg(&ctl->tie_nlist);
+  constexpr int kPer = kTiePlanChunk / 1024;
+  __shared__ uint32_t buf[kTiePlanChunk + kTiePlanChunk / 32];
+  __shared__ int64_t s_cut;
+  auto pad = [](int j) { return j + (j >> 5); };
+  const int tid = threadIdx.x;
+  if (tid == 0) s_cut = nl;
+  uint64_t base = 0;
+  for (int64_t c0 = 0; c0 < nl; c0 += kTiePlanChunk) {
+    const int cn = static_cast<int>(imin64(kTiePlanChunk, nl - c0));
+#pragma unroll
+    for (int e = 0; e < kPer; ++e) {
+      const int jj = e * 1024 + tid;
+      if (jj < cn) buf[pad(jj)] = static_cast<uint32_t>(p.tstat[c0 + jj]);
+    }
+    __syncthreads();
+    uint32_t v[kPer], sum = 0;
+#pragma unroll
+    for (int e = 0; e < kPer; ++e) {
+      const int jj = tid * kPer + e;
+      v[e] = jj < cn ? buf[pad(jj)] : 0u;
+      sum += v[e];
+    }
+    uint32_t tot;
+    uint64_t run = base + block_scan_excl<1024>(sum, &tot);
+    int64_t cut = -1;
+#pragma unroll
+    for (int e = 0; e < kPer; ++e) {
+      const int jj = tid * kPer + e;
+      if (jj < cn) {
+        buf[pad(jj)] = static_cast<uint32_t>(run < need ? run : need);
+        if (cut < 0 && run >= need) cut = c0 + jj;
+      }
+      run += v[e];
+    }
+    if (cut >= 0) atomicMin(reinterpret_cast<unsigned long long*>(&s_cut), static_cast<unsigned long long>(cut));
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < kPer; ++e) {
+      const int jj = e * 1024 + tid;
+      if (jj < cn) p.tstat[c0 + jj] = buf[pad(jj)];
+    }
+    base += tot;
+    __syncthreads();
+  }
+  if (tid == 0) ctl->tie_cut_inv = ~static_cast<uint32_t>(s_cut);  // first list entry not needed
+}
+
+// Sparse ties, step 3: the tiles before the cut write their ties, in
+// parallel (their prefixes are known), a warp per interesting subrange.
+template <int DT, int B>
+__global__ void __launch_bounds__(kThreads, 4) tie_place_kernel(TieParams p) {
+  Ctl* ctl = p.ctl;
+  if (__ldcg(&ctl->mode) != kModeTies || __ldcg(&ctl->tie_dense) != 0) return;
+  const uint32_t tau = __ldcg(&ctl->tau);
+  const uint32_t need = __ldcg(&ctl->need);
+  const uint32_t g = __ldcg(&ctl->g_count);
+  const int64_t cut = ~__ldcg(&ctl->tie_cut_inv);
+  const int64_t nl = imin64(__ldcg(&ctl->tie_nlist), cut);
+  tie_copy_g(p, g);
+  __shared__ TieSparseSmem sm;
+  const uint32_t lane = lane_id();
+  const int warp = threadIdx.x >> 5;
+  const int alpha = p.alpha;
+  uint32_t read_subs = 0, emitted = 0;
+  for (int64_t j = blockIdx.x; j < nl; j += gridDim.x) {
+    const int64_t t = p.list[j] & ~kTieInexact;
+    const uint32_t E = static_cast<uint32_t>(p.tstat[j]);
+    tie_sparse_tile<DT, B>(p, t, tau, sm, read_subs);
+    const int64_t i_lo = t * p.tsub;
+    for (uint32_t q = warp; q < sm.n; q += kThreads / 32) {
+      const uint32_t r0 = E + sm.cnt[q];
+      if (r0 >= need) continue;
+      const uint32_t e = sm.sub[q];
+      const int64_t i = i_lo + (e & 0x7FFF);
+      if (e & 0x8000) {
+        // read in index order and rank the ties
+        const int64_t lo = i << alpha;
+        const int64_t len = sub_len(i, alpha, p.n);
+        uint32_t run = 0;
+        for (int64_t off = 0; off < len && r0 + run < need; off += 32) {
+          const int64_t x = off + lane;
+          const bool is_t = x < len && map_key<DT>(__ldg(p.keys + lo + x)) == tau;
+          const uint32_t bal = __ballot_sync(0xFFFFFFFFu, is_t);
+          const uint32_t r = r0 + run + __popc(bal & lanemask_lt());
+          if (is_t && r < need) {
+            p.w[g + r] = make_comp(tau, static_cast<uint32_t>(lo + x));
             ++emitted;
           }
+          run += __popc(bal);
         }
-      }
-      // subranges whose ties are all delegates (alpha >= 5), a warp each:
-      // D lists equal keys in index order (segment, then occurrence); the
-      // position is the occurrence-th key equal to tau in the 32-key
-      // segment, found by one coalesced read and a vote
-      for (int64_t ii = warp; ii < nsub; ii += kThreads / 32) {
-        if (s_read[ii] || s_dc[ii] == 0) continue;
-        uint32_t r = E + s_seg[static_cast<int>((ii << alpha) >> 5)];
-        if (r >= need) continue;
-        const int64_t i = i_lo + ii;
+      } else {
+        // every tie is a delegate: D lists equal keys in index order; the
+        // position is the occurrence-th key equal to tau in its segment
         uint32_t dk[B];
         uint16_t ds[B];
 #pragma unroll
-        for (int q = 0; q < B; ++q) {
-          dk[q] = p.dkeys[i * B + q];
-          ds[q] = p.dsegs[i * B + q];
+        for (int z = 0; z < B; ++z) {
+          dk[z] = p.dkeys[i * B + z];
+          ds[z] = p.dsegs[i * B + z];
         }
+        uint32_t r = r0;
 #pragma unroll
-        for (int q = 0; q < B; ++q) {
-          if (dk[q] == tau && ds[q] != kNoSeg && r < need) {
-            const int o = occ_rank<B>(dk, ds, q);
-            const int64_t lo = (i << alpha) + int64_t(ds[q]) * 32;
+        for (int z = 0; z < B; ++z) {
+          if (dk[z] == tau && ds[z] != kNoSeg && r < need) {
+            const int o = occ_rank<B>(dk, ds, z);
+            const int64_t lo = (i << alpha) + int64_t(ds[z]) * 32;
             const int64_t hi = imin64(imin64(p.n, lo + 32), (i + 1) << alpha);
             const bool m = lo + lane < hi && map_key<DT>(__ldg(p.keys + lo + lane)) == tau;
             uint32_t bal = __ballot_sync(0xFFFFFFFFu, m);
-            for (int z = 0; z < o; ++z) bal &= bal - 1;
+            for (int y = 0; y < o; ++y) bal &= bal - 1;
             if (lane == 0) {
               if (bal == 0) atomicOr(&ctl->error, kErrTieRank);
               p.w[g + r] = make_comp(tau, static_cast<uint32_t>(lo + (bal ? __ffs(bal) - 1 : 0)));
@@ -1013,10 +1343,7 @@ __global__ void __launch_bounds__(kThreads, 1) tie_emit_kernel(TieParams p) {
     }
     __syncthreads();
   }
-  read_subs = __reduce_add_sync(0xFFFFFFFFu, read_subs);
-  if (lane == 0 && read_subs) atomicAdd(&ctl->tie_scanned, read_subs);
-  emitted = __reduce_add_sync(0xFFFFFFFFu, emitted);
-  if (lane == 0 && emitted) atomicAdd(&ctl->w_count, emitted);
+  tie_finish(p, read_subs, emitted);
 }
 
 // ----------------------------------------------------------- k-th output ---
@@ -1145,12 +1472,16 @@ cudaError_t launch_ties(const Work& w, const void* keys, int sms, cudaStream_t s
   if (e != cudaSuccess) return e;
   const int ga = static_cast<int>(std::min<int64_t>((p.S + kThreads * 4 - 1) / (kThreads * 4), int64_t(sms) * 8));
   const int gc = static_cast<int>(std::min<int64_t>(p.ntiles, int64_t(sms)));
-#define DRTOPK_TIE_CASE(DTV, BV)                                                          \
-  tie_lb_kernel<BV><<<ga, kThreads, 0, s>>>(p);                                           \
-  tie_plan_kernel<<<1, 1024, 0, s>>>(p);                                                  \
-  cudaFuncSetAttribute(tie_emit_kernel<DTV, BV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                       kTieBufBytes);                                                     \
-  tie_emit_kernel<DTV, BV><<<gc, kThreads, kTieBufBytes, s>>>(p);
+  const int gs = static_cast<int>(std::min<int64_t>(p.ntiles, int64_t(sms) * 4));
+#define DRTOPK_TIE_CASE(DTV, BV)                                                       \
+  tie_lb_kernel<BV><<<ga, kThreads, 0, s>>>(p);                                        \
+  tie_plan_kernel<<<1, 1024, 0, s>>>(p);                                               \
+  cudaFuncSetAttribute(tie_walk_kernel<DTV, BV>,                                       \
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, kTieBufBytes);     \
+  tie_walk_kernel<DTV, BV><<<gc, kThreads, kTieBufBytes, s>>>(p);                      \
+  tie_count_kernel<DTV, BV><<<gs, kThreads, 0, s>>>(p);                                \
+  tie_scan_kernel<<<1, 1024, 0, s>>>(p);                                               \
+  tie_place_kernel<DTV, BV><<<gs, kThreads, 0, s>>>(p);
 #define DRTOPK_TIE_BETA(DTV)                    \
   switch (w.beta) {                             \
     case 1: DRTOPK_TIE_CASE(DTV, 1) break;      \
@@ -1165,7 +1496,7 @@ cudaError_t launch_ties(const Work& w, const void* keys, int sms, cudaStream_t s
   }
 #undef DRTOPK_TIE_BETA
 #undef DRTOPK_TIE_CASE
-  note_launch(3);
+  note_launch(6);
   return cudaGetLastError();
 }
 
