@@ -66,8 +66,17 @@ constexpr size_t kAlign = 256;
 size_t al(size_t b) { return (b + kAlign - 1) & ~(kAlign - 1); }
 
 struct Layout {
-  size_t ctl, dkeys, dsegs, ds, scanq, g, sv, w, w2, tstat, sstat, total;
+  size_t ctl, dkeys, dsegs, ds, scanq, rq, g, sv, w, w2, tstat, sstat, total;
 };
+
+// Delegates the filter may queue for position resolution: those > tau,
+// fewer than k when tau is the k-th delegate (or all beta S of them when
+// there are fewer than k); every delegate under the shortcut ablation.
+int64_t rq_capacity(const Plan& p, int64_t k) {
+  const int64_t d = p.S * p.beta;
+  if (p.ablate & kAblateSkipLastDigit) return d;
+  return std::max<int64_t>(1, std::min(d, k));
+}
 
 Layout layout(const Plan& p, int64_t k, bool need_topk, bool external_dkeys) {
   Layout L;
@@ -78,6 +87,7 @@ Layout layout(const Plan& p, int64_t k, bool need_topk, bool external_dkeys) {
   L.dsegs = o; o += al(D * 2);
   L.ds = o; if (p.fuse_hist) o += al(D * 4);
   L.scanq = o; o += al(static_cast<size_t>(p.S) * 4);
+  L.rq = o; o += al(static_cast<size_t>(rq_capacity(p, k)) * 4);
   L.g = o; o += al(static_cast<size_t>(p.g_cap) * 8);
   L.sv = o; o += al(static_cast<size_t>(p.g_cap) * 8);
   L.w = o; if (need_topk) o += al(static_cast<size_t>(k) * 8);
@@ -182,6 +192,8 @@ void bind_work(Work& w, char* ws, const Layout& L, const Plan& P, int64_t n, int
   w.dsegs = reinterpret_cast<uint16_t*>(ws + L.dsegs);
   w.ds = reinterpret_cast<uint32_t*>(ws + L.ds);
   w.scanq = reinterpret_cast<uint32_t*>(ws + L.scanq);
+  w.rq = reinterpret_cast<uint32_t*>(ws + L.rq);
+  w.rq_cap = rq_capacity(P, k);
   w.g = reinterpret_cast<uint64_t*>(ws + L.g);
   w.sv = reinterpret_cast<uint64_t*>(ws + L.sv);
   w.w = reinterpret_cast<uint64_t*>(ws + L.w);

@@ -106,6 +106,7 @@ struct Ctl {
   uint32_t sort_tiles[8];    // dynamic tile ids of the output radix sort
   uint32_t sort_hist[8][256];  // digit counts of the output composites
   uint32_t sort_skip[8];
+  uint32_t rq_count;         // delegates queued for position resolution
   uint32_t tie_nlist;        // tiles listed for the tie emission
   uint32_t tie_dense;        // the listed tiles are read whole (bulk copies)
 };
@@ -123,6 +124,8 @@ struct Work {
   uint16_t* dsegs;    // [S * beta] delegate segment ids (kNoSeg = pad)
   uint32_t* ds;       // [S * beta] delegate keys surviving the first digit
   uint32_t* scanq;    // [S] subranges queued for the filter scan
+  uint32_t* rq;       // [rq_cap] delegates > tau to place (subrange << 2 | slot)
+  int64_t rq_cap;
   uint64_t* g;        // [g_cap] composites of {x > tau}
   uint64_t* sv;       // [g_cap] second-select ping-pong buffer
   uint64_t* w;        // [k] winners (unsorted), later sorted

@@ -59,8 +59,8 @@ extern "C" drtopk_status drtopk_kth_noalloc(const void* keys, drtopk_dtype dtype
 
   // The kernels of the k-selection path need: control block, delegate keys
   // and segments, the delegate keys kept by the first threshold digit, the
-  // queue of subranges to scan, the candidates above the threshold and
-  // their survivors.
+  // queues of subranges to scan and of delegates to place, the candidates
+  // above the threshold and their survivors.
   const int64_t S = (n + (int64_t(1) << alpha) - 1) >> alpha;
   int64_t g_cap = n;
   if (static_cast<int64_t>(beta) * S >= k)
@@ -70,7 +70,11 @@ extern "C" drtopk_status drtopk_kth_noalloc(const void* keys, drtopk_dtype dtype
   const size_t o_ds = o_dk + al(static_cast<size_t>(S) * beta * 4);
   const size_t o_dsv = o_ds + al(static_cast<size_t>(S) * beta * 2);
   const size_t o_q = o_dsv + al(static_cast<size_t>(S) * beta * 4);
-  const size_t o_g = o_q + al(static_cast<size_t>(S) * 4);
+  // delegates > tau queued for position resolution: fewer than k, or all
+  // beta S of them when there are fewer than k
+  const int64_t rq_cap = std::max<int64_t>(1, std::min<int64_t>(S * beta, k));
+  const size_t o_rq = o_q + al(static_cast<size_t>(S) * 4);
+  const size_t o_g = o_rq + al(static_cast<size_t>(rq_cap) * 4);
   const size_t o_sv = o_g + al(static_cast<size_t>(g_cap) * 8);
   const size_t total = o_sv + al(static_cast<size_t>(g_cap) * 8);
   if (total > kScratchBytes) return DRTOPK_ERR_NOMEM;  // does not fit the fixed scratch
@@ -90,6 +94,8 @@ extern "C" drtopk_status drtopk_kth_noalloc(const void* keys, drtopk_dtype dtype
   w.dsegs = reinterpret_cast<uint16_t*>(ws + o_ds);
   w.ds = reinterpret_cast<uint32_t*>(ws + o_dsv);
   w.scanq = reinterpret_cast<uint32_t*>(ws + o_q);
+  w.rq = reinterpret_cast<uint32_t*>(ws + o_rq);
+  w.rq_cap = rq_cap;
   w.g = reinterpret_cast<uint64_t*>(ws + o_g);
   w.sv = reinterpret_cast<uint64_t*>(ws + o_sv);
   w.n = n;

@@ -246,6 +246,8 @@ struct FilterParams {
   uint32_t* scanq;
   uint64_t* g;
   Ctl* ctl;
+  uint32_t* rq;   // delegates > tau to place: subrange << 2 | delegate slot
+  int64_t rq_cap;
   int kth_only;
   int no_filter;  // ablation: Rule 2 off
 };
@@ -260,13 +262,11 @@ constexpr int kClsQCap = kThreads * kClsSub * 2;
 
 template <int DT, int B>
 __global__ void __launch_bounds__(kThreads) filter_classify_kernel(FilterParams p) {
-  __shared__ uint32_t sh[256];
-  __shared__ uint64_t gbuf[kClsGCap];
+  __shared__ uint32_t rbuf[kClsGCap];
   __shared__ uint32_t qbuf[kClsQCap];
-  __shared__ uint32_t g_fill, q_fill;
-  zero_hist(sh);
+  __shared__ uint32_t r_fill, q_fill;
   if (threadIdx.x == 0) {
-    g_fill = 0;
+    r_fill = 0;
     q_fill = 0;
   }
   __syncthreads();
@@ -277,18 +277,14 @@ __global__ void __launch_bounds__(kThreads) filter_classify_kernel(FilterParams 
   for (int64_t base = int64_t(blockIdx.x) * per_step; base < p.S;
        base += int64_t(gridDim.x) * per_step) {
     uint32_t dk[kClsSub][B];
-    uint16_t ds[kClsSub][B];
 #pragma unroll
     for (int u = 0; u < kClsSub; ++u) {
       const int64_t i = base + int64_t(u) * kThreads + threadIdx.x;
 #pragma unroll
-      for (int j = 0; j < B; ++j) {
-        dk[u][j] = (i < p.S) ? p.dkeys[i * B + j] : 0u;
-        ds[u][j] = (i < p.S) ? p.dsegs[i * B + j] : static_cast<uint16_t>(kNoSeg);
-      }
+      for (int j = 0; j < B; ++j) dk[u][j] = (i < p.S) ? p.dkeys[i * B + j] : 0u;
     }
-    uint32_t scanm = 0, nitems = 0;
-    uint64_t items[kClsSub * B];
+    uint32_t scanm = 0, nreq = 0;
+    uint32_t req[kClsSub * B];
 #pragma unroll
     for (int u = 0; u < kClsSub; ++u) {
       const int64_t i = base + int64_t(u) * kThreads + threadIdx.x;
@@ -299,15 +295,11 @@ __global__ void __launch_bounds__(kThreads) filter_classify_kernel(FilterParams 
         if (dk[u][B - 1] > tau && sub_len(i, alpha, p.n) > B) {
           scanm |= 1u << u;
         } else {
+          // its keys > tau are exactly its delegates > tau (Rule 3); their
+          // positions are resolved by filter_resolve_kernel
 #pragma unroll
-          for (int j = 0; j < B; ++j) {
-            if (dk[u][j] > tau) {
-              const int r = occ_rank<B>(dk[u], ds[u], j);
-              const int64_t pos = resolve_pos<DT>(p.keys, p.n, alpha, i, ds[u][j], dk[u][j], r);
-              if (pos < 0) atomicOr(&p.ctl->error, kErrTieRank);
-              items[nitems++] = make_comp(dk[u][j], static_cast<uint32_t>(pos));
-            }
-          }
+          for (int j = 0; j < B; ++j)
+            if (dk[u][j] > tau) req[nreq++] = static_cast<uint32_t>(i << 2) | static_cast<uint32_t>(j);
         }
       }
     }
@@ -317,25 +309,131 @@ __global__ void __launch_bounds__(kThreads) filter_classify_kernel(FilterParams 
     for (int u = 0; u < kClsSub; ++u)
       if (scanm & (1u << u)) qbuf[qs++] = static_cast<uint32_t>(base + int64_t(u) * kThreads + threadIdx.x);
     nscan += __popc(scanm);
-    uint32_t gs = stage_reserve<uint64_t, kThreads, kClsGCap>(
-        gbuf, &g_fill, nitems, &p.ctl->g_count, p.g, static_cast<uint64_t>(p.g_cap), &p.ctl->error,
+    uint32_t rs = stage_reserve<uint32_t, kThreads, kClsGCap>(
+        rbuf, &r_fill, nreq, &p.ctl->rq_count, p.rq, static_cast<uint64_t>(p.rq_cap), &p.ctl->error,
         kErrOverflowG);
-    for (uint32_t e = 0; e < nitems; ++e) {
-      gbuf[gs + e] = items[e];
-      atomicAdd(&sh[static_cast<uint32_t>(items[e] >> 56)], 1u);
-    }
+    for (uint32_t e = 0; e < nreq; ++e) rbuf[rs + e] = req[e];
   }
   stage_flush<uint32_t, kThreads>(qbuf, &q_fill, &p.ctl->scanq_count, p.scanq, ~uint64_t(0),
                                   &p.ctl->error, 0u);
-  stage_flush<uint64_t, kThreads>(gbuf, &g_fill, &p.ctl->g_count, p.g,
-                                  static_cast<uint64_t>(p.g_cap), &p.ctl->error, kErrOverflowG);
-  flush_hist(sh, p.ctl->gsel.hist[0]);
+  stage_flush<uint32_t, kThreads>(rbuf, &r_fill, &p.ctl->rq_count, p.rq,
+                                  static_cast<uint64_t>(p.rq_cap), &p.ctl->error, kErrOverflowG);
   if (nscan) atomicAdd(&p.ctl->scanned, nscan);
 }
 
+// Positions of the queued delegates: the occurrence-th key equal to the
+// delegate in its 32-key segment, found by one coalesced read per request
+// and a vote. A warp takes 32 requests (lane u decodes request u), then
+// reads their segments 8 at a time (broadcast by shuffles, 8 reads in
+// flight); lane u keeps the composite of request u. The composites join G
+// (staged per block) and the histogram of their first digit. The last block
+// decides the query mode (G large enough, or ties at tau).
+constexpr int kResCap = kThreads * 4;
+
+template <int DT, int B>
+__global__ void __launch_bounds__(kThreads) filter_resolve_kernel(FilterParams p) {
+  __shared__ uint32_t sh[256];
+  __shared__ uint64_t gbuf[kResCap];
+  __shared__ uint32_t g_fill;
+  zero_hist(sh);
+  if (threadIdx.x == 0) g_fill = 0;
+  __syncthreads();
+  Ctl* ctl = p.ctl;
+  const int64_t nq = __ldcg(&ctl->rq_count);
+  const int alpha = p.alpha;
+  const uint32_t lane = lane_id();
+  const int warp = threadIdx.x >> 5;
+  for (int64_t b0 = int64_t(blockIdx.x) * kThreads; b0 < nq; b0 += int64_t(gridDim.x) * kThreads) {
+    const int64_t q = b0 + threadIdx.x;  // this lane's request
+    uint32_t key = 0;
+    int64_t lo = 0, hi = 0;
+    int occ = 0;
+    if (q < nq) {
+      const uint32_t r = p.rq[q];
+      const int64_t i = r >> 2;
+      const int j = static_cast<int>(r & 3u);
+      uint32_t dk[B];
+      uint16_t ds[B];
+#pragma unroll
+      for (int z = 0; z < B; ++z) {
+        dk[z] = p.dkeys[i * B + z];
+        ds[z] = p.dsegs[i * B + z];
+      }
+      // register selects (j is data-dependent): no local-memory arrays
+      uint32_t sj = 0;
+#pragma unroll
+      for (int z = 0; z < B; ++z) {
+        if (z == j) {
+          key = dk[z];
+          sj = ds[z];
+        }
+      }
+#pragma unroll
+      for (int z = 0; z < B; ++z) occ += (z < j && dk[z] == key && ds[z] == sj) ? 1 : 0;
+      lo = (i << alpha) + int64_t(sj) * 32;
+      hi = imin64(imin64(p.n, lo + 32), (i + 1) << alpha);
+    }
+    uint64_t item = 0;
+    const bool has = q < nq;
+#pragma unroll
+    for (int g8 = 0; g8 < 4; ++g8) {
+      uint32_t x[8], kk[8];
+      int64_t l8[8], h8[8];
+      int o8[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int src = g8 * 8 + u;
+        kk[u] = __shfl_sync(0xFFFFFFFFu, key, src);
+        l8[u] = __shfl_sync(0xFFFFFFFFu, lo, src);
+        h8[u] = __shfl_sync(0xFFFFFFFFu, hi, src);
+        o8[u] = __shfl_sync(0xFFFFFFFFu, occ, src);
+        x[u] = l8[u] + lane < h8[u] ? __ldg(p.keys + l8[u] + lane) : 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        uint32_t bal = __ballot_sync(0xFFFFFFFFu, l8[u] + lane < h8[u] && map_key<DT>(x[u]) == kk[u]);
+        for (int z = 0; z < o8[u]; ++z) bal &= bal - 1;
+        if (static_cast<int>(lane) == g8 * 8 + u && has) {
+          if (bal == 0) atomicOr(&ctl->error, kErrTieRank);
+          item = make_comp(key, static_cast<uint32_t>(lo + (bal ? __ffs(bal) - 1 : 0)));
+        }
+      }
+    }
+    (void)warp;
+    const uint32_t slot = stage_reserve<uint64_t, kThreads, kResCap>(
+        gbuf, &g_fill, has ? 1u : 0u, &ctl->g_count, p.g, static_cast<uint64_t>(p.g_cap),
+        &ctl->error, kErrOverflowG);
+    if (has) {
+      gbuf[slot] = item;
+      atomicAdd(&sh[static_cast<uint32_t>(item >> 56)], 1u);
+    }
+  }
+  stage_flush<uint64_t, kThreads>(gbuf, &g_fill, &ctl->g_count, p.g, static_cast<uint64_t>(p.g_cap),
+                                  &ctl->error, kErrOverflowG);
+  flush_hist(sh, ctl->gsel.hist[0]);
+  if (last_block(&ctl->filter_ticket)) {
+    if (threadIdx.x < 32) {
+      const uint32_t g = __ldcg(&ctl->g_count);
+      const uint64_t k = static_cast<uint64_t>(p.k);
+      if (g >= k) {
+        if (threadIdx.x == 0) {
+          ctl->mode = kModeSelect;
+          ctl->gsel.k_rem = static_cast<uint32_t>(k);
+        }
+        __syncwarp();
+        __threadfence();
+        select_digit<8>(&ctl->gsel, 0, 64, !p.kth_only);
+      } else if (threadIdx.x == 0) {
+        ctl->mode = kModeTies;
+        ctl->need = static_cast<uint32_t>(k - g);
+        ctl->kth_mapped = __ldcg(&ctl->tau);
+      }
+    }
+  }
+}
+
 // All queued subranges read as one virtual array of nq * 2^alpha keys,
-// 8192 per block step, appended with one atomic per block step. The last
-// block decides the query mode.
+// 8192 per block step, appended with one atomic per block step.
 template <int DT>
 __global__ void __launch_bounds__(kThreads) filter_scan_kernel(FilterParams p) {
   __shared__ uint32_t sh[256];
@@ -392,26 +490,6 @@ __global__ void __launch_bounds__(kThreads) filter_scan_kernel(FilterParams p) {
   rh.flush(sh);
   __syncthreads();
   flush_hist(sh, p.ctl->gsel.hist[0]);
-  if (last_block_of(&p.ctl->filter_ticket, nact)) {
-    if (threadIdx.x < 32) {
-      Ctl* ctl = p.ctl;
-      const uint32_t g = __ldcg(&ctl->g_count);
-      const uint64_t k = static_cast<uint64_t>(p.k);
-      if (g >= k) {
-        if (threadIdx.x == 0) {
-          ctl->mode = kModeSelect;
-          ctl->gsel.k_rem = static_cast<uint32_t>(k);
-        }
-        __syncwarp();
-        __threadfence();
-        select_digit<8>(&ctl->gsel, 0, 64, !p.kth_only);
-      } else if (threadIdx.x == 0) {
-        ctl->mode = kModeTies;
-        ctl->need = static_cast<uint32_t>(k - g);
-        ctl->kth_mapped = tau;
-      }
-    }
-  }
 }
 
 // --------------------------------------------------------- second select ---
@@ -1398,9 +1476,10 @@ cudaError_t launch_threshold(const Work& w, int sms, cudaStream_t s) {
 }
 
 template <int DT, int B>
-static void filter_t(const FilterParams& p, int g1, int g2, cudaStream_t s) {
+static void filter_t(const FilterParams& p, int g1, int g2, int g3, cudaStream_t s) {
   filter_classify_kernel<DT, B><<<g1, kThreads, 0, s>>>(p);
   filter_scan_kernel<DT><<<g2, kThreads, 0, s>>>(p);
+  filter_resolve_kernel<DT, B><<<g3, kThreads, 0, s>>>(p);
 }
 
 cudaError_t launch_filter(const Work& w, const void* keys, bool kth_only, int sms,
@@ -1419,15 +1498,19 @@ cudaError_t launch_filter(const Work& w, const void* keys, bool kth_only, int sm
   p.ctl = w.ctl;
   p.kth_only = kth_only ? 1 : 0;
   p.no_filter = (w.ablate & kAblateNoFilter) ? 1 : 0;
+  p.rq = w.rq;
+  p.rq_cap = w.rq_cap;
   const int g1 = grid_for(w.S, kThreads, sms, 8);
+  // requests to resolve: at most rq_cap, one per thread per block step
+  const int g3 = grid_for(w.rq_cap, kThreads, sms, 4);
   // scanned keys are bounded by the G capacity (or n when tau = 0)
   const int g2 = grid_for(w.g_cap, kThreads * kScanKPT, sms, 8);
 #define DRTOPK_FILTER_CASE(DTV)                              \
   switch (w.beta) {                                          \
-    case 1: filter_t<DTV, 1>(p, g1, g2, s); break;           \
-    case 2: filter_t<DTV, 2>(p, g1, g2, s); break;           \
-    case 3: filter_t<DTV, 3>(p, g1, g2, s); break;           \
-    default: filter_t<DTV, 4>(p, g1, g2, s); break;          \
+    case 1: filter_t<DTV, 1>(p, g1, g2, g3, s); break;       \
+    case 2: filter_t<DTV, 2>(p, g1, g2, g3, s); break;       \
+    case 3: filter_t<DTV, 3>(p, g1, g2, g3, s); break;       \
+    default: filter_t<DTV, 4>(p, g1, g2, g3, s); break;      \
   }
   switch (w.dtype) {
     case DRTOPK_U32: DRTOPK_FILTER_CASE(DRTOPK_U32); break;
@@ -1435,7 +1518,7 @@ cudaError_t launch_filter(const Work& w, const void* keys, bool kth_only, int sm
     default: DRTOPK_FILTER_CASE(DRTOPK_F32); break;
   }
 #undef DRTOPK_FILTER_CASE
-  note_launch(2);
+  note_launch(3);
   return cudaGetLastError();
 }
 
