@@ -107,6 +107,9 @@ struct Ctl {
   uint32_t sort_hist[8][256];  // digit counts of the output composites
   uint32_t sort_skip[8];
   uint32_t rq_count;         // delegates queued for position resolution
+  uint32_t thr_lo_inv;       // ~(smallest delegate key in the first-digit bucket)
+  uint32_t thr_hi;           // largest delegate key in the first-digit bucket
+  uint32_t thr_done;         // tau found after digit 1 (the bucket holds one value)
   uint32_t tie_nlist;        // tiles listed for the tie emission
   uint32_t tie_dense;        // the listed tiles are read whole (bulk copies)
 };

@@ -149,7 +149,7 @@ constexpr int kThrStageCap = kThreads * 16;
 // the later passes read the delegate keys in place.
 __global__ void __launch_bounds__(kThreads) thr_compact_kernel(const uint32_t* dkeys,
                                                                int64_t count, uint32_t* ds,
-                                                               Ctl* ctl) {
+                                                               Ctl* ctl, int allow_done) {
   __shared__ uint32_t sh[256];
   __shared__ uint32_t sbuf[kThrStageCap];
   __shared__ uint32_t s_fill;
@@ -161,6 +161,7 @@ __global__ void __launch_bounds__(kThreads) thr_compact_kernel(const uint32_t* d
   const bool inplace = uint64_t(__ldcg(&st->bucket)) * 8 > static_cast<uint64_t>(count);
   if (inplace && blockIdx.x == 0 && threadIdx.x == 0) ctl->ds_inplace = 1;
   RunHist rh;
+  uint32_t lo = 0xFFFFFFFFu, hi = 0;  // range of the bucket's keys
   const int64_t step = int64_t(gridDim.x) * kThreads * 16;
   for (int64_t base = int64_t(blockIdx.x) * kThreads * 16; base < count; base += step) {
     uint32_t v[16];
@@ -172,6 +173,8 @@ __global__ void __launch_bounds__(kThreads) thr_compact_kernel(const uint32_t* d
       if (i < count && (v[e] >> 24) == d0) {
         hit |= 1u << e;
         rh.add(sh, (v[e] >> 16) & 255u);
+        lo = min(lo, v[e]);
+        hi = max(hi, v[e]);
       }
     }
     if (!inplace) {
@@ -185,10 +188,27 @@ __global__ void __launch_bounds__(kThreads) thr_compact_kernel(const uint32_t* d
   if (!inplace) stage_flush<uint32_t, kThreads>(sbuf, &s_fill, &ctl->ds_count, ds, ~uint64_t(0),
                                                 &ctl->error, 0u);
   rh.flush(sh);
+  lo = __reduce_min_sync(0xFFFFFFFFu, lo);
+  hi = __reduce_max_sync(0xFFFFFFFFu, hi);
+  if ((threadIdx.x & 31) == 0 && hi >= lo) {
+    atomicMax(&ctl->thr_lo_inv, ~lo);
+    atomicMax(&ctl->thr_hi, hi);
+  }
   __syncthreads();
   flush_hist(sh, st->hist[1]);
   if (last_block(&st->ticket[1])) {
     if (threadIdx.x < 32) select_digit<4>(st, 1, 32, false);
+    if (threadIdx.x == 0) {
+      // every key of the bucket holding the k-th delegate is the same: it is
+      // tau, and the digit 2 and 3 passes have nothing left to decide
+      const uint32_t blo = ~__ldcg(&ctl->thr_lo_inv), bhi = __ldcg(&ctl->thr_hi);
+      if (allow_done && blo == bhi) {
+        ctl->tau = bhi;
+        __threadfence();
+        ctl->tau_ready = 1;
+        ctl->thr_done = 1;
+      }
+    }
   }
 }
 
@@ -197,6 +217,7 @@ __global__ void __launch_bounds__(kThreads) thr_pass_kernel(const uint32_t* dsv,
                                                             const uint32_t* dkeys,
                                                             int64_t dcount, Ctl* ctl,
                                                             int pass, int last_pass) {
+  if (__ldcg(&ctl->thr_done)) return;  // tau already known
   __shared__ uint32_t sh[256];
   zero_hist(sh);
   __syncthreads();
@@ -1463,7 +1484,10 @@ __global__ void resolve_kernel(const uint32_t* keys, int64_t n, int64_t S, int a
 cudaError_t launch_threshold(const Work& w, int sms, cudaStream_t s) {
   const int64_t count = w.S * w.beta;
   const int g1 = grid_for(count, kThreads * 16, sms, 4);
-  thr_compact_kernel<<<g1, kThreads, 0, s>>>(w.dkeys, count, w.ds, w.ctl);
+  // the one-value shortcut after digit 1 is off under the ablation that
+  // stops the select one digit early (its tau must stay the truncated one)
+  thr_compact_kernel<<<g1, kThreads, 0, s>>>(w.dkeys, count, w.ds, w.ctl,
+                                             (w.ablate & kAblateSkipLastDigit) ? 0 : 1);
   const int g2 = grid_for(count, kThreads * 8, sms, 4);
   // the shortcut stops after digit 2: tau = the k-th delegate's top 24 bits
   // (low byte 0), a lower threshold, still exact (the tie reading holds for
