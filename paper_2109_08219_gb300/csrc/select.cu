@@ -646,7 +646,8 @@ struct TieParams {
   uint32_t* tlb;     // per tile: lower bound | inexact << 31
   uint32_t* lbpre;   // per tile: exclusive prefix of the lower bounds
   uint32_t* list;    // tiles to visit, index order; bit 31: no inexact tile before
-  int64_t tsub;      // subranges per tile
+  int64_t tsub;      // subranges per tile (a power of two)
+  int tsub_log;
   int64_t ntiles;
   const uint64_t* g;
   uint64_t* w;
@@ -676,22 +677,22 @@ __device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t* p) {
 
 // Ties at tau a subrange holds by its delegates, and whether non-delegates
 // may hold more (all beta delegates reach tau and the subrange is longer).
+// A delegate slot is real iff its index is below the subrange's length (the
+// delegate pass pads only the slots a short subrange cannot fill), so the
+// segment ids are not read here.
 template <int B>
 __device__ __forceinline__ uint32_t tie_lb_of(const TieParams& p, int64_t i, uint32_t tau,
                                               bool* inexact) {
   uint32_t dk[B];
-  uint16_t ds[B];
 #pragma unroll
-  for (int j = 0; j < B; ++j) {
-    dk[j] = p.dkeys[i * B + j];
-    ds[j] = p.dsegs[i * B + j];
-  }
+  for (int j = 0; j < B; ++j) dk[j] = p.dkeys[i * B + j];
   uint32_t c = 0;
   *inexact = false;
   if (dk[0] >= tau) {
+    const int64_t len = sub_len(i, p.alpha, p.n);
 #pragma unroll
-    for (int j = 0; j < B; ++j) c += (dk[j] == tau && ds[j] != kNoSeg) ? 1u : 0u;
-    *inexact = dk[B - 1] >= tau && sub_len(i, p.alpha, p.n) > B;
+    for (int j = 0; j < B; ++j) c += (dk[j] == tau && j < len) ? 1u : 0u;
+    *inexact = dk[B - 1] >= tau && len > B;
   }
   return c;
 }
@@ -714,35 +715,32 @@ __global__ void __launch_bounds__(kThreads) tie_lb_kernel(TieParams p) {
   __syncthreads();
   for (int64_t i0 = int64_t(blockIdx.x) * kThreads * kU; i0 < p.S;
        i0 += int64_t(gridDim.x) * kThreads * kU) {
-    const int64_t t0 = i0 / p.tsub;
+    const int64_t t0 = i0 >> p.tsub_log;
     const int nt_blk = static_cast<int>(
-        (imin64(p.S, i0 + int64_t(kThreads) * kU) - 1) / p.tsub - t0 + 1);
+        ((imin64(p.S, i0 + int64_t(kThreads) * kU) - 1) >> p.tsub_log) - t0 + 1);
     uint32_t dk[kU][B];
-    uint16_t ds[kU][B];
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       const int64_t i = i0 + int64_t(u) * kThreads + threadIdx.x;
 #pragma unroll
-      for (int q = 0; q < B; ++q) {
-        dk[u][q] = i < p.S ? p.dkeys[i * B + q] : 0u;
-        ds[u][q] = i < p.S ? p.dsegs[i * B + q] : static_cast<uint16_t>(kNoSeg);
-      }
+      for (int q = 0; q < B; ++q) dk[u][q] = i < p.S ? p.dkeys[i * B + q] : 0u;
     }
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       const int64_t i = i0 + int64_t(u) * kThreads + threadIdx.x;
       uint32_t c = 0, x = 0;
       if (i < p.S && dk[u][0] >= tau) {
+        const int64_t len = sub_len(i, p.alpha, p.n);
 #pragma unroll
-        for (int q = 0; q < B; ++q) c += (dk[u][q] == tau && ds[u][q] != kNoSeg) ? 1u : 0u;
-        x = (dk[u][B - 1] >= tau && sub_len(i, p.alpha, p.n) > B) ? 1u : 0u;
+        for (int q = 0; q < B; ++q) c += (dk[u][q] == tau && q < len) ? 1u : 0u;
+        x = (dk[u][B - 1] >= tau && len > B) ? 1u : 0u;
       }
       for (int o = 1; o < grp; o <<= 1) {
         c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
         x += __shfl_xor_sync(0xFFFFFFFFu, x, o);  // inexact subranges of the group
       }
       if ((lane & (grp - 1)) == 0 && i < p.S && (c | x)) {
-        const int t = static_cast<int>(i / p.tsub - t0);
+        const int t = static_cast<int>((i >> p.tsub_log) - t0);
         atomicAdd(&s_lb[t], c | (x << 16));
         if (x) atomicOr(&s_lb[t], kTieInexact);
       }
@@ -911,7 +909,7 @@ struct TieTileSmem {
 // exclusive prefixes; returns the tile's total (block-wide, all threads).
 // kTma: the tile comes whole by bulk copies (bounded waits; *timed_out set
 // on failure), else only the keys of the subranges read are loaded.
-template <int DT, int B, bool kTma>
+template <int DT, int B, bool kTma, int NT>
 __device__ uint32_t tie_tile_count(const TieParams& p, int64_t t, uint32_t tau, TieTileSmem& sm,
                                    unsigned char* tbuf, uint64_t* bar, uint32_t& phase,
                                    uint64_t pol, uint32_t* s_shift, uint32_t& read_subs,
@@ -925,13 +923,13 @@ __device__ uint32_t tie_tile_count(const TieParams& p, int64_t t, uint32_t tau, 
   const int64_t khi = imin64(p.n, (i_lo + nsub) << alpha);
   const int nseg = static_cast<int>((khi - klo + 31) >> 5);
   *timed_out = false;
-  for (int q = tid; q < nseg; q += kThreads) {
+  for (int q = tid; q < nseg; q += NT) {
     sm.seg[q] = 0;
     sm.bits[q] = 0;
   }
   __syncthreads();
   uint32_t nread = 0;
-  for (int64_t ii = tid; ii < nsub; ii += kThreads) {
+  for (int64_t ii = tid; ii < nsub; ii += NT) {
     bool x;
     const uint32_t c = tie_lb_of<B>(p, i_lo + ii, tau, &x);
     const bool rd = alpha < 5 ? (c > 0 || x) : x;
@@ -946,18 +944,18 @@ __device__ uint32_t tie_tile_count(const TieParams& p, int64_t t, uint32_t tau, 
     // direct loads over the tile as one array, 4 in flight per thread, only
     // the keys of subranges read (block-uniform trip count; a segment is one
     // warp step)
-    for (int64_t xb = klo; xb < khi; xb += int64_t(kThreads) * 4) {
+    for (int64_t xb = klo; xb < khi; xb += int64_t(NT) * 4) {
       uint32_t v[4];
       bool on[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const int64_t x = xb + tid + int64_t(u) * kThreads;
+        const int64_t x = xb + tid + int64_t(u) * NT;
         on[u] = x < khi && sm.rd[(x >> alpha) - i_lo];
         v[u] = on[u] ? __ldg(p.keys + x) : 0u;
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const int64_t x = xb + tid + int64_t(u) * kThreads;
+        const int64_t x = xb + tid + int64_t(u) * NT;
         const uint32_t bal = __ballot_sync(0xFFFFFFFFu, on[u] && map_key<DT>(v[u]) == tau);
         if (lane == 0 && bal) {
           const int seg = static_cast<int>((x - klo) >> 5);
@@ -986,7 +984,7 @@ __device__ uint32_t tie_tile_count(const TieParams& p, int64_t t, uint32_t tau, 
       return 0;
     }
     const uint32_t* kb = reinterpret_cast<const uint32_t*>(tbuf) + *s_shift;
-    for (int64_t xb = 0; xb < cn; xb += kThreads) {
+    for (int64_t xb = 0; xb < cn; xb += NT) {
       const int64_t e = xb + tid;
       const int64_t x = c0 + e;
       const bool on = e < cn && sm.rd[(x >> alpha) - i_lo];
@@ -1002,7 +1000,7 @@ __device__ uint32_t tie_tile_count(const TieParams& p, int64_t t, uint32_t tau, 
   }
   // exclusive prefixes over the segments (8 consecutive per thread)
   uint32_t tot = 0;
-  constexpr int kPer = kTieMaxSeg / kThreads;
+  constexpr int kPer = kTieMaxSeg / NT;
   uint32_t c[kPer];
   uint32_t sum = 0;
 #pragma unroll
@@ -1011,7 +1009,7 @@ __device__ uint32_t tie_tile_count(const TieParams& p, int64_t t, uint32_t tau, 
     c[e] = q < nseg ? sm.seg[q] : 0u;
     sum += c[e];
   }
-  uint32_t run = block_scan_excl<kThreads>(sum, &tot);
+  uint32_t run = block_scan_excl<NT>(sum, &tot);
 #pragma unroll
   for (int e = 0; e < kPer; ++e) {
     const int q = tid * kPer + e;
@@ -1024,7 +1022,7 @@ __device__ uint32_t tie_tile_count(const TieParams& p, int64_t t, uint32_t tau, 
 
 // Writes the ties of tile t whose ranks E + (prefix in the tile) are below
 // `need`, from the segment bitmasks and the delegates (block-wide).
-template <int DT, int B>
+template <int DT, int B, int NT>
 __device__ void tie_tile_emit(const TieParams& p, int64_t t, uint32_t tau, uint32_t need,
                               uint32_t g, uint32_t E, const TieTileSmem& sm, uint32_t& emitted) {
   const int tid = threadIdx.x;
@@ -1037,7 +1035,7 @@ __device__ void tie_tile_emit(const TieParams& p, int64_t t, uint32_t tau, uint3
   const int64_t khi = imin64(p.n, (i_lo + nsub) << alpha);
   const int nseg = static_cast<int>((khi - klo + 31) >> 5);
   // from the bitmasks: a warp per segment, coalesced writes
-  for (int q = warp; q < nseg; q += kThreads / 32) {
+  for (int q = warp; q < nseg; q += NT / 32) {
     const uint32_t bits = sm.bits[q];
     const uint32_t r0 = E + sm.seg[q];
     if (bits == 0 || r0 >= need) continue;
@@ -1053,7 +1051,7 @@ __device__ void tie_tile_emit(const TieParams& p, int64_t t, uint32_t tau, uint3
   // lists equal keys in index order (segment, then occurrence); the position
   // is the occurrence-th key equal to tau in the 32-key segment, found by
   // one coalesced read and a vote
-  for (int64_t ii = warp; ii < nsub; ii += kThreads / 32) {
+  for (int64_t ii = warp; ii < nsub; ii += NT / 32) {
     if (sm.rd[ii] || sm.dc[ii] == 0) continue;
     uint32_t r = E + sm.seg[static_cast<int>((ii << alpha) >> 5)];
     if (r >= need) continue;
@@ -1087,8 +1085,8 @@ __device__ void tie_tile_emit(const TieParams& p, int64_t t, uint32_t tau, uint3
 
 __device__ __forceinline__ void tie_copy_g(const TieParams& p, uint32_t g) {
   // G is part of the answer, in front of the ties
-  for (int64_t j = int64_t(blockIdx.x) * kThreads + threadIdx.x; j < g;
-       j += int64_t(gridDim.x) * kThreads)
+  for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < g;
+       j += int64_t(gridDim.x) * blockDim.x)
     p.w[j] = p.g[j];
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&p.ctl->w_count, g);
 }
@@ -1105,8 +1103,10 @@ __device__ __forceinline__ void tie_finish(const TieParams& p, uint32_t read_sub
 // Dense ties: the listed tiles walked in order (ticket), each read whole by
 // bulk copies; its prefix = lower-bound prefix + corrections of the earlier
 // listed tiles (decoupled look-back); the first tile reaching `need` cuts.
+constexpr int kWalkThreads = 512;
+
 template <int DT, int B>
-__global__ void __launch_bounds__(kThreads, 1) tie_walk_kernel(TieParams p) {
+__global__ void __launch_bounds__(kWalkThreads, 1) tie_walk_kernel(TieParams p) {
   Ctl* ctl = p.ctl;
   if (__ldcg(&ctl->mode) != kModeTies || __ldcg(&ctl->tie_dense) == 0) return;
   const uint32_t tau = __ldcg(&ctl->tau);
@@ -1145,8 +1145,9 @@ __global__ void __launch_bounds__(kThreads, 1) tie_walk_kernel(TieParams p) {
     if (!s_go) break;
     const int64_t j = s_j, t = s_t;
     bool timed_out;
-    const uint32_t tot = tie_tile_count<DT, B, true>(p, t, tau, sm, tbuf, &s_bar, phase, pol,
-                                                     &s_shift, read_subs, &timed_out);
+    const uint32_t tot = tie_tile_count<DT, B, true, kWalkThreads>(p, t, tau, sm, tbuf, &s_bar,
+                                                                   phase, pol, &s_shift, read_subs,
+                                                                   &timed_out);
     if (timed_out) break;
     if (warp == 0) {
       const uint32_t corr = tot - tlb_lb(p.tlb[t]);
@@ -1197,7 +1198,7 @@ __global__ void __launch_bounds__(kThreads, 1) tie_walk_kernel(TieParams p) {
     }
     __syncthreads();
     const uint32_t E = s_E;
-    if (E < need) tie_tile_emit<DT, B>(p, t, tau, need, g, E, sm, emitted);
+    if (E < need) tie_tile_emit<DT, B, kWalkThreads>(p, t, tau, need, g, E, sm, emitted);
     __syncthreads();
   }
   tie_finish(p, read_subs, emitted);
@@ -1566,6 +1567,8 @@ cudaError_t launch_ties(const Work& w, const void* keys, int sms, cudaStream_t s
   p.dkeys = w.dkeys;
   p.dsegs = w.dsegs;
   p.tsub = tie_tile_subs(w.alpha);
+  p.tsub_log = 0;
+  while ((int64_t(1) << p.tsub_log) < p.tsub) ++p.tsub_log;
   p.ntiles = tie_tiles(w.S, w.alpha);
   p.tstat = w.tstat;
   p.tlb = reinterpret_cast<uint32_t*>(w.tstat + p.ntiles);
@@ -1585,7 +1588,7 @@ cudaError_t launch_ties(const Work& w, const void* keys, int sms, cudaStream_t s
   tie_plan_kernel<<<1, 1024, 0, s>>>(p);                                               \
   cudaFuncSetAttribute(tie_walk_kernel<DTV, BV>,                                       \
                        cudaFuncAttributeMaxDynamicSharedMemorySize, kTieBufBytes);     \
-  tie_walk_kernel<DTV, BV><<<gc, kThreads, kTieBufBytes, s>>>(p);                      \
+  tie_walk_kernel<DTV, BV><<<gc, kWalkThreads, kTieBufBytes, s>>>(p);                  \
   tie_count_kernel<DTV, BV><<<gs, kThreads, 0, s>>>(p);                                \
   tie_scan_kernel<<<1, 1024, 0, s>>>(p);                                               \
   tie_place_kernel<DTV, BV><<<gs, kThreads, 0, s>>>(p);
