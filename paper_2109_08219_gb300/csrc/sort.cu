@@ -28,11 +28,6 @@ constexpr uint64_t kFlagAgg = uint64_t(1) << 32;
 constexpr uint64_t kFlagIncl = uint64_t(2) << 32;
 constexpr uint32_t kLookbackSpin = 1u << 22;
 
-__device__ __forceinline__ uint32_t lanemask_lt_s() {
-  uint32_t m;
-  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-  return m;
-}
 
 __device__ __forceinline__ void st_relaxed(uint64_t* p, uint64_t v) {
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
