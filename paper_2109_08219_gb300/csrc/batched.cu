@@ -227,6 +227,694 @@ __device__ __forceinline__ V warp_min(V v) {
   return v;
 }
 
+template <class V>
+struct SelResult {
+  V value;        // exact mode: the krem-th largest; else a threshold T
+  uint32_t need;  // exact mode: values equal to it among the top krem
+};
+
+// The krem-th largest of cnt values get(i) (MSD radix select, Sec. 4.1's
+// digits of 8 bits). When every value of the selected bucket is among the
+// top krem the search stops: in exact mode the answer is the bucket's
+// minimum (found by one more pass); otherwise the returned T (the bucket's
+// prefix, low bits 0) still has exactly krem values >= T when the values
+// are distinct. mm: one 64-bit shared word.
+template <class V, bool kExact, class Get>
+__device__ SelResult<V> block_select(Get get, uint32_t cnt, uint32_t krem, uint32_t* hist,
+                                     uint32_t* s_bc, unsigned long long* mm) {
+  constexpr int kBits = sizeof(V) * 8;
+  const int tid = threadIdx.x;
+  int hb = kBits;  // bits above hb are fixed in prefix
+  V prefix = 0;
+  while (hb > 0) {
+    const int width = hb < 8 ? hb : 8;
+    const int sh = hb - width;
+    for (int i = tid; i < 256; i += kBT) hist[i] = 0;
+    __syncthreads();
+    for (uint32_t i = tid; i < cnt; i += kBT) {
+      const V x = get(i);
+      if (hb >= kBits || (x >> hb) == (prefix >> hb))
+        atomicAdd(&hist[static_cast<uint32_t>(x >> sh) & ((1u << width) - 1u)], 1u);
+    }
+    __syncthreads();
+    if (tid < 32) bucket_search(hist, krem, s_bc);
+    __syncthreads();
+    prefix |= static_cast<V>(s_bc[0]) << sh;
+    krem = s_bc[1];
+    const uint32_t hd = s_bc[2];
+    __syncthreads();
+    hb = sh;
+    if (hd == krem && hb > 0) {
+      if constexpr (!kExact) {
+        return {prefix, 0u};
+      } else {
+        // the whole bucket is among the top: the answer is its minimum,
+        // needed as many times as it occurs
+        if (tid == 0) {
+          mm[0] = ~0ull;
+          s_bc[3] = 0;
+        }
+        __syncthreads();
+        V lo = static_cast<V>(~V(0));
+        for (uint32_t i = tid; i < cnt; i += kBT) {
+          const V x = get(i);
+          if ((x >> hb) == (prefix >> hb)) lo = x < lo ? x : lo;
+        }
+        lo = warp_min(lo);
+        if ((tid & 31) == 0) atomicMin(&mm[0], static_cast<unsigned long long>(lo));
+        __syncthreads();
+        const V v = static_cast<V>(mm[0]);
+        uint32_t c = 0;
+        for (uint32_t i = tid; i < cnt; i += kBT) c += get(i) == v ? 1u : 0u;
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+        if ((tid & 31) == 0) atomicAdd(&s_bc[3], c);
+        __syncthreads();
+        const uint32_t need = s_bc[3];
+        __syncthreads();
+        return {v, need};
+      }
+    }
+  }
+  return {prefix, krem};
+}
+
+// Bitonic sort (descending) of w[0..cnt) in shared memory, cnt <= kBMaxK;
+// pads w[cnt..P) with 0 (P = next power of two), which sorts last. The
+// pairs q of a warp in one sweep, [32m, 32m + 32), touch only elements
+// [64m, 64m + 64) while the stride is at most 32, so such consecutive
+// stages need only the warp in step.
+__device__ void block_sort_desc(uint64_t* w, int cnt) {
+  int P = 1;
+  while (P < cnt) P <<= 1;
+  for (int i = cnt + threadIdx.x; i < P; i += kBT) w[i] = 0ull;
+  __syncthreads();
+  const int half = P >> 1;
+  for (int size = 2; size <= P; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int q = threadIdx.x; q < half; q += kBT) {
+        const int i = 2 * q - (q & (stride - 1));
+        const int j = i + stride;
+        const bool desc = (i & size) == 0;
+        const uint64_t a = w[i], b = w[j];
+        if ((a < b) == desc) {
+          w[i] = b;
+          w[j] = a;
+        }
+      }
+      const int next = stride > 1 ? stride >> 1 : size;  // stride of the next stage
+      if (stride > 32 || next > 32) __syncthreads();
+      else __syncwarp();
+    }
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------ direct row --
+// Rows of at most kBDirectMax keys where delegates cannot reduce the work
+// (short rows, or beta * n / 32 < 2k): the row is copied into the ring and
+// the k-th largest key is found by an MSD radix select over it (Sec. 4.1's
+// 8-bit digits); then one ordered pass collects the keys above it and the
+// smallest-index keys equal to it, which go straight to the output.
+template <int DT>
+__device__ void direct_row(const BatchParams& p, const RowDesc& r, const Smem& sm, Ring& ring,
+                           uint32_t* hist, uint32_t* s_bc, uint32_t* s_cnt,
+                           unsigned long long* mm, long long& tmark) {
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
+  const int64_t n = r.n;
+  const uint32_t k = static_cast<uint32_t>(r.k);
+  const int nch = static_cast<int>((n + kBChunk - 1) / kBChunk);  // <= kBStages
+  const uint64_t seq0 = ring.seq;
+  if (tid == 0) {
+    for (int c = 0; c < nch; ++c) {
+      const uint64_t q = seq0 + c;
+      issue_row_chunk(p, r, c, sm.ring + (q % kBStages) * kBStageBytes, &ring.bar[q % kBStages],
+                      ring.pol_first);
+    }
+  }
+  const uint32_t* base[kBStages];
+  bool ok = true;
+#pragma unroll
+  for (int c = 0; c < kBStages; ++c) {
+    const uint64_t q = seq0 + c;
+    const int shift = row_shift(p, r);
+    base[c] = reinterpret_cast<const uint32_t*>(sm.ring + (q % kBStages) * kBStageBytes) + shift;
+    if (c < nch) ok = mbar_wait_bounded(&ring.bar[q % kBStages], static_cast<uint32_t>((q / kBStages) & 1)) && ok;
+  }
+  ring.seq = seq0 + static_cast<uint64_t>(nch);
+  if (__syncthreads_or(!ok)) {
+    if (tid == 0) atomicOr(p.err, kErrTimeout);
+    return;
+  }
+  static_assert(kBStages == 2, "a direct row spans at most two stage buffers");
+  const uint32_t* b0 = base[0];
+  const uint32_t* b1 = base[1];
+  auto key_at = [&](int64_t i) -> uint32_t {
+    return map_key<DT>((i < kBChunk ? b0 : b1)[i & (kBChunk - 1)]);
+  };
+  phase_mark(p, 6, tmark);
+
+  // k-th largest mapped key: four 8-bit digit passes over the row on chip
+  const SelResult<uint32_t> sel = block_select<uint32_t, true>(
+      [&](uint32_t i) { return key_at(i); }, static_cast<uint32_t>(n), k, hist, s_bc, mm);
+  const uint32_t kth = sel.value;
+  const uint32_t need = sel.need;  // keys equal to kth among the top k
+  phase_mark(p, 7, tmark);
+  const uint32_t gt = k - need; // keys above kth
+
+  // ordered pass: keys > kth to gbuf (any order), ties in index order to
+  // the output after the gt largest
+  constexpr int kU = 8;
+  uint32_t* wt = hist;  // per-warp tie counts
+  uint32_t tbase = 0;
+  const uint32_t tie_raw = unmap_key(DT, kth);
+  for (int64_t t0 = 0; t0 < n; t0 += int64_t(kBT) * kU) {
+    const int64_t wb = t0 + int64_t(warp) * 32 * kU;
+    uint32_t bal[kU];
+    uint32_t wcount = 0;
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int64_t i = wb + u * 32 + lane;
+      const uint32_t x = i < n ? key_at(i) : 0u;
+      const bool big = i < n && x > kth;
+      const uint32_t bb = __ballot_sync(0xFFFFFFFFu, big);
+      if (bb) {
+        uint32_t b0 = 0;
+        if (lane == __ffs(bb) - 1) b0 = atomicAdd(&s_cnt[0], __popc(bb));
+        b0 = __shfl_sync(0xFFFFFFFFu, b0, __ffs(bb) - 1);
+        if (big) {
+          const uint32_t slot = b0 + __popc(bb & lanemask_lt_b());
+          if (slot < gt) sm.gbuf[slot] = make_comp(x, static_cast<uint32_t>(i));
+          else atomicOr(p.err, kErrOverflowW);
+        }
+      }
+      bal[u] = __ballot_sync(0xFFFFFFFFu, i < n && x == kth);
+      wcount += __popc(bal[u]);
+    }
+    if (lane == 0) wt[warp] = wcount;
+    __syncthreads();
+    uint32_t pre = tbase, tot = 0;
+#pragma unroll
+    for (int q = 0; q < kBWarps; ++q) {
+      const uint32_t c = wt[q];
+      pre += q < warp ? c : 0u;
+      tot += c;
+    }
+    if (pre < tbase + need) {
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const uint32_t rank = pre + __popc(bal[u] & lanemask_lt_b());
+        if (((bal[u] >> lane) & 1u) && rank < need) {
+          row_out_keys(p, r)[gt + rank] = tie_raw;
+          row_out_idx(p, r)[gt + rank] = static_cast<int32_t>(wb + u * 32 + lane);
+        }
+        pre += __popc(bal[u]);
+      }
+    }
+    tbase += tot;
+    __syncthreads();
+  }
+  phase_mark(p, 8, tmark);
+  block_sort_desc(sm.gbuf, static_cast<int>(gt));
+  for (uint32_t j = tid; j < gt; j += kBT) {
+    const uint64_t c = sm.gbuf[j];
+    row_out_keys(p, r)[j] = unmap_key(DT, comp_key(c));
+    row_out_idx(p, r)[j] = static_cast<int32_t>(comp_idx(c));
+  }
+  __syncthreads();
+  phase_mark(p, 9, tmark);
+}
+
+// ------------------------------------------------------------ one row ----
+template <int DT, int B>
+__device__ void process_row(const BatchParams& p, const RowDesc& r, const Smem& sm, Ring& ring,
+                            uint32_t* hist, uint32_t* s_bc, uint32_t* s_cnt, uint64_t* s_lists,
+                            unsigned long long* mm) {
+  constexpr int P = Pow2<B>::v;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
+  const int64_t n = r.n;
+  const uint32_t k = static_cast<uint32_t>(r.k);
+  const int alpha = r.alpha;
+  uint64_t* scr = p.scratch + static_cast<int64_t>(blockIdx.x) * p.scap;
+  const uint32_t* rk = row_keys(p, r);
+
+  if (tid == 0) {
+    s_cnt[0] = 0;  // |G|
+    s_cnt[1] = 0;  // scan list length
+    s_cnt[2] = 0;  // winners
+    s_cnt[3] = 0;  // resolve requests
+  }
+  // the previous row wrote the ring with generic stores; the bulk copies of
+  // this row write it through the async proxy
+  fence_proxy_async_smem();
+  __syncthreads();
+
+  long long tmark = clock64();
+  int64_t S = 0;
+  uint32_t tau = 0;
+  if (alpha == 0) {
+    direct_row<DT>(p, r, sm, ring, hist, s_bc, s_cnt, mm, tmark);
+    return;
+  }
+  {
+    // ---------------------------------------------- 1. delegate pass ----
+    S = (n + (int64_t(1) << alpha) - 1) >> alpha;
+    const int64_t nch = (n + kBChunk - 1) / kBChunk;
+    const int cps_log = alpha > kBLogChunk ? alpha - kBLogChunk : 0;
+    const uint64_t seq0 = ring.seq;
+    // rows up to kBKeepL2 bytes stay in L2 for the filter's second reads
+    const uint64_t pol = n * 4 <= kBKeepL2 ? ring.pol_normal : ring.pol_first;
+    if (tid == 0) {
+      for (int64_t c = 0; c < kBStages && c < nch; ++c) {
+        const uint64_t q = seq0 + c;
+        issue_row_chunk(p, r, c, sm.ring + (q % kBStages) * kBStageBytes, &ring.bar[q % kBStages],
+                        pol);
+      }
+    }
+    uint64_t run[P];
+#pragma unroll
+    for (int i = 0; i < P; ++i) run[i] = 0;
+    for (int64_t c = 0; c < nch; ++c) {
+      const uint64_t q = seq0 + c;
+      const int stage = static_cast<int>(q % kBStages);
+      const bool ok = mbar_wait_bounded(&ring.bar[stage], static_cast<uint32_t>((q / kBStages) & 1));
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) {
+          atomicOr(p.err, kErrTimeout);
+          // let the copies still in flight land (bounded) before leaving
+          for (int64_t c2 = c; c2 < nch && c2 < c + kBStages; ++c2) {
+            const uint64_t q2 = seq0 + c2;
+            mbar_wait_bounded(&ring.bar[q2 % kBStages], static_cast<uint32_t>((q2 / kBStages) & 1));
+          }
+        }
+        __syncthreads();
+        return;
+      }
+      const uint32_t* cb = reinterpret_cast<const uint32_t*>(sm.ring + stage * kBStageBytes);
+      const int shift = row_shift(p, r);
+      const int64_t seg_start = c * kBChunk + int64_t(tid) * 32;  // row-relative
+      const int64_t valid = n - seg_start;
+      uint32_t m[B];
+#pragma unroll
+      for (int i = 0; i < B; ++i) m[i] = 0;
+      int cntv;
+      if (valid >= 32) {
+        // rotated reads: lane l starts at word l of its 32 (no bank conflicts)
+#pragma unroll
+        for (int j = 0; j < 32; ++j) insert1<DT, B>(m, cb[shift + tid * 32 + ((j + lane) & 31)]);
+        cntv = 32;
+      } else {
+        cntv = 0;
+        for (int j = 0; j < 32; ++j) {
+          if (j < valid) {
+            insert1<DT, B>(m, cb[shift + tid * 32 + j]);
+            ++cntv;
+          }
+        }
+      }
+      const int64_t sub = seg_start >> alpha;
+      const uint32_t seg = static_cast<uint32_t>((seg_start - (sub << alpha)) >> 5);
+      uint64_t a[P];
+#pragma unroll
+      for (int i = 0; i < P; ++i) a[i] = (i < B && i < cntv) ? make_dc(m[i < B ? i : 0], seg) : 0ull;
+      if (alpha <= kBLogChunk) {
+        const int g_log = alpha - 5;
+        const int wl = g_log < 5 ? g_log : 5;
+        for (int l = 0; l < wl; ++l) shfl_merge<P>(a, 1 << l);
+        if (g_log <= 5) {
+          if ((lane & ((1 << g_log) - 1)) == 0 && sub < S) {
+#pragma unroll
+            for (int j = 0; j < B; ++j) {
+              sm.dkeys[sub * B + j] = dc_key(a[j]);
+              sm.dsegs[sub * B + j] = static_cast<uint16_t>(a[j] == 0 ? kNoSeg : dc_seg(a[j]));
+            }
+          }
+        } else {
+          if (lane == 0) {
+#pragma unroll
+            for (int i = 0; i < P; ++i) s_lists[warp * P + i] = a[i];
+          }
+          __syncthreads();
+          const int wps_log = g_log - 5;
+          const int nsub_chunk = kBWarps >> wps_log;
+          if (warp < nsub_chunk) {
+            uint64_t b[P];
+            const int src = warp * (1 << wps_log) + (lane & ((1 << wps_log) - 1));
+#pragma unroll
+            for (int i = 0; i < P; ++i) b[i] = s_lists[src * P + i];
+            for (int l = 0; l < wps_log; ++l) shfl_merge<P>(b, 1 << l);
+            const int64_t sub2 = ((c * kBChunk) >> alpha) + warp;
+            if (lane == 0 && sub2 < S) {
+#pragma unroll
+              for (int j = 0; j < B; ++j) {
+                sm.dkeys[sub2 * B + j] = dc_key(b[j]);
+                sm.dsegs[sub2 * B + j] = static_cast<uint16_t>(b[j] == 0 ? kNoSeg : dc_seg(b[j]));
+              }
+            }
+          }
+        }
+      } else {
+        merge_desc<P>(run, a);
+        const int64_t cps = int64_t(1) << cps_log;
+        if (((c & (cps - 1)) == cps - 1) || (c == nch - 1)) {
+          for (int l = 0; l < 5; ++l) shfl_merge<P>(run, 1 << l);
+          if (lane == 0) {
+#pragma unroll
+            for (int i = 0; i < P; ++i) s_lists[warp * P + i] = run[i];
+          }
+          __syncthreads();
+          if (warp == 0) {
+            uint64_t b[P];
+#pragma unroll
+            for (int i = 0; i < P; ++i) b[i] = s_lists[(lane & (kBWarps - 1)) * P + i];
+            for (int l = 0; l < kBLogWarps; ++l) shfl_merge<P>(b, 1 << l);
+            const int64_t sub3 = c >> cps_log;
+            if (lane == 0) {
+#pragma unroll
+              for (int j = 0; j < B; ++j) {
+                sm.dkeys[sub3 * B + j] = dc_key(b[j]);
+                sm.dsegs[sub3 * B + j] = static_cast<uint16_t>(b[j] == 0 ? kNoSeg : dc_seg(b[j]));
+              }
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < P; ++i) run[i] = 0;
+        }
+      }
+      __syncthreads();  // stage consumed
+      if (tid == 0 && c + kBStages < nch) {
+        const uint64_t qn = q + kBStages;
+        issue_row_chunk(p, r, c + kBStages, sm.ring + (qn % kBStages) * kBStageBytes,
+                        &ring.bar[qn % kBStages], pol);
+      }
+    }
+    ring.seq = seq0 + static_cast<uint64_t>(nch);
+    phase_mark(p, 0, tmark);
+
+    // ------------------------------------------------- 2. threshold ----
+    const int dcnt = static_cast<int>(S * B);
+    if (dcnt >= static_cast<int>(k)) {
+      const uint32_t* dk = sm.dkeys;
+      tau = block_select<uint32_t, true>([dk](uint32_t i) { return dk[i]; },
+                                         static_cast<uint32_t>(dcnt), k, hist, s_bc, mm).value;
+    }
+    phase_mark(p, 1, tmark);
+
+    // ------------------------------------------------- 3. filter -------
+    // (a) classify each subrange: read again when its beta-th delegate
+    // exceeds tau (non-delegates may too), else its delegates > tau are
+    // candidates whose positions are resolved in (b).
+    uint16_t* scanl = reinterpret_cast<uint16_t*>(sm.ring + kScanOff);
+    uint64_t* reql = reinterpret_cast<uint64_t*>(sm.ring + kReqOff);
+    for (int64_t i0 = 0; i0 < S; i0 += kBT) {
+      const int64_t i = i0 + tid;
+      if (i < S) {
+        uint32_t dk[B];
+        uint16_t ds[B];
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+          dk[j] = sm.dkeys[i * B + j];
+          ds[j] = sm.dsegs[i * B + j];
+        }
+        const int64_t len = imin64(int64_t(1) << alpha, n - (i << alpha));
+        if (dk[0] > tau) {
+          if (dk[B - 1] > tau && len > B) {
+            scanl[atomicAdd(&s_cnt[1], 1u)] = static_cast<uint16_t>(i);
+          } else {
+#pragma unroll
+            for (int j = 0; j < B; ++j) {
+              if (dk[j] > tau) {
+                // the (occ+1)-th key equal to dk[j] in segment ds[j]
+                uint32_t occ = 0;
+#pragma unroll
+                for (int q = 0; q < j; ++q) occ += (dk[q] == dk[j] && ds[q] == ds[j]) ? 1u : 0u;
+                const uint64_t lo = static_cast<uint64_t>((i << alpha) + int64_t(ds[j]) * 32);
+                reql[atomicAdd(&s_cnt[3], 1u)] = (uint64_t(dk[j]) << 32) | (uint64_t(occ) << 24) | lo;
+              }
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+    // (b) resolve positions: a warp reads a 32-key segment per request
+    // (coalesced), kRU requests in flight per warp
+    {
+      constexpr int kRU = 8;
+      const uint32_t nreq = s_cnt[3];
+      for (uint32_t q0 = warp * kRU; q0 < nreq; q0 += (kBT / 32) * kRU) {
+        uint32_t x[kRU];
+        uint64_t rq[kRU];
+#pragma unroll
+        for (int u = 0; u < kRU; ++u) {
+          rq[u] = (q0 + u < nreq) ? reql[q0 + u] : 0ull;
+          const int64_t lo = static_cast<int64_t>(rq[u] & 0xFFFFFFu);
+          const int64_t hi = imin64(imin64(n, lo + 32), ((lo >> alpha) + 1) << alpha);
+          x[u] = (q0 + u < nreq && lo + lane < hi) ? rk[lo + lane] : 0u;
+          if (!(q0 + u < nreq && lo + lane < hi)) rq[u] |= (1ull << 31);  // lane not in segment
+        }
+#pragma unroll
+        for (int u = 0; u < kRU; ++u) {
+          if (q0 + u >= nreq) break;
+          const uint32_t key = static_cast<uint32_t>(rq[u] >> 32);
+          const bool m = !((rq[u] >> 31) & 1u) && map_key<DT>(x[u]) == key;
+          uint32_t bal = __ballot_sync(0xFFFFFFFFu, m);
+          const uint32_t occ = static_cast<uint32_t>(rq[u] >> 24) & 3u;
+          for (uint32_t t = 0; t < occ; ++t) bal &= bal - 1;
+          if (lane == 0) {
+            const int64_t lo = static_cast<int64_t>(rq[u] & 0xFFFFFFu);
+            int64_t pos = -1;
+            if (bal) pos = lo + (__ffs(bal) - 1);
+            else atomicOr(p.err, kErrTieRank);
+            g_put(sm, scr, p.scap, atomicAdd(&s_cnt[0], 1u),
+                  make_comp(key, static_cast<uint32_t>(pos)), p.err);
+          }
+        }
+      }
+    }
+    // (c) read the listed subranges again: kFU keys per thread in flight
+    {
+      constexpr int kFU = 16;
+      const uint32_t nq = s_cnt[1];
+      const int64_t vtotal = int64_t(nq) << alpha;
+      const int64_t vmask = (int64_t(1) << alpha) - 1;
+      const uint32_t nn = static_cast<uint32_t>(n);
+      for (int64_t v0 = 0; v0 < vtotal; v0 += int64_t(kBT) * kFU) {
+        uint32_t x[kFU];
+        uint32_t gi[kFU];
+#pragma unroll
+        for (int u = 0; u < kFU; ++u) {
+          const int64_t v = v0 + int64_t(u) * kBT + tid;
+          gi[u] = v < vtotal ? static_cast<uint32_t>((int64_t(scanl[v >> alpha]) << alpha) + (v & vmask))
+                             : nn;
+          x[u] = gi[u] < nn ? rk[gi[u]] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < kFU; ++u) {
+          const uint32_t mk = map_key<DT>(x[u]);
+          const bool has = gi[u] < nn && mk > tau;
+          g_append(sm, scr, p.scap, &s_cnt[0], has, make_comp(mk, gi[u]), p.err);
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  // ------------------------------------------------- 4. second top-k ----
+  uint64_t* w = reinterpret_cast<uint64_t*>(sm.ring);  // winners (the ring is free)
+  const uint32_t gcnt = s_cnt[0];
+  phase_mark(p, 2, tmark);
+  if (gcnt >= k) {
+    if (gcnt <= 2 * k && gcnt <= static_cast<uint32_t>(kBMaxK)) {
+      // few candidates beyond k: sorting them all is cheaper than a select
+      for (uint32_t i = tid; i < gcnt; i += kBT) w[i] = g_get(sm, scr, i);
+      block_sort_desc(w, static_cast<int>(gcnt));
+      phase_mark(p, 3, tmark);
+    } else {
+      const uint64_t T = block_select<uint64_t, false>(
+          [&sm, scr](uint32_t i) { return g_get(sm, scr, i); }, gcnt, k, hist, s_bc, mm).value;
+      for (uint32_t i0 = 0; i0 < gcnt; i0 += kBT) {
+        const uint32_t i = i0 + tid;
+        uint64_t v = 0;
+        bool win = false;
+        if (i < gcnt) {
+          v = g_get(sm, scr, i);
+          win = v >= T;
+        }
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, win);
+        if (!bal) continue;
+        uint32_t base = 0;
+        if (lane == __ffs(bal) - 1) base = atomicAdd(&s_cnt[2], __popc(bal));
+        base = __shfl_sync(0xFFFFFFFFu, base, __ffs(bal) - 1);
+        if (win) {
+          const uint32_t slot = base + __popc(bal & lanemask_lt_b());
+          if (slot < k) w[slot] = v;
+          else atomicOr(p.err, kErrOverflowW);
+        }
+      }
+      phase_mark(p, 3, tmark);
+      block_sort_desc(w, static_cast<int>(k));
+      phase_mark(p, 5, tmark);
+    }
+  } else {
+    // the k-th key is tau: G (all > tau, fewer than k) sorted, then the
+    // smallest-index ties at tau in index order, which keeps the whole
+    // output sorted
+    for (uint32_t i = tid; i < gcnt; i += kBT) w[i] = g_get(sm, scr, i);
+    block_sort_desc(w, static_cast<int>(gcnt));
+    phase_mark(p, 3, tmark);
+    const uint32_t need = k - gcnt;
+    uint32_t base = 0;  // ties placed so far (uniform)
+    for (int64_t i0 = 0; i0 < S && base < need; i0 += kBT) {
+      const int64_t i = i0 + tid;
+      uint32_t cnt = 0;
+      bool scan = false;
+      if (i < S) {
+        const int64_t len = imin64(int64_t(1) << alpha, n - (i << alpha));
+        const uint32_t m0 = sm.dkeys[i * B], mb = sm.dkeys[i * B + B - 1];
+        if (m0 >= tau) {
+          if (mb >= tau && len > B) {
+            scan = true;  // non-delegates may equal tau
+          } else {
+#pragma unroll
+            for (int j = 0; j < B; ++j)
+              cnt += (sm.dkeys[i * B + j] == tau && sm.dsegs[i * B + j] != kNoSeg) ? 1u : 0u;
+          }
+        }
+      }
+      // exact counts of the subranges that must be read: a warp each
+      __syncthreads();
+      if (tid == 0) s_cnt[3] = 0;
+      __syncthreads();
+      uint16_t* lst = reinterpret_cast<uint16_t*>(sm.ring + kTieOff);
+      if (scan) lst[atomicAdd(&s_cnt[3], 1u)] = static_cast<uint16_t>(tid);
+      __syncthreads();
+      uint32_t* cnts = reinterpret_cast<uint32_t*>(sm.ring + kTieOff + size_t(kBT) * 2);
+      cnts[tid] = cnt;
+      __syncthreads();
+      const uint32_t nscan = s_cnt[3];
+      for (uint32_t q = warp; q < nscan; q += kBT / 32) {
+        const int64_t ii = i0 + lst[q];
+        const int64_t lo = ii << alpha;
+        const int64_t len = imin64(int64_t(1) << alpha, n - lo);
+        uint32_t c = 0;
+        for (int64_t t = lane; t < len; t += 32) c += (map_key<DT>(rk[lo + t]) == tau);
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+        if (lane == 0) cnts[lst[q]] = c;
+      }
+      __syncthreads();
+      uint32_t tot;
+      const uint32_t pre = base + block_scan_excl<kBT>(cnts[tid], &tot);
+      // emit: delegate-exact subranges by their thread, read ones by a warp
+      if (i < S && !scan && cnts[tid] > 0 && pre < need) {
+        uint32_t rr = pre;
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+          if (sm.dkeys[i * B + j] == tau && sm.dsegs[i * B + j] != kNoSeg && rr < need) {
+            int occ = 0;
+            for (int q = 0; q < j; ++q)
+              if (sm.dkeys[i * B + q] == tau && sm.dsegs[i * B + q] == sm.dsegs[i * B + j]) ++occ;
+            const int64_t lo = (i << alpha) + int64_t(sm.dsegs[i * B + j]) * 32;
+            const int64_t hi = imin64(imin64(n, lo + 32), (i + 1) << alpha);
+            int64_t pos = -1;
+            int cq = 0;
+            for (int64_t t = lo; t < hi; ++t) {
+              if (map_key<DT>(rk[t]) == tau) {
+                if (cq == occ) {
+                  pos = t;
+                  break;
+                }
+                ++cq;
+              }
+            }
+            if (pos < 0) atomicOr(p.err, kErrTieRank);
+            w[gcnt + rr] = make_comp(tau, static_cast<uint32_t>(pos));
+            ++rr;
+          }
+        }
+      }
+      uint32_t* pres = cnts + kBT;
+      pres[tid] = pre;
+      __syncthreads();
+      for (uint32_t q = warp; q < nscan; q += kBT / 32) {
+        const int64_t ii = i0 + lst[q];
+        uint32_t rr = pres[lst[q]];
+        const int64_t lo = ii << alpha;
+        const int64_t len = imin64(int64_t(1) << alpha, n - lo);
+        for (int64_t off = 0; off < len && rr < need; off += 32) {
+          const int64_t t = off + lane;
+          const bool is_t = t < len && map_key<DT>(rk[lo + t]) == tau;
+          const uint32_t bal = __ballot_sync(0xFFFFFFFFu, is_t);
+          const uint32_t rank = rr + __popc(bal & lanemask_lt_b());
+          if (is_t && rank < need) w[gcnt + rank] = make_comp(tau, static_cast<uint32_t>(lo + t));
+          rr += __popc(bal);
+        }
+      }
+      base += tot;
+      __syncthreads();
+    }
+    __syncthreads();
+    phase_mark(p, 4, tmark);
+  }
+
+  // ------------------------------------------------- 5. write ------------
+  for (uint32_t j = tid; j < k; j += kBT) {
+    const uint64_t c = w[j];
+    row_out_keys(p, r)[j] = unmap_key(DT, comp_key(c));
+    row_out_idx(p, r)[j] = static_cast<int32_t>(comp_idx(c));
+  }
+  __syncthreads();
+  phase_mark(p, 5, tmark);
+}
+
+template <int DT>
+__global__ void __launch_bounds__(kBT, 1) batched_kernel(BatchParams p) {
+  extern __shared__ __align__(128) unsigned char bsm[];
+  __shared__ __align__(8) uint64_t bars[kBStages];
+  __shared__ uint32_t hist[256];
+  __shared__ unsigned long long mm[2];
+  __shared__ uint32_t s_bc[4];
+  __shared__ uint32_t s_cnt[4];
+  __shared__ uint32_t s_row;
+  __shared__ uint64_t s_lists[kBWarps * 4];
+  Smem sm;
+  sm.ring = bsm;
+  sm.dkeys = reinterpret_cast<uint32_t*>(bsm + kRingBytes);
+  sm.dsegs = reinterpret_cast<uint16_t*>(bsm + kRingBytes + size_t(kBDMax) * 4);
+  sm.gbuf = reinterpret_cast<uint64_t*>(bsm + kRingBytes + size_t(kBDMax) * 6);
+  Ring ring;
+  ring.bar = bars;
+  ring.seq = 0;
+  ring.pol_first = l2_evict_first_policy();
+  ring.pol_normal = l2_evict_normal_policy();
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kBStages; ++s) mbar_init(&bars[s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  for (;;) {
+    if (threadIdx.x == 0) s_row = atomicAdd(p.row_ctr, 1u);
+    __syncthreads();
+    const uint32_t ri = s_row;
+    __syncthreads();
+    if (ri >= static_cast<uint32_t>(p.nrows)) break;
+    const RowDesc r = p.rows[ri];
+    switch (r.beta) {
+      case 1: process_row<DT, 1>(p, r, sm, ring, hist, s_bc, s_cnt, s_lists, mm); break;
+      case 3: process_row<DT, 3>(p, r, sm, ring, hist, s_bc, s_cnt, s_lists, mm); break;
+      case 4: process_row<DT, 4>(p, r, sm, ring, hist, s_bc, s_cnt, s_lists, mm); break;
+      default: process_row<DT, 2>(p, r, sm, ring, hist, s_bc, s_cnt, s_lists, mm); break;
+    }
+    // a bounded wait gave up: copies may still be in flight, stop this CTA
+    if (__syncthreads_or(threadIdx.x == 0 && (__ldcg(p.err) & kErrTimeout))) break;
+  }
+}
+
 // Fills every key with hashed bits (tuning inputs only).
 __global__ void fill_hash_kernel(uint32_t* a, int64_t n, uint64_t seed) {
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
