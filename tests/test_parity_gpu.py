@@ -298,3 +298,24 @@ def test_ablations_stay_exact(flags):
                     assert st["tau"] <= base["tau"] and (st["tau"] & 0xFF) == 0 or st["tau"] == 0
                 if no_filter and not skip_last:
                     assert st["greater"] >= base["greater"]  # whole subranges kept
+
+
+def test_tie_paths_dense_and_sparse():
+    """Ties at tau over many tiles: sparse (ND-like, ties spread thinly; one
+    tie needed among distinct keys) and dense (few values, all equal), with
+    the cut falling inside the walk; checked against the oracle."""
+    n = 1 << 22
+    dev = torch.device("cuda")
+    cases = [("nd", inputs.nd_u32(n, 5, device=dev), (1000, 65536, 500000)),
+             ("distinct16", inputs.distinct16_u32(n, 6, device=dev), (1024, 300000, 1 << 20)),
+             ("all_equal", inputs.all_equal_u32(n, device=dev), (7, 4096, 1 << 20)),
+             ("uniform", inputs.uniform_u32(n, 7, device=dev), (1, 1024, 100000))]
+    for name, x, ks in cases:
+        bits = host_bits(x)
+        for k in ks:
+            for alpha in (0, 5, 9, 14):
+                ok, oi, _, st = drtopk.drtopk_topk_ex(x, k, alpha=alpha, dtype="u32")
+                rk, ri = oracle.topk(bits, oracle.U32, k)
+                assert st["error"] == 0, (name, k, alpha, st)
+                assert np.array_equal(host_bits(ok), rk) and np.array_equal(oi.cpu().numpy(), ri), \
+                    (name, k, alpha, st)
