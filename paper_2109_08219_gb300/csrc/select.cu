@@ -106,6 +106,26 @@ __device__ __forceinline__ int occ_rank(const uint32_t* dk, const uint16_t* ds, 
   return r;
 }
 
+// The beta delegate keys of subrange i (contiguous in the workspace, which
+// is 256-byte aligned): one vector load for beta 2 and 4.
+template <int B>
+__device__ __forceinline__ void load_dkeys(const uint32_t* dkeys, int64_t i, uint32_t (&d)[B]) {
+  if constexpr (B == 2) {
+    const uint2 v = __ldg(reinterpret_cast<const uint2*>(dkeys) + i);
+    d[0] = v.x;
+    d[1] = v.y;
+  } else if constexpr (B == 4) {
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(dkeys) + i);
+    d[0] = v.x;
+    d[1] = v.y;
+    d[2] = v.z;
+    d[3] = v.w;
+  } else {
+#pragma unroll
+    for (int j = 0; j < B; ++j) d[j] = __ldg(dkeys + i * B + j);
+  }
+}
+
 int grid_for(int64_t work, int per_block, int sms, int per_sm) {
   int64_t g = (work + per_block - 1) / per_block;
   const int64_t cap = static_cast<int64_t>(sms) * per_sm;
@@ -295,15 +315,29 @@ __global__ void __launch_bounds__(kThreads) filter_classify_kernel(FilterParams 
   const int alpha = p.alpha;
   uint32_t nscan = 0;
   const int64_t per_step = int64_t(kThreads) * kClsSub;
-  for (int64_t base = int64_t(blockIdx.x) * per_step; base < p.S;
-       base += int64_t(gridDim.x) * per_step) {
-    uint32_t dk[kClsSub][B];
+  // the next step's delegates are loaded before this step's block-wide
+  // staging (double-buffered in registers)
+  uint32_t dk[kClsSub][B], nk[kClsSub][B];
+  auto load_step = [&](int64_t b) {
 #pragma unroll
     for (int u = 0; u < kClsSub; ++u) {
-      const int64_t i = base + int64_t(u) * kThreads + threadIdx.x;
+      const int64_t i = b + int64_t(u) * kThreads + threadIdx.x;
+      if (i < p.S) {
+        load_dkeys<B>(p.dkeys, i, nk[u]);
+      } else {
 #pragma unroll
-      for (int j = 0; j < B; ++j) dk[u][j] = (i < p.S) ? p.dkeys[i * B + j] : 0u;
+        for (int j = 0; j < B; ++j) nk[u][j] = 0u;
+      }
     }
+  };
+  load_step(int64_t(blockIdx.x) * per_step);
+  for (int64_t base = int64_t(blockIdx.x) * per_step; base < p.S;
+       base += int64_t(gridDim.x) * per_step) {
+#pragma unroll
+    for (int u = 0; u < kClsSub; ++u)
+#pragma unroll
+      for (int j = 0; j < B; ++j) dk[u][j] = nk[u][j];
+    if (base + int64_t(gridDim.x) * per_step < p.S) load_step(base + int64_t(gridDim.x) * per_step);
     uint32_t scanm = 0, nreq = 0;
     uint32_t req[kClsSub * B];
 #pragma unroll
@@ -560,14 +594,20 @@ __global__ void __launch_bounds__(kThreads) gstage_kernel(GSelParams p, int s) {
   const int nsh = 48 - 8 * level;  // next digit shift
   RunHist rh;
   const int64_t stepn = int64_t(nact) * kThreads * kGIpt;
+  // the next step's composites are loaded before this step's block scan and
+  // staging (double-buffered in registers)
+  uint64_t c[kGIpt], nc[kGIpt];
+  auto load_step = [&](int64_t b) {
+#pragma unroll
+    for (int u = 0; u < kGIpt; ++u)
+      nc[u] = __ldcg(src + imin64(b + threadIdx.x + int64_t(u) * kThreads, count - 1));
+  };
+  load_step(int64_t(blockIdx.x) * kThreads * kGIpt);
   for (int64_t base = int64_t(blockIdx.x) * kThreads * kGIpt; base < count; base += stepn) {
-    uint64_t c[kGIpt];
     uint32_t win = 0, sur = 0;
 #pragma unroll
-    for (int u = 0; u < kGIpt; ++u) {
-      const int64_t i = base + threadIdx.x + int64_t(u) * kThreads;
-      c[u] = __ldcg(src + imin64(i, count - 1));
-    }
+    for (int u = 0; u < kGIpt; ++u) c[u] = nc[u];
+    if (base + stepn < count) load_step(base + stepn);
 #pragma unroll
     for (int u = 0; u < kGIpt; ++u) {
       const int64_t i = base + threadIdx.x + int64_t(u) * kThreads;
@@ -713,18 +753,32 @@ __global__ void __launch_bounds__(kThreads) tie_lb_kernel(TieParams p) {
   __shared__ uint32_t s_lb[kThreads * kU + 1];
   for (int q = threadIdx.x; q <= kThreads * kU; q += kThreads) s_lb[q] = 0;
   __syncthreads();
-  for (int64_t i0 = int64_t(blockIdx.x) * kThreads * kU; i0 < p.S;
-       i0 += int64_t(gridDim.x) * kThreads * kU) {
+  // the next step's delegates are loaded before this step's reductions
+  // (double-buffered in registers)
+  uint32_t dk[kU][B], nk[kU][B];
+  const int64_t stride = int64_t(gridDim.x) * kThreads * kU;
+  auto load_step = [&](int64_t b) {
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int64_t i = b + int64_t(u) * kThreads + threadIdx.x;
+      if (i < p.S) {
+        load_dkeys<B>(p.dkeys, i, nk[u]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < B; ++q) nk[u][q] = 0u;
+      }
+    }
+  };
+  load_step(int64_t(blockIdx.x) * kThreads * kU);
+  for (int64_t i0 = int64_t(blockIdx.x) * kThreads * kU; i0 < p.S; i0 += stride) {
     const int64_t t0 = i0 >> p.tsub_log;
     const int nt_blk = static_cast<int>(
         ((imin64(p.S, i0 + int64_t(kThreads) * kU) - 1) >> p.tsub_log) - t0 + 1);
-    uint32_t dk[kU][B];
 #pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      const int64_t i = i0 + int64_t(u) * kThreads + threadIdx.x;
+    for (int u = 0; u < kU; ++u)
 #pragma unroll
-      for (int q = 0; q < B; ++q) dk[u][q] = i < p.S ? p.dkeys[i * B + q] : 0u;
-    }
+      for (int q = 0; q < B; ++q) dk[u][q] = nk[u][q];
+    if (i0 + stride < p.S) load_step(i0 + stride);
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       const int64_t i = i0 + int64_t(u) * kThreads + threadIdx.x;
