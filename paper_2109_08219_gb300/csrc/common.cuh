@@ -344,6 +344,44 @@ __device__ __forceinline__ void stage_flush(T* buf, uint32_t* s_fill, uint32_t* 
   __syncthreads();
 }
 
+// Per-warp variant: a warp gathers items in its own shared buffer of CAP
+// entries (ranked by ballots, no block barrier) and copies them out with one
+// atomicAdd per flush. All 32 lanes call push/flush with the same
+// arguments; `fill` stays warp-uniform.
+template <typename T, int CAP>
+struct WarpStage {
+  T* buf;
+  uint32_t fill;
+
+  __device__ __forceinline__ void flush(uint32_t* gctr, T* gdst, uint64_t gcap, uint32_t* err,
+                                        uint32_t ebit) {
+    __syncwarp();
+    const uint32_t lane = threadIdx.x & 31u;
+    uint32_t base = 0;
+    if (lane == 0 && fill) base = atomicAdd(gctr, fill);
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    for (uint32_t j = lane; j < fill; j += 32) {
+      if (uint64_t(base) + j < gcap) gdst[base + j] = buf[j];
+      else atomicOr(err, ebit);
+    }
+    __syncwarp();
+    fill = 0;
+  }
+
+  // Stages `item` of every lane with `has` (flushing first when the buffer
+  // cannot take them all).
+  __device__ __forceinline__ void push(bool has, T item, uint32_t* gctr, T* gdst, uint64_t gcap,
+                                       uint32_t* err, uint32_t ebit) {
+    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, has);
+    if (bal == 0) return;
+    if (fill + __popc(bal) > CAP) flush(gctr, gdst, gcap, err, ebit);
+    uint32_t lt;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+    if (has) buf[fill + __popc(bal & lt)] = item;
+    fill += __popc(bal);
+  }
+};
+
 // Reserves cnt staged slots for the calling thread (flushing first when the
 // buffer cannot take this round); returns the first slot in buf. The caller
 // writes buf[slot .. slot + cnt) before the next stage call.

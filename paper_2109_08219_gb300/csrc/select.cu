@@ -171,42 +171,35 @@ __global__ void __launch_bounds__(kThreads) thr_compact_kernel(const uint32_t* d
                                                                int64_t count, uint32_t* ds,
                                                                Ctl* ctl, int allow_done) {
   __shared__ uint32_t sh[256];
+  constexpr int kWCap = kThrStageCap / (kThreads / 32);
   __shared__ uint32_t sbuf[kThrStageCap];
-  __shared__ uint32_t s_fill;
   zero_hist(sh);
-  if (threadIdx.x == 0) s_fill = 0;
   __syncthreads();
   SelState<4>* st = &ctl->dsel;
   const uint32_t d0 = static_cast<uint32_t>(__ldcg(&st->prefix)) >> 24;
   const bool inplace = uint64_t(__ldcg(&st->bucket)) * 8 > static_cast<uint64_t>(count);
   if (inplace && blockIdx.x == 0 && threadIdx.x == 0) ctl->ds_inplace = 1;
   RunHist rh;
+  // kept keys are staged per warp (no block barrier in the loop)
+  WarpStage<uint32_t, kWCap> stg{sbuf + (threadIdx.x >> 5) * kWCap, 0u};
   uint32_t lo = 0xFFFFFFFFu, hi = 0;  // range of the bucket's keys
   const int64_t step = int64_t(gridDim.x) * kThreads * 16;
   for (int64_t base = int64_t(blockIdx.x) * kThreads * 16; base < count; base += step) {
     uint32_t v[16];
     load16<kThreads>(dkeys, count, base, v);
-    uint32_t hit = 0;
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
       const int64_t i = base + (int64_t(e >> 2) * kThreads + threadIdx.x) * 4 + (e & 3);
-      if (i < count && (v[e] >> 24) == d0) {
-        hit |= 1u << e;
+      const bool hit = i < count && (v[e] >> 24) == d0;
+      if (hit) {
         rh.add(sh, (v[e] >> 16) & 255u);
         lo = min(lo, v[e]);
         hi = max(hi, v[e]);
       }
-    }
-    if (!inplace) {
-      uint32_t slot = stage_reserve<uint32_t, kThreads, kThrStageCap>(
-          sbuf, &s_fill, __popc(hit), &ctl->ds_count, ds, ~uint64_t(0), &ctl->error, 0u);
-#pragma unroll
-      for (int e = 0; e < 16; ++e)
-        if (hit & (1u << e)) sbuf[slot++] = v[e];
+      if (!inplace) stg.push(hit, v[e], &ctl->ds_count, ds, ~uint64_t(0), &ctl->error, 0u);
     }
   }
-  if (!inplace) stage_flush<uint32_t, kThreads>(sbuf, &s_fill, &ctl->ds_count, ds, ~uint64_t(0),
-                                                &ctl->error, 0u);
+  if (!inplace) stg.flush(&ctl->ds_count, ds, ~uint64_t(0), &ctl->error, 0u);
   rh.flush(sh);
   lo = __reduce_min_sync(0xFFFFFFFFu, lo);
   hi = __reduce_max_sync(0xFFFFFFFFu, hi);
@@ -296,27 +289,28 @@ struct FilterParams {
 // Each thread classifies 4 subranges per step: skip (m^0 <= tau), queue
 // for a scan (m^{beta-1} > tau: Rule 3 says every element may qualify) or
 // emit its delegates > tau (Rule 3: they are all of its elements > tau).
-// Queue entries and emitted candidates are staged in shared memory.
+// Queue entries and emitted delegate slots are staged per warp in shared
+// memory.
 constexpr int kClsSub = 4;
 constexpr int kClsGCap = kThreads * kClsSub * 4;
 constexpr int kClsQCap = kThreads * kClsSub * 2;
 
 template <int DT, int B>
 __global__ void __launch_bounds__(kThreads) filter_classify_kernel(FilterParams p) {
+  constexpr int kWR = kClsGCap / (kThreads / 32);
+  constexpr int kWQ = kClsQCap / (kThreads / 32);
   __shared__ uint32_t rbuf[kClsGCap];
   __shared__ uint32_t qbuf[kClsQCap];
-  __shared__ uint32_t r_fill, q_fill;
-  if (threadIdx.x == 0) {
-    r_fill = 0;
-    q_fill = 0;
-  }
-  __syncthreads();
+  // queue entries and requests are staged per warp (no block barrier)
+  const int warp = threadIdx.x >> 5;
+  WarpStage<uint32_t, kWQ> sq{qbuf + warp * kWQ, 0u};
+  WarpStage<uint32_t, kWR> sr{rbuf + warp * kWR, 0u};
   const uint32_t tau = __ldcg(&p.ctl->tau);
   const int alpha = p.alpha;
   uint32_t nscan = 0;
   const int64_t per_step = int64_t(kThreads) * kClsSub;
-  // the next step's delegates are loaded before this step's block-wide
-  // staging (double-buffered in registers)
+  // the next step's delegates are loaded before this step is classified
+  // (double-buffered in registers)
   uint32_t dk[kClsSub][B], nk[kClsSub][B];
   auto load_step = [&](int64_t b) {
 #pragma unroll
@@ -338,42 +332,40 @@ __global__ void __launch_bounds__(kThreads) filter_classify_kernel(FilterParams 
 #pragma unroll
       for (int j = 0; j < B; ++j) dk[u][j] = nk[u][j];
     if (base + int64_t(gridDim.x) * per_step < p.S) load_step(base + int64_t(gridDim.x) * per_step);
-    uint32_t scanm = 0, nreq = 0;
-    uint32_t req[kClsSub * B];
 #pragma unroll
     for (int u = 0; u < kClsSub; ++u) {
       const int64_t i = base + int64_t(u) * kThreads + threadIdx.x;
+      bool scan = false;
+      uint32_t emit = 0;  // delegate slots to place
       if (p.no_filter) {
         // Rule 1 alone: a subrange whose maximum delegate reaches tau is kept whole
-        if (i < p.S && dk[u][0] >= tau) scanm |= 1u << u;
+        scan = i < p.S && dk[u][0] >= tau;
       } else if (i < p.S && dk[u][0] > tau) {
         if (dk[u][B - 1] > tau && sub_len(i, alpha, p.n) > B) {
-          scanm |= 1u << u;
+          scan = true;
         } else {
           // its keys > tau are exactly its delegates > tau (Rule 3); their
           // positions are resolved by filter_resolve_kernel
 #pragma unroll
-          for (int j = 0; j < B; ++j)
-            if (dk[u][j] > tau) req[nreq++] = static_cast<uint32_t>(i << 2) | static_cast<uint32_t>(j);
+          for (int j = 0; j < B; ++j) emit |= (dk[u][j] > tau) ? (1u << j) : 0u;
         }
       }
-    }
-    uint32_t qs = stage_reserve<uint32_t, kThreads, kClsQCap>(
-        qbuf, &q_fill, __popc(scanm), &p.ctl->scanq_count, p.scanq, ~uint64_t(0), &p.ctl->error, 0u);
+      sq.push(scan, static_cast<uint32_t>(i), &p.ctl->scanq_count, p.scanq, ~uint64_t(0),
+              &p.ctl->error, 0u);
+      nscan += scan ? 1u : 0u;
+      if (__any_sync(0xFFFFFFFFu, emit != 0)) {
 #pragma unroll
-    for (int u = 0; u < kClsSub; ++u)
-      if (scanm & (1u << u)) qbuf[qs++] = static_cast<uint32_t>(base + int64_t(u) * kThreads + threadIdx.x);
-    nscan += __popc(scanm);
-    uint32_t rs = stage_reserve<uint32_t, kThreads, kClsGCap>(
-        rbuf, &r_fill, nreq, &p.ctl->rq_count, p.rq, static_cast<uint64_t>(p.rq_cap), &p.ctl->error,
-        kErrOverflowG);
-    for (uint32_t e = 0; e < nreq; ++e) rbuf[rs + e] = req[e];
+        for (int j = 0; j < B; ++j)
+          sr.push((emit >> j) & 1u, static_cast<uint32_t>(i << 2) | static_cast<uint32_t>(j),
+                  &p.ctl->rq_count, p.rq, static_cast<uint64_t>(p.rq_cap), &p.ctl->error,
+                  kErrOverflowG);
+      }
+    }
   }
-  stage_flush<uint32_t, kThreads>(qbuf, &q_fill, &p.ctl->scanq_count, p.scanq, ~uint64_t(0),
-                                  &p.ctl->error, 0u);
-  stage_flush<uint32_t, kThreads>(rbuf, &r_fill, &p.ctl->rq_count, p.rq,
-                                  static_cast<uint64_t>(p.rq_cap), &p.ctl->error, kErrOverflowG);
-  if (nscan) atomicAdd(&p.ctl->scanned, nscan);
+  sq.flush(&p.ctl->scanq_count, p.scanq, ~uint64_t(0), &p.ctl->error, 0u);
+  sr.flush(&p.ctl->rq_count, p.rq, static_cast<uint64_t>(p.rq_cap), &p.ctl->error, kErrOverflowG);
+  nscan = __reduce_add_sync(0xFFFFFFFFu, nscan);
+  if ((threadIdx.x & 31) == 0 && nscan) atomicAdd(&p.ctl->scanned, nscan);
 }
 
 // Positions of the queued delegates: the occurrence-th key equal to the
@@ -737,78 +729,64 @@ __device__ __forceinline__ uint32_t tie_lb_of(const TieParams& p, int64_t i, uin
   return c;
 }
 
-// One thread per subrange, 4 subranges in flight per thread (grid-stride,
-// block-uniform trip count); the lanes of one tile (aligned groups of
-// min(tsub, 32)) are summed by shuffles and added to the tile's word (zeroed
-// before the launch).
+// A warp owns whole tiles: chunks of max(tsub, 32) consecutive subranges
+// (one tile, or 32 / tsub tiles of tsub lanes each), 8 subranges in flight
+// per lane. Each subrange adds (ties it surely holds) | (inexact << 16) to
+// its lane's sum; the sums of a tile are reduced in the warp and its word is
+// stored whole (no atomics, no block barrier).
 template <int B>
 __global__ void __launch_bounds__(kThreads) tie_lb_kernel(TieParams p) {
   Ctl* ctl = p.ctl;
   if (__ldcg(&ctl->mode) != kModeTies) return;
   const uint32_t tau = __ldcg(&ctl->tau);
-  const int grp = p.tsub < 32 ? static_cast<int>(p.tsub) : 32;
   const uint32_t lane = lane_id();
-  constexpr int kU = 4;
-  // the tiles one step of the block touches, summed in shared memory first
-  __shared__ uint32_t s_lb[kThreads * kU + 1];
-  for (int q = threadIdx.x; q <= kThreads * kU; q += kThreads) s_lb[q] = 0;
-  __syncthreads();
-  // the next step's delegates are loaded before this step's reductions
-  // (double-buffered in registers)
-  uint32_t dk[kU][B], nk[kU][B];
-  const int64_t stride = int64_t(gridDim.x) * kThreads * kU;
-  auto load_step = [&](int64_t b) {
+  constexpr int kU = 8;
+  const int grp = p.tsub < 32 ? static_cast<int>(p.tsub) : 32;
+  const int64_t csub = p.tsub < 32 ? 32 : p.tsub;
+  const int64_t nchunks = (p.S + csub - 1) / csub;
+  const int64_t nw = int64_t(gridDim.x) * (kThreads / 32);
+  for (int64_t ch = int64_t(blockIdx.x) * (kThreads / 32) + (threadIdx.x >> 5); ch < nchunks;
+       ch += nw) {
+    const int64_t i0 = ch * csub;
+    const int64_t i1 = imin64(p.S, i0 + csub);
+    uint32_t acc = 0;
+    for (int64_t b = i0; b < i1; b += 32 * kU) {
+      uint32_t dk[kU][B];
 #pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      const int64_t i = b + int64_t(u) * kThreads + threadIdx.x;
-      if (i < p.S) {
-        load_dkeys<B>(p.dkeys, i, nk[u]);
-      } else {
+      for (int u = 0; u < kU; ++u) {
+        const int64_t i = b + u * 32 + lane;
+        if (i < i1) {
+          load_dkeys<B>(p.dkeys, i, dk[u]);
+        } else {
 #pragma unroll
-        for (int q = 0; q < B; ++q) nk[u][q] = 0u;
+          for (int q = 0; q < B; ++q) dk[u][q] = 0u;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int64_t i = b + u * 32 + lane;
+        if (i < i1 && dk[u][0] >= tau) {
+          const int64_t len = sub_len(i, p.alpha, p.n);
+          uint32_t c = 0;
+#pragma unroll
+          for (int q = 0; q < B; ++q) c += (dk[u][q] == tau && q < len) ? 1u : 0u;
+          const uint32_t x = (dk[u][B - 1] >= tau && len > B) ? 1u : 0u;
+          acc += c | (x << 16);
+        }
       }
     }
-  };
-  load_step(int64_t(blockIdx.x) * kThreads * kU);
-  for (int64_t i0 = int64_t(blockIdx.x) * kThreads * kU; i0 < p.S; i0 += stride) {
-    const int64_t t0 = i0 >> p.tsub_log;
-    const int nt_blk = static_cast<int>(
-        ((imin64(p.S, i0 + int64_t(kThreads) * kU) - 1) >> p.tsub_log) - t0 + 1);
-#pragma unroll
-    for (int u = 0; u < kU; ++u)
-#pragma unroll
-      for (int q = 0; q < B; ++q) dk[u][q] = nk[u][q];
-    if (i0 + stride < p.S) load_step(i0 + stride);
-#pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      const int64_t i = i0 + int64_t(u) * kThreads + threadIdx.x;
-      uint32_t c = 0, x = 0;
-      if (i < p.S && dk[u][0] >= tau) {
-        const int64_t len = sub_len(i, p.alpha, p.n);
-#pragma unroll
-        for (int q = 0; q < B; ++q) c += (dk[u][q] == tau && q < len) ? 1u : 0u;
-        x = (dk[u][B - 1] >= tau && len > B) ? 1u : 0u;
-      }
-      for (int o = 1; o < grp; o <<= 1) {
-        c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
-        x += __shfl_xor_sync(0xFFFFFFFFu, x, o);  // inexact subranges of the group
-      }
-      if ((lane & (grp - 1)) == 0 && i < p.S && (c | x)) {
-        const int t = static_cast<int>((i >> p.tsub_log) - t0);
-        atomicAdd(&s_lb[t], c | (x << 16));
-        if (x) atomicOr(&s_lb[t], kTieInexact);
-      }
+    // lb <= B * tsub <= 4096 and inexact <= tsub <= 1024: the packed sums
+    // cannot carry into each other
+    if (grp == 32) {
+      acc = __reduce_add_sync(0xFFFFFFFFu, acc);
+    } else {
+      for (int o = 1; o < grp; o <<= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
     }
-    __syncthreads();
-    for (int q = threadIdx.x; q < nt_blk; q += kThreads) {
-      const uint32_t v = s_lb[q];
-      if (v) {
-        if (v & ~kTieInexact) atomicAdd(&p.tlb[t0 + q], v & ~kTieInexact);
-        if (v & kTieInexact) atomicOr(&p.tlb[t0 + q], kTieInexact);
-      }
-      s_lb[q] = 0;
+    const int64_t first = i0 + (grp == 32 ? 0 : int64_t(lane));
+    if ((lane & (grp - 1)) == 0 && first < p.S) {
+      const uint32_t ninex = acc >> 16;
+      p.tlb[first >> p.tsub_log] = (acc & 0xFFFFu) | (ninex << 16) | (ninex ? kTieInexact : 0u);
     }
-    __syncthreads();
   }
 }
 
@@ -1538,7 +1516,7 @@ __global__ void resolve_kernel(const uint32_t* keys, int64_t n, int64_t S, int a
 
 cudaError_t launch_threshold(const Work& w, int sms, cudaStream_t s) {
   const int64_t count = w.S * w.beta;
-  const int g1 = grid_for(count, kThreads * 16, sms, 4);
+  const int g1 = grid_for(count, kThreads * 16, sms, 6);
   // the one-value shortcut after digit 1 is off under the ablation that
   // stops the select one digit early (its tau must stay the truncated one)
   thr_compact_kernel<<<g1, kThreads, 0, s>>>(w.dkeys, count, w.ds, w.ctl,
@@ -1634,7 +1612,10 @@ cudaError_t launch_ties(const Work& w, const void* keys, int sms, cudaStream_t s
   // look-back words and tile lower bounds start at zero
   cudaError_t e = cudaMemsetAsync(w.tstat, 0, static_cast<size_t>(p.ntiles) * 12, s);
   if (e != cudaSuccess) return e;
-  const int ga = static_cast<int>(std::min<int64_t>((p.S + kThreads * 4 - 1) / (kThreads * 4), int64_t(sms) * 8));
+  // tie_lb: one warp per chunk of max(tsub, 32) subranges
+  const int64_t lb_chunks = (p.S + std::max<int64_t>(p.tsub, 32) - 1) / std::max<int64_t>(p.tsub, 32);
+  const int ga = static_cast<int>(
+      std::min<int64_t>((lb_chunks + kThreads / 32 - 1) / (kThreads / 32), int64_t(sms) * 8));
   const int gc = static_cast<int>(std::min<int64_t>(p.ntiles, int64_t(sms)));
   const int gs = static_cast<int>(std::min<int64_t>(p.ntiles, int64_t(sms) * 4));
 #define DRTOPK_TIE_CASE(DTV, BV)                                                       \
