@@ -448,11 +448,11 @@ drtopk_status run_query(const void* keys, int dtype, int64_t n, int64_t k, int a
     stats->subranges = P.S;
     stats->tau = c.tau;
     stats->kth_mapped = c.kth_mapped;
-    stats->greater = c.g_count;
+    stats->greater = c.g_total;
     stats->ties_needed = (c.mode == kModeTies) ? c.need : 0;
     stats->scanned = c.scanned;
     stats->tie_scanned = c.tie_scanned;
-    stats->survivors = c.sv_count;
+    stats->survivors = c.stage_count[2];
     stats->emitted = c.w_count;
     stats->error = c.error;
     if (c.error & kErrTimeout) st = DRTOPK_ERR_TIMEOUT;

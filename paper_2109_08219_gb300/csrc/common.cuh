@@ -88,8 +88,7 @@ struct Ctl {
   uint32_t tau_ready;
   uint32_t mode;
   uint32_t need;     // ties at tau still needed (mode == kModeTies)
-  uint32_t g_count;  // |{x > tau}| written to G
-  uint32_t sv_count; // survivors of the first digit of the second select
+  uint32_t g_count;  // composites written to G
   uint32_t w_count;  // outputs written to W
   uint32_t error;
   uint32_t scanned;
@@ -112,6 +111,7 @@ struct Ctl {
   uint32_t thr_done;         // tau found after digit 1 (the bucket holds one value)
   uint32_t tie_nlist;        // tiles listed for the tie emission
   uint32_t tie_dense;        // the listed tiles are read whole (bulk copies)
+  uint32_t g_total;          // |G| = |{x > tau}| at the mode decision
 };
 
 // Ablations of the method (drtopk_topk_ablate): Rule 2's filtering off

@@ -29,7 +29,7 @@ namespace drtopk {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kScanKPT = 16;  // virtual keys per thread per filter-scan step
+constexpr int kScanKPT = 8;  // virtual keys per thread per filter-scan step
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
   uint32_t m;
@@ -462,6 +462,7 @@ __global__ void __launch_bounds__(kThreads) filter_resolve_kernel(FilterParams p
     if (threadIdx.x < 32) {
       const uint32_t g = __ldcg(&ctl->g_count);
       const uint64_t k = static_cast<uint64_t>(p.k);
+      if (threadIdx.x == 0) ctl->g_total = g;
       if (g >= k) {
         if (threadIdx.x == 0) {
           ctl->mode = kModeSelect;
@@ -480,44 +481,86 @@ __global__ void __launch_bounds__(kThreads) filter_resolve_kernel(FilterParams p
 }
 
 // All queued subranges read as one virtual array of nq * 2^alpha keys,
-// 8192 per block step, appended with one atomic per block step.
+// 2048 per block step. The queue entries a step needs are staged in shared
+// memory one step ahead (ScanQ), so a step waits for one round trip (its
+// keys), not two (entry, then key). Kept keys are appended with one atomic
+// per block step.
+constexpr int kScanStep = kThreads * kScanKPT;     // virtual keys per block step
+constexpr int kScanQ = kScanStep >> kMinAlpha;     // queue entries per step at most
+constexpr int kScanQPer = kScanQ / kThreads;
+
+struct ScanQ {
+  uint32_t (*s)[kScanQ];  // [2][kScanQ] in shared memory
+  uint32_t r[kScanQPer];  // entries of the next step, in flight
+  int64_t nq;
+  int alpha;
+
+  // entries of the step starting at virtual key b (a multiple of kScanStep)
+  __device__ __forceinline__ int64_t first(int64_t b) const { return b >> alpha; }
+  __device__ __forceinline__ int64_t count(int64_t b) const {
+    const int64_t c = ((b + kScanStep - 1) >> alpha) - (b >> alpha) + 1;
+    return c < kScanQ ? c : kScanQ;
+  }
+  __device__ __forceinline__ void fetch(const uint32_t* scanq, int64_t b) {
+    const int64_t q0 = first(b), c = count(b);
+#pragma unroll
+    for (int e = 0; e < kScanQPer; ++e) {
+      const int64_t j = threadIdx.x + e * kThreads;
+      r[e] = (j < c && q0 + j < nq) ? __ldg(scanq + q0 + j) : 0u;
+    }
+  }
+  __device__ __forceinline__ void put(int buf) {
+#pragma unroll
+    for (int e = 0; e < kScanQPer; ++e) s[buf][threadIdx.x + e * kThreads] = r[e];
+  }
+  // position of virtual key v of the step starting at b
+  __device__ __forceinline__ int64_t pos(int buf, int64_t b, int64_t v) const {
+    return (int64_t(s[buf][(v >> alpha) - (b >> alpha)]) << alpha) + (v & ((int64_t(1) << alpha) - 1));
+  }
+};
+
 template <int DT>
 __global__ void __launch_bounds__(kThreads) filter_scan_kernel(FilterParams p) {
   __shared__ uint32_t sh[256];
+  __shared__ uint32_t s_q[2][kScanQ];
   zero_hist(sh);
-  __syncthreads();
   const uint32_t tau = __ldcg(&p.ctl->tau);
-  const int alpha = p.alpha;
   const int64_t nq = __ldcg(&p.ctl->scanq_count);
-  const int64_t total = nq << alpha;
-  const int64_t mask = (int64_t(1) << alpha) - 1;
-  const uint32_t nact = active_blocks(total, int64_t(kThreads) * kScanKPT);
+  const int64_t total = nq << p.alpha;
+  const uint32_t nact = active_blocks(total, kScanStep);
   if (blockIdx.x >= nact) return;
   RunHist rh;
-  const int64_t step = int64_t(nact) * kThreads * kScanKPT;
-  for (int64_t base = int64_t(blockIdx.x) * kThreads * kScanKPT; base < total; base += step) {
+  const int64_t step = int64_t(nact) * kScanStep;
+  const int64_t b0 = int64_t(blockIdx.x) * kScanStep;
+  ScanQ sq{s_q, {}, nq, p.alpha};
+  if (b0 < total) {
+    sq.fetch(p.scanq, b0);
+    sq.put(0);
+  }
+  __syncthreads();
+  const uint32_t lt = lanemask_lt();
+  int cur = 0;
+  for (int64_t base = b0; base < total; base += step) {
     uint32_t x[kScanKPT];
-    uint32_t sq[kScanKPT];
     uint32_t hit = 0;
-    // phase 1: queue entries (independent loads, all in flight)
-#pragma unroll
-    for (int u = 0; u < kScanKPT; ++u) {
-      const int64_t v = imin64(base + threadIdx.x + int64_t(u) * kThreads, total - 1);
-      sq[u] = __ldg(p.scanq + (v >> alpha));
-    }
-    // phase 2: keys (clamped addresses, unconditional loads)
 #pragma unroll
     for (int u = 0; u < kScanKPT; ++u) {
       const int64_t v = base + threadIdx.x + int64_t(u) * kThreads;
-      const int64_t gi = (int64_t(sq[u]) << alpha) + (v & mask);
-      const bool ok = v < total && gi < p.n;
-      x[u] = map_key<DT>(__ldg(p.keys + (ok ? gi : 0)));
-      if (ok && (x[u] > tau || p.no_filter)) hit |= 1u << u;
+      const int64_t gi = v < total ? sq.pos(cur, base, v) : p.n;
+      const bool ok = gi < p.n;
+      x[u] = __ldg(p.keys + (ok ? gi : 0));
+      if (ok) hit |= 1u << u;
+    }
+    const bool more = base + step < total;
+    if (more) sq.fetch(p.scanq, base + step);  // in flight with this step's keys
+#pragma unroll
+    for (int u = 0; u < kScanKPT; ++u) {
+      x[u] = map_key<DT>(x[u]);
+      if (!(x[u] > tau || p.no_filter)) hit &= ~(1u << u);
     }
     const uint32_t wt = __reduce_add_sync(0xFFFFFFFFu, __popc(hit));
     uint32_t wb, unused;
     block_reserve2<kThreads>(&p.ctl->g_count, wt, nullptr, 0, wb, unused);
-    const uint32_t lt = lanemask_lt();
     uint32_t run = 0;
 #pragma unroll
     for (int u = 0; u < kScanKPT; ++u) {
@@ -525,14 +568,16 @@ __global__ void __launch_bounds__(kThreads) filter_scan_kernel(FilterParams p) {
       const uint32_t bal = __ballot_sync(0xFFFFFFFFu, h);
       if (h) {
         const int64_t v = base + threadIdx.x + int64_t(u) * kThreads;
-        const int64_t gi = (int64_t(sq[u]) << alpha) + (v & mask);
         const uint32_t slot = wb + run + __popc(bal & lt);
-        if (slot < p.g_cap) p.g[slot] = make_comp(x[u], static_cast<uint32_t>(gi));
+        if (slot < p.g_cap) p.g[slot] = make_comp(x[u], static_cast<uint32_t>(sq.pos(cur, base, v)));
         else atomicOr(&p.ctl->error, kErrOverflowG);
         rh.add(sh, x[u] >> 24);
       }
       run += __popc(bal);
     }
+    if (more) sq.put(cur ^ 1);
+    __syncthreads();
+    cur ^= 1;
   }
   rh.flush(sh);
   __syncthreads();
@@ -1561,7 +1606,7 @@ cudaError_t launch_filter(const Work& w, const void* keys, bool kth_only, int sm
   // requests to resolve: at most rq_cap, one per thread per block step
   const int g3 = grid_for(w.rq_cap, kThreads, sms, 4);
   // scanned keys are bounded by the G capacity (or n when tau = 0)
-  const int g2 = grid_for(w.g_cap, kThreads * kScanKPT, sms, 8);
+  const int g2 = grid_for(w.g_cap, kScanStep, sms, 4);
 #define DRTOPK_FILTER_CASE(DTV)                              \
   switch (w.beta) {                                          \
     case 1: filter_t<DTV, 1>(p, g1, g2, g3, s); break;       \

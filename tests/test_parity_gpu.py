@@ -319,3 +319,38 @@ def test_tie_paths_dense_and_sparse():
                 assert st["error"] == 0, (name, k, alpha, st)
                 assert np.array_equal(host_bits(ok), rk) and np.array_equal(oi.cpu().numpy(), ri), \
                     (name, k, alpha, st)
+
+
+def test_large_scan_sets():
+    """Scan sets of more than 2^22 keys (sorted input, large k: Rule 2 keeps
+    k / beta whole subranges): select mode over many scan steps,
+    k-selection, and tie mode with every subrange scanned."""
+    n = 1 << 25
+    large = 0
+    for dt, kind in (("u32", "asc"), ("u32", "desc"), ("f32", "asc")):
+        bits = make(kind, n, 41, dt)
+        x = to_dev(bits, dt)
+        for k, alpha in ((1 << 20, 0), (1 << 18, 6), (300001, 8)):
+            st = check_topk(bits, dt, k, alpha=alpha)
+            large += (st["scanned"] << st["alpha"]) > (1 << 22)
+            assert st["greater"] >= k, st
+        got = drtopk.drtopk_kth(x, 1 << 20, dtype=dt)
+        torch.cuda.synchronize()
+        assert int(host_bits(got)[0]) == oracle.kth(bits, DT[dt], 1 << 20), (dt, kind)
+    assert large >= 6
+    # two large keys per 64-key subrange, zeros elsewhere: with k just above
+    # the number of large keys, tau = 0, every subrange is scanned and the
+    # last 1000 answers are the zeros of smallest index
+    rng = np.random.default_rng(43)
+    S = n >> 6
+    bits = np.zeros(n, np.uint32)
+    off = np.argsort(rng.random((S, 64)), axis=1)[:, :2]
+    pos = (np.arange(S)[:, None] * 64 + off).ravel()
+    bits[pos] = rng.integers(1, 2**32, pos.size, dtype=np.uint64).astype(np.uint32)
+    k = 2 * S + 1000
+    st = check_topk(bits, "u32", k, alpha=6, beta=2)
+    assert st["tau"] == 0 and st["greater"] == 2 * S and st["ties_needed"] == 1000, st
+    assert (st["scanned"] << 6) > (1 << 22), st
+    got = drtopk.drtopk_kth(to_dev(bits, "u32"), k, dtype="u32")
+    torch.cuda.synchronize()
+    assert int(host_bits(got)[0]) == 0
