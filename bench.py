@@ -665,6 +665,19 @@ def main():
         del xs
         torch.cuda.empty_cache()
 
+        # the host link alone: one H2D copy of each pinned input (the bound
+        # of any path that must move the keys to the GPU)
+        stage = torch.empty(n, dtype=torch.int32, device=dev)
+        stage.copy_(hosts[dists[0]], non_blocking=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for d in dists:
+            stage.copy_(hosts[d], non_blocking=True)
+        torch.cuda.synchronize()
+        link_gbs = 4.0 * n * len(dists) / (time.perf_counter() - t0) / 1e9
+        del stage
+        torch.cuda.empty_cache()
+
         def estep():
             for d in dists:
                 for k in ks:
@@ -681,7 +694,9 @@ def main():
         out["e2e"] = {"value": float(n) * queries * esteps / et / 1e9, "unit": "Gkeys/s",
                       "h2d_bytes_per_step": 4 * n * queries,
                       "d2h_bytes_per_step": 8 * sum(ks) * len(dists),
-                      "steps": esteps, "api": "drtopk_topk_host (pinned host keys)"}
+                      "steps": esteps, "api": "drtopk_topk_host (pinned host keys)",
+                      "h2d_link_gbs": link_gbs,
+                      "link_bound_gkeys": link_gbs / 4.0}
 
     print(json.dumps(out))
 

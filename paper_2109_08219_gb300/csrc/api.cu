@@ -285,6 +285,15 @@ struct GraphEntry {
   uint64_t nlaunch = 0;
 };
 
+// Device staging of drtopk_topk_host, one buffer per device.
+constexpr int kMaxDevices = 64;
+struct HostStage {
+  std::mutex mu;
+  char* d = nullptr;
+  size_t cap = 0;
+};
+HostStage g_hstage[kMaxDevices];
+
 constexpr size_t kGraphMaxEntries = 64;
 constexpr size_t kSeenKeys = 256;
 std::mutex g_gmu;
@@ -582,16 +591,34 @@ drtopk_status drtopk_topk_host(const void* keys, drtopk_dtype dtype, int64_t n, 
   drtopk_status st = check_args(keys, dtype, n, k);
   if (st != DRTOPK_OK) return st;
   if (!out_keys || !out_idx) return DRTOPK_ERR_INVALID;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return DRTOPK_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  char* d = nullptr;
   const size_t kb = al(static_cast<size_t>(n) * 4);
   const size_t ob = al(static_cast<size_t>(k) * 4);
-  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&d), kb + 2 * ob, s);
-  if (e != cudaSuccess) return cuda_status(e);
-  e = cudaMemcpyAsync(d, keys, static_cast<size_t>(n) * 4, cudaMemcpyHostToDevice, s);
+  // the device's staging buffer, grown to the largest call and kept: the
+  // same addresses every call, so the query replays a cached graph
+  HostStage& hs = g_hstage[dev];
+  std::lock_guard<std::mutex> lk(hs.mu);
+  if (hs.cap < kb + 2 * ob) {
+    if (hs.d) {
+      cudaError_t e = cudaFree(hs.d);  // waits for the device
+      hs.d = nullptr;
+      hs.cap = 0;
+      if (e != cudaSuccess) return cuda_status(e);
+    }
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&hs.d), kb + 2 * ob);
+    if (e != cudaSuccess) {
+      hs.d = nullptr;
+      return cuda_status(e);
+    }
+    hs.cap = kb + 2 * ob;
+  }
+  char* d = hs.d;
+  cudaError_t e = cudaMemcpyAsync(d, keys, static_cast<size_t>(n) * 4, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) {
     st = run_query(d, dtype, n, k, 0, 0, d + kb, reinterpret_cast<int32_t*>(d + kb + ob), nullptr,
-                   nullptr, s, false);
+                   nullptr, s, true);
     if (st == DRTOPK_OK) {
       e = cudaMemcpyAsync(out_keys, d + kb, static_cast<size_t>(k) * 4, cudaMemcpyDeviceToHost, s);
       if (e == cudaSuccess)
@@ -599,10 +626,8 @@ drtopk_status drtopk_topk_host(const void* keys, drtopk_dtype dtype, int64_t n, 
                             cudaMemcpyDeviceToHost, s);
     }
   }
-  cudaError_t e2 = cudaFreeAsync(d, s);
   cudaError_t e3 = cudaStreamSynchronize(s);
   if (st != DRTOPK_OK) return st;
-  if (e == cudaSuccess) e = e2;
   if (e == cudaSuccess) e = e3;
   return cuda_status(e);
 }

@@ -202,10 +202,16 @@ def test_generated_workload_recipes_small():
 
 
 def test_host_entry_point():
-    bits = make("few", 77777, 1, "u32")
-    ok, oi = drtopk.drtopk_topk_host(bits, 500, "u32")
-    rk, ri = oracle.topk(bits, oracle.U32, 500)
-    assert np.array_equal(ok, rk) and np.array_equal(oi, ri)
+    """Host keys through the library's staging buffer: repeated shapes with
+    new contents (graph replays), a larger call that grows the buffer, and
+    the small shape again inside the grown buffer."""
+    calls = [("few", 77777, 500, 1), ("uniform", 77777, 500, 2), ("asc", 77777, 500, 3),
+             ("uniform", 300007, 70000, 4), ("few", 77777, 500, 5), ("zipf", 77777, 500, 6)]
+    for kind, n, k, seed in calls:
+        bits = make(kind, n, seed, "u32")
+        ok, oi = drtopk.drtopk_topk_host(bits, k, "u32")
+        rk, ri = oracle.topk(bits, oracle.U32, k)
+        assert np.array_equal(ok, rk) and np.array_equal(oi, ri), (kind, n, k)
 
 
 def test_streams_and_repeat_calls_are_independent():
