@@ -368,6 +368,26 @@ struct WarpStage {
     fill = 0;
   }
 
+  // Reserves `cnt` consecutive slots for every lane (prefix over the warp;
+  // at most CAP in total), flushing first when they do not fit; returns the
+  // lane's first slot in buf. The lanes write their slots before the next
+  // call.
+  __device__ __forceinline__ uint32_t reserve(uint32_t cnt, uint32_t* gctr, T* gdst, uint64_t gcap,
+                                              uint32_t* err, uint32_t ebit) {
+    const uint32_t lane = threadIdx.x & 31u;
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if (lane >= static_cast<uint32_t>(o)) incl += t;
+    }
+    const uint32_t tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    if (fill + tot > CAP) flush(gctr, gdst, gcap, err, ebit);
+    const uint32_t pos = fill + incl - cnt;
+    fill += tot;
+    return pos;
+  }
+
   // Stages `item` of every lane with `has` (flushing first when the buffer
   // cannot take them all).
   __device__ __forceinline__ void push(bool has, T item, uint32_t* gctr, T* gdst, uint64_t gcap,

@@ -187,16 +187,29 @@ __global__ void __launch_bounds__(kThreads) thr_compact_kernel(const uint32_t* d
   for (int64_t base = int64_t(blockIdx.x) * kThreads * 16; base < count; base += step) {
     uint32_t v[16];
     load16<kThreads>(dkeys, count, base, v);
+    const bool full = base + kThreads * 16 <= count;  // no bounds checks needed
+    uint32_t hit = 0;
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
-      const int64_t i = base + (int64_t(e >> 2) * kThreads + threadIdx.x) * 4 + (e & 3);
-      const bool hit = i < count && (v[e] >> 24) == d0;
-      if (hit) {
-        rh.add(sh, (v[e] >> 16) & 255u);
-        lo = min(lo, v[e]);
-        hi = max(hi, v[e]);
+      bool in = true;
+      if (!full) in = base + (int64_t(e >> 2) * kThreads + threadIdx.x) * 4 + (e & 3) < count;
+      if (in && (v[e] >> 24) == d0) hit |= 1u << e;
+    }
+    if (__any_sync(0xFFFFFFFFu, hit != 0)) {  // the bucket is small: most warp steps skip this
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        if ((hit >> e) & 1u) {
+          rh.add(sh, (v[e] >> 16) & 255u);
+          lo = min(lo, v[e]);
+          hi = max(hi, v[e]);
+        }
       }
-      if (!inplace) stg.push(hit, v[e], &ctl->ds_count, ds, ~uint64_t(0), &ctl->error, 0u);
+      if (!inplace) {
+        uint32_t pos = stg.reserve(__popc(hit), &ctl->ds_count, ds, ~uint64_t(0), &ctl->error, 0u);
+#pragma unroll
+        for (int e = 0; e < 16; ++e)
+          if ((hit >> e) & 1u) stg.buf[pos++] = v[e];
+      }
     }
   }
   if (!inplace) stg.flush(&ctl->ds_count, ds, ~uint64_t(0), &ctl->error, 0u);
@@ -332,34 +345,44 @@ __global__ void __launch_bounds__(kThreads) filter_classify_kernel(FilterParams 
 #pragma unroll
       for (int j = 0; j < B; ++j) dk[u][j] = nk[u][j];
     if (base + int64_t(gridDim.x) * per_step < p.S) load_step(base + int64_t(gridDim.x) * per_step);
+    uint32_t scanm = 0;  // subranges to scan (bit u)
+    uint32_t emitm = 0;  // delegate slots to place (bit u * B + j)
 #pragma unroll
     for (int u = 0; u < kClsSub; ++u) {
       const int64_t i = base + int64_t(u) * kThreads + threadIdx.x;
-      bool scan = false;
-      uint32_t emit = 0;  // delegate slots to place
       if (p.no_filter) {
         // Rule 1 alone: a subrange whose maximum delegate reaches tau is kept whole
-        scan = i < p.S && dk[u][0] >= tau;
+        if (i < p.S && dk[u][0] >= tau) scanm |= 1u << u;
       } else if (i < p.S && dk[u][0] > tau) {
         if (dk[u][B - 1] > tau && sub_len(i, alpha, p.n) > B) {
-          scan = true;
+          scanm |= 1u << u;
         } else {
           // its keys > tau are exactly its delegates > tau (Rule 3); their
           // positions are resolved by filter_resolve_kernel
 #pragma unroll
-          for (int j = 0; j < B; ++j) emit |= (dk[u][j] > tau) ? (1u << j) : 0u;
+          for (int j = 0; j < B; ++j) emitm |= (dk[u][j] > tau) ? (1u << (u * B + j)) : 0u;
         }
       }
-      sq.push(scan, static_cast<uint32_t>(i), &p.ctl->scanq_count, p.scanq, ~uint64_t(0),
-              &p.ctl->error, 0u);
-      nscan += scan ? 1u : 0u;
-      if (__any_sync(0xFFFFFFFFu, emit != 0)) {
+    }
+    if (__any_sync(0xFFFFFFFFu, scanm != 0)) {
+      uint32_t pos = sq.reserve(__popc(scanm), &p.ctl->scanq_count, p.scanq, ~uint64_t(0),
+                                &p.ctl->error, 0u);
+#pragma unroll
+      for (int u = 0; u < kClsSub; ++u)
+        if ((scanm >> u) & 1u)
+          sq.buf[pos++] = static_cast<uint32_t>(base + int64_t(u) * kThreads + threadIdx.x);
+      nscan += __popc(scanm);
+    }
+    if (__any_sync(0xFFFFFFFFu, emitm != 0)) {
+      uint32_t pos = sr.reserve(__popc(emitm), &p.ctl->rq_count, p.rq,
+                                static_cast<uint64_t>(p.rq_cap), &p.ctl->error, kErrOverflowG);
+#pragma unroll
+      for (int u = 0; u < kClsSub; ++u)
 #pragma unroll
         for (int j = 0; j < B; ++j)
-          sr.push((emit >> j) & 1u, static_cast<uint32_t>(i << 2) | static_cast<uint32_t>(j),
-                  &p.ctl->rq_count, p.rq, static_cast<uint64_t>(p.rq_cap), &p.ctl->error,
-                  kErrOverflowG);
-      }
+          if ((emitm >> (u * B + j)) & 1u)
+            sr.buf[pos++] = static_cast<uint32_t>((base + int64_t(u) * kThreads + threadIdx.x) << 2) |
+                            static_cast<uint32_t>(j);
     }
   }
   sq.flush(&p.ctl->scanq_count, p.scanq, ~uint64_t(0), &p.ctl->error, 0u);
@@ -1561,7 +1584,7 @@ __global__ void resolve_kernel(const uint32_t* keys, int64_t n, int64_t S, int a
 
 cudaError_t launch_threshold(const Work& w, int sms, cudaStream_t s) {
   const int64_t count = w.S * w.beta;
-  const int g1 = grid_for(count, kThreads * 16, sms, 6);
+  const int g1 = grid_for(count, kThreads * 16, sms, 4);
   // the one-value shortcut after digit 1 is off under the ablation that
   // stops the select one digit early (its tau must stay the truncated one)
   thr_compact_kernel<<<g1, kThreads, 0, s>>>(w.dkeys, count, w.ds, w.ctl,
