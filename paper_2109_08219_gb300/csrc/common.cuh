@@ -345,9 +345,9 @@ __device__ __forceinline__ void stage_flush(T* buf, uint32_t* s_fill, uint32_t* 
 }
 
 // Per-warp variant: a warp gathers items in its own shared buffer of CAP
-// entries (ranked by ballots, no block barrier) and copies them out with one
-// atomicAdd per flush. All 32 lanes call push/flush with the same
-// arguments; `fill` stays warp-uniform.
+// entries (a prefix over the lanes, no block barrier) and copies them out
+// with one atomicAdd per flush. All 32 lanes call reserve/flush with the
+// same arguments; `fill` stays warp-uniform.
 template <typename T, int CAP>
 struct WarpStage {
   T* buf;
@@ -386,19 +386,6 @@ struct WarpStage {
     const uint32_t pos = fill + incl - cnt;
     fill += tot;
     return pos;
-  }
-
-  // Stages `item` of every lane with `has` (flushing first when the buffer
-  // cannot take them all).
-  __device__ __forceinline__ void push(bool has, T item, uint32_t* gctr, T* gdst, uint64_t gcap,
-                                       uint32_t* err, uint32_t ebit) {
-    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, has);
-    if (bal == 0) return;
-    if (fill + __popc(bal) > CAP) flush(gctr, gdst, gcap, err, ebit);
-    uint32_t lt;
-    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
-    if (has) buf[fill + __popc(bal & lt)] = item;
-    fill += __popc(bal);
   }
 };
 
