@@ -18,10 +18,12 @@
 // only when its count is not already known from its delegates and an
 // earlier prefix could still be short.
 //
-// GB300 organisation: every variable-size output is appended with one
-// atomic per block (block_append); uneven work (scanned subranges, tie
-// counts) goes through global queues that all warps of the grid drain; each
-// radix pass keeps only the survivors of the previous digit.
+// GB300 organisation: every variable-size output is gathered in shared
+// memory and appended with one atomic per block step or per warp flush
+// (block_reserve2, stage_reserve / stage_flush, WarpStage); uneven work
+// (scanned subranges, tie counts) goes through global queues that all
+// warps of the grid drain; each radix pass keeps only the survivors of the
+// previous digit.
 #include "common.cuh"
 #include "launch.h"
 

@@ -8,7 +8,7 @@
 //   * k <= 4096: one CTA bitonic-sorts W in shared memory;
 //   * larger k: a stable LSD radix sort of the complemented composites
 //     (ascending) with 8-bit digits. One kernel histograms all 8 digits at
-//     once; each digit pass is then a single kernel: tiles of 4096 are taken
+//     once; each digit pass is then a single kernel: tiles of 8192 are taken
 //     in order from an atomic counter, ranked stably in shared memory, and
 //     their global offsets come from a decoupled look-back over the earlier
 //     tiles' per-digit counts (bounded waits). A digit equal for all k
@@ -22,7 +22,7 @@ namespace {
 constexpr int kSmallSort = 4096;
 constexpr int kSortThreads = 512;
 constexpr int kItems = 16;
-constexpr int kTile = kSortThreads * kItems;  // 16384
+constexpr int kTile = kSortThreads * kItems;  // 8192
 constexpr int kHistThreads = 256;
 constexpr uint64_t kFlagAgg = uint64_t(1) << 32;
 constexpr uint64_t kFlagIncl = uint64_t(2) << 32;
