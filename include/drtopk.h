@@ -27,14 +27,19 @@
  *   - 1 <= k <= n <= 2^31 - 1. Other values return DRTOPK_ERR_K (k) or
  *     DRTOPK_ERR_INVALID (n, pointers).
  *   - Device pointers point to memory of the current CUDA device. Keys must
- *     be 4-byte aligned; 16-byte alignment takes the TMA fast path.
+ *     be 4-byte aligned; 16-byte alignment takes the TMA fast path. With any
+ *     alignment, bulk copies may read the bytes of the 16-byte block that
+ *     holds keys[0] before keys[0] (never past the 16-byte block that holds
+ *     keys[n-1]); those bytes are never part of a result.
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *     stream). Calls are asynchronous on `stream` unless stated otherwise:
  *     results are valid once the stream has reached the call. The input
  *     must stay alive and unmodified until then.
  *   - The library allocates its temporary workspace with the stream-ordered
- *     allocator (cudaMallocAsync / cudaFreeAsync on `stream`) and owns it;
- *     the caller owns every input and output buffer.
+ *     allocator from a memory pool of its own per device (freed workspace
+ *     stays cached there; the device's default pool is left untouched) and
+ *     owns it; under a caller's stream capture the workspace is a graph
+ *     allocation. The caller owns every input and output buffer.
  *   - drtopk_kth, drtopk_topk and drtopk_topk_ex (without statistics) keep a
  *     cache of CUDA graphs of whole queries, keyed by every argument
  *     (pointers, sizes, dtype, alpha, beta, device, stream): the second
@@ -47,6 +52,17 @@
  *     launch kernel by kernel (into the caller's capture).
  *   - Calls return a drtopk_status and never abort. A CUDA error returns
  *     DRTOPK_ERR_CUDA; argument checks happen before any CUDA call.
+ *   - Device-side errors: every wait inside a kernel is bounded; a wait
+ *     that gives up (DRTOPK_ERR_TIMEOUT) or a capacity guard that fires
+ *     (DRTOPK_ERR_INTERNAL) leaves that query's outputs undefined. Since
+ *     calls are asynchronous, such an error is reported later: the last
+ *     kernel of each query of drtopk_kth / drtopk_topk / drtopk_topk_ex
+ *     (without statistics) ORs its error flags into a per-device report
+ *     word, which the next of these calls on the device reads and clears
+ *     (it then returns the error and does nothing), and which
+ *     drtopk_sync_status reads and clears after synchronizing. Calls with
+ *     statistics and the synchronous calls (drtopk_topk_host, batched
+ *     plans' status, server tickets) report their own errors directly.
  */
 #ifndef DRTOPK_H
 #define DRTOPK_H
@@ -73,11 +89,32 @@ typedef enum {
   DRTOPK_ERR_CUDA = 5,    /* a CUDA call failed */
   DRTOPK_ERR_BUDGET = 6,  /* server: request larger than the HBM budget */
   DRTOPK_ERR_TIMEOUT = 7, /* a bounded device-side wait gave up */
-  DRTOPK_PENDING = 8      /* server: ticket not finished yet */
+  DRTOPK_PENDING = 8,     /* server: ticket not finished yet */
+  DRTOPK_ERR_INTERNAL = 9 /* a device-side capacity guard fired */
 } drtopk_status;
 
 /* Human-readable name of a status. Never NULL. */
 const char* drtopk_status_str(drtopk_status s);
+
+/*
+ * Synchronizes `stream`, then reads and clears the device-side error flags
+ * reported on the current device since the last check (by single queries
+ * and by drtopk_kth_noalloc; see the conventions above): DRTOPK_OK when
+ * none, DRTOPK_ERR_TIMEOUT when a bounded wait gave up, DRTOPK_ERR_INTERNAL
+ * for any other device-side flag. The flags are per device, not per stream.
+ */
+drtopk_status drtopk_sync_status(void* stream);
+
+/*
+ * Self-test of device-side wait handling (no counterpart in the paper):
+ * launches one small kernel on `stream` that waits, bounded by timeout_us
+ * microseconds (1 .. 10^7), on an mbarrier phase that nothing completes,
+ * using the same bounded wait as the bulk-copy rings, and reports the
+ * timeout through the device's report word like a query does. Afterwards
+ * drtopk_sync_status returns DRTOPK_ERR_TIMEOUT once; the context stays
+ * usable. No GPU fault is involved.
+ */
+drtopk_status drtopk_wait_selftest(uint32_t timeout_us, void* stream);
 
 /*
  * Parameter choice (host only, no CUDA call). Rule 4 / Eq. 9 (Sec. 4.2):
@@ -188,6 +225,8 @@ drtopk_status drtopk_delegates(const void* keys, drtopk_dtype dtype,
  *     contents (the call clears what must start at zero). Calls that overlap
  *     on the GPU (different streams or threads without ordering between
  *     them) race on the array and give wrong results: order them.
+ *   - Device-side errors of these calls are reported by drtopk_sync_status
+ *     (the call itself cannot read them back without allocating).
  */
 drtopk_status drtopk_kth_noalloc(const void* keys, drtopk_dtype dtype,
                                  int64_t n, int64_t k, void* out_kth,
@@ -416,6 +455,12 @@ drtopk_status drtopk_profile_end(drtopk_profile* out);
 
 /* Number of kernels this library has launched since it was loaded. */
 uint64_t drtopk_launch_count(void);
+
+/* Number of device or pinned-host allocations this library has made since
+ * it was loaded (each workspace taken from its stream-ordered pool counts,
+ * as do memory pools, staging buffers, graph-cache workspaces, batched
+ * plans and server buffers). Host only. */
+uint64_t drtopk_alloc_count(void);
 
 #ifdef __cplusplus
 }

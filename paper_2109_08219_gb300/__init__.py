@@ -23,7 +23,7 @@ _NAMES = {"u32": U32, "i32": I32, "f32": F32}
 
 STATUS = ["DRTOPK_OK", "DRTOPK_ERR_INVALID", "DRTOPK_ERR_K", "DRTOPK_ERR_DTYPE",
           "DRTOPK_ERR_NOMEM", "DRTOPK_ERR_CUDA", "DRTOPK_ERR_BUDGET",
-          "DRTOPK_ERR_TIMEOUT", "DRTOPK_PENDING"]
+          "DRTOPK_ERR_TIMEOUT", "DRTOPK_PENDING", "DRTOPK_ERR_INTERNAL"]
 NUM_STAGES = 6
 STAGE_NAMES = ["delegate", "threshold", "filter", "ties", "second_select", "sort"]
 BATCH_PHASES = ["delegate", "threshold", "filter", "second_select", "ties", "sort_output",
@@ -90,10 +90,14 @@ def lib():
         L.drtopk_topk_host.argtypes = [p, i32, i64, i64, p, p, p]
         L.drtopk_kth_noalloc.argtypes = [p, i32, i64, i64, p, p]
         L.drtopk_kth_noalloc.restype = i32
+        L.drtopk_sync_status.argtypes = [p]
+        L.drtopk_wait_selftest.argtypes = [ctypes.c_uint32, p]
         L.drtopk_profile_begin.argtypes = []
         L.drtopk_profile_end.argtypes = [ctypes.POINTER(Profile)]
         L.drtopk_launch_count.argtypes = []
         L.drtopk_launch_count.restype = ctypes.c_uint64
+        L.drtopk_alloc_count.argtypes = []
+        L.drtopk_alloc_count.restype = ctypes.c_uint64
         pi32 = ctypes.POINTER(ctypes.c_int32)
         pi64 = ctypes.POINTER(ctypes.c_int64)
         L.drtopk_batch_plan_create.argtypes = [i32, pi64, pi32, i32, i32, i32,
@@ -117,7 +121,7 @@ def lib():
         L.drtopk_tune_get.argtypes = [i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
         L.drtopk_tune_set.argtypes = [i32, i32, i32, i32]
         L.drtopk_autotune_batched.argtypes = [i32, i32, i32, i32, p]
-        for fn in ("drtopk_plan", "drtopk_kth", "drtopk_topk", "drtopk_topk_ex", "drtopk_topk_ablate",
+        for fn in ("drtopk_sync_status", "drtopk_wait_selftest", "drtopk_plan", "drtopk_kth", "drtopk_topk", "drtopk_topk_ex", "drtopk_topk_ablate",
                    "drtopk_delegates", "drtopk_topk_host", "drtopk_profile_begin",
                    "drtopk_profile_end", "drtopk_batch_plan_create", "drtopk_batch_plan_run",
                    "drtopk_batch_plan_status", "drtopk_batch_plan_params",
@@ -170,6 +174,19 @@ def _dev(t):
 
 def status_str(status):
     return lib().drtopk_status_str(status).decode()
+
+
+def sync_status(stream=None):
+    """Synchronizes the stream and raises DrTopkError when queries on the
+    current device reported a device-side error since the last check
+    (drtopk_sync_status); the flags are cleared."""
+    _check(lib().drtopk_sync_status(_stream(stream)), "drtopk_sync_status")
+
+
+def wait_selftest(timeout_us, stream=None):
+    """Launches the bounded-wait self-test kernel (drtopk_wait_selftest):
+    a wait on a phase nothing completes, given up after timeout_us."""
+    _check(lib().drtopk_wait_selftest(timeout_us, _stream(stream)), "drtopk_wait_selftest")
 
 
 def drtopk_plan(n, k):
@@ -315,6 +332,11 @@ def profile_end():
 
 def launch_count():
     return int(lib().drtopk_launch_count())
+
+
+def alloc_count():
+    """Allocations the library has made since it was loaded (drtopk_alloc_count)."""
+    return int(lib().drtopk_alloc_count())
 
 
 # ------------------------------------------------------------------ batched --

@@ -14,26 +14,33 @@ namespace drtopk {
 
 static std::atomic<uint64_t> g_launches{0};
 void note_launch(int n) { g_launches.fetch_add(static_cast<uint64_t>(n)); }
+static std::atomic<uint64_t> g_allocs{0};
+void note_alloc(int n) { g_allocs.fetch_add(static_cast<uint64_t>(n)); }
 
 namespace {
 
 // ------------------------------------------------------------- planning ---
-struct Plan {
-  int alpha;
-  int beta;
-  int64_t S;
-  int64_t g_cap;
-  bool fuse_hist;  // beta * S >= k: tau from the delegates, else tau = 0
-  int ablate = 0;
-};
-
 int alpha_rule4(int64_t n, int64_t k) {
   // Rule 4 / Eq. 9 with const = 3, rounded down (Sec. 4.2)
   const double a = 0.5 * (std::log2(static_cast<double>(n)) - std::log2(static_cast<double>(k)) + 3.0);
   return static_cast<int>(std::floor(a));
 }
 
-bool make_plan(int64_t n, int64_t k, int alpha, int beta, Plan* p, int ablate = 0) {
+constexpr size_t kAlign = 256;
+size_t al(size_t b) { return (b + kAlign - 1) & ~(kAlign - 1); }
+
+// Delegates the filter may queue for position resolution: those > tau,
+// fewer than k when tau is the k-th delegate (or all beta S of them when
+// there are fewer than k); every delegate under the shortcut ablation.
+int64_t rq_capacity(const Plan& p, int64_t k) {
+  const int64_t d = p.S * p.beta;
+  if (p.ablate & kAblateSkipLastDigit) return d;
+  return std::max<int64_t>(1, std::min(d, k));
+}
+
+}  // namespace
+
+bool make_plan(int64_t n, int64_t k, int alpha, int beta, Plan* p, int ablate) {
   if (beta <= 0) beta = 2;  // Sec. 3.3: beta = 2 performs best
   if (beta < 1 || beta > kMaxBeta) return false;
   if (alpha <= 0) {
@@ -62,22 +69,6 @@ bool make_plan(int64_t n, int64_t k, int alpha, int beta, Plan* p, int ablate = 
   return true;
 }
 
-constexpr size_t kAlign = 256;
-size_t al(size_t b) { return (b + kAlign - 1) & ~(kAlign - 1); }
-
-struct Layout {
-  size_t ctl, dkeys, dsegs, ds, scanq, rq, g, sv, w, w2, tstat, sstat, total;
-};
-
-// Delegates the filter may queue for position resolution: those > tau,
-// fewer than k when tau is the k-th delegate (or all beta S of them when
-// there are fewer than k); every delegate under the shortcut ablation.
-int64_t rq_capacity(const Plan& p, int64_t k) {
-  const int64_t d = p.S * p.beta;
-  if (p.ablate & kAblateSkipLastDigit) return d;
-  return std::max<int64_t>(1, std::min(d, k));
-}
-
 Layout layout(const Plan& p, int64_t k, bool need_topk, bool external_dkeys) {
   Layout L;
   const size_t D = static_cast<size_t>(p.S) * p.beta;
@@ -98,30 +89,104 @@ Layout layout(const Plan& p, int64_t k, bool need_topk, bool external_dkeys) {
   return L;
 }
 
+void bind_work(Work& w, char* ws, const Layout& L, const Plan& P, int64_t n, int64_t k,
+               int dtype) {
+  w.ctl = reinterpret_cast<Ctl*>(ws + L.ctl);
+  w.dkeys = reinterpret_cast<uint32_t*>(ws + L.dkeys);
+  w.dsegs = reinterpret_cast<uint16_t*>(ws + L.dsegs);
+  w.ds = reinterpret_cast<uint32_t*>(ws + L.ds);
+  w.scanq = reinterpret_cast<uint32_t*>(ws + L.scanq);
+  w.rq = reinterpret_cast<uint32_t*>(ws + L.rq);
+  w.rq_cap = rq_capacity(P, k);
+  w.g = reinterpret_cast<uint64_t*>(ws + L.g);
+  w.sv = reinterpret_cast<uint64_t*>(ws + L.sv);
+  w.w = reinterpret_cast<uint64_t*>(ws + L.w);
+  w.w2 = reinterpret_cast<uint64_t*>(ws + L.w2);
+  w.tstat = reinterpret_cast<uint64_t*>(ws + L.tstat);
+  w.sort_status = reinterpret_cast<uint64_t*>(ws + L.sstat);
+  w.n = n;
+  w.S = P.S;
+  w.g_cap = P.g_cap;
+  w.k = k;
+  w.alpha = P.alpha;
+  w.beta = P.beta;
+  w.dtype = dtype;
+  w.ablate = P.ablate;
+  w.err_out = nullptr;
+}
+
+drtopk_status error_status(uint32_t flags) {
+  if (flags == 0) return DRTOPK_OK;
+  return (flags & kErrTimeout) ? DRTOPK_ERR_TIMEOUT : DRTOPK_ERR_INTERNAL;
+}
+
+namespace {
+
 // --------------------------------------------------------------- device ---
+// Per device: SM count, the library's own stream-ordered memory pool (freed
+// workspace stays cached in it; the device's default pool is left as the
+// process configured it) and the report word of device-side errors: one
+// host-mapped word that the last kernel of every query ORs its error flags
+// into, read and cleared by the next call on the device or by
+// drtopk_sync_status.
 struct DevInfo {
   int sms = 0;
-  bool pool_set = false;
+  cudaMemPool_t pool = nullptr;
+  uint32_t* err_host = nullptr;  // mapped pinned host word
+  uint32_t* err_dev = nullptr;   // its device address
 };
 std::mutex g_dev_mu;
 DevInfo g_dev[64];
 
-drtopk_status dev_info(int* sms) {
+drtopk_status dev_info(int* sms, DevInfo** out = nullptr) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return DRTOPK_ERR_CUDA;
   std::lock_guard<std::mutex> lk(g_dev_mu);
   DevInfo& d = g_dev[dev];
   if (d.sms == 0) {
-    if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    int nsm = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
       return DRTOPK_ERR_CUDA;
-    cudaMemPool_t pool;
-    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
-      uint64_t thr = UINT64_MAX;  // keep freed workspace cached in the pool
-      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) return DRTOPK_ERR_CUDA;
+    note_alloc(2);  // the pool and the report word below
+    uint64_t thr = UINT64_MAX;  // keep freed workspace cached in the pool
+    if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr) != cudaSuccess) {
+      cudaMemPoolDestroy(pool);
+      return DRTOPK_ERR_CUDA;
     }
+    uint32_t* h = nullptr;
+    uint32_t* dp = nullptr;
+    if (cudaHostAlloc(reinterpret_cast<void**>(&h), sizeof(uint32_t),
+                      cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+      cudaMemPoolDestroy(pool);
+      return DRTOPK_ERR_CUDA;
+    }
+    *h = 0;
+    if (cudaHostGetDevicePointer(reinterpret_cast<void**>(&dp), h, 0) != cudaSuccess) {
+      cudaFreeHost(h);
+      cudaMemPoolDestroy(pool);
+      return DRTOPK_ERR_CUDA;
+    }
+    d.pool = pool;
+    d.err_host = h;
+    d.err_dev = dp;
+    d.sms = nsm;
   }
   *sms = d.sms;
+  if (out) *out = &d;
   return DRTOPK_OK;
+}
+
+// Takes (reads and clears) the error flags reported on the device so far.
+uint32_t take_errors(DevInfo* d) {
+  if (!d || !d->err_host) return 0;
+  return __atomic_exchange_n(d->err_host, 0u, __ATOMIC_ACQ_REL);
 }
 
 // ------------------------------------------------------------ profiling ---
@@ -184,31 +249,6 @@ drtopk_status check_args(const void* keys, int dtype, int64_t n, int64_t k) {
       goto done;                                 \
     }                                            \
   } while (0)
-
-void bind_work(Work& w, char* ws, const Layout& L, const Plan& P, int64_t n, int64_t k,
-               int dtype) {
-  w.ctl = reinterpret_cast<Ctl*>(ws + L.ctl);
-  w.dkeys = reinterpret_cast<uint32_t*>(ws + L.dkeys);
-  w.dsegs = reinterpret_cast<uint16_t*>(ws + L.dsegs);
-  w.ds = reinterpret_cast<uint32_t*>(ws + L.ds);
-  w.scanq = reinterpret_cast<uint32_t*>(ws + L.scanq);
-  w.rq = reinterpret_cast<uint32_t*>(ws + L.rq);
-  w.rq_cap = rq_capacity(P, k);
-  w.g = reinterpret_cast<uint64_t*>(ws + L.g);
-  w.sv = reinterpret_cast<uint64_t*>(ws + L.sv);
-  w.w = reinterpret_cast<uint64_t*>(ws + L.w);
-  w.w2 = reinterpret_cast<uint64_t*>(ws + L.w2);
-  w.tstat = reinterpret_cast<uint64_t*>(ws + L.tstat);
-  w.sort_status = reinterpret_cast<uint64_t*>(ws + L.sstat);
-  w.n = n;
-  w.S = P.S;
-  w.g_cap = P.g_cap;
-  w.k = k;
-  w.alpha = P.alpha;
-  w.beta = P.beta;
-  w.dtype = dtype;
-  w.ablate = P.ablate;
-}
 
 // Every launch of one query, in order, on stream s (no allocation, no sync).
 cudaError_t enqueue_query(const Work& w, const Plan& P, const void* keys, bool topk,
@@ -332,13 +372,15 @@ void destroy_entry(GraphEntry& e) {
 // Builds an entry (capture + instantiate). Caller holds g_gmu.
 cudaError_t build_entry(GraphEntry& ent, const Plan& P, const Layout& L, const void* keys,
                         int dtype, int64_t n, int64_t k, bool topk, void* out_keys,
-                        int32_t* out_idx, void* out_kth, int sms, int dev) {
+                        int32_t* out_idx, void* out_kth, int sms, int dev, uint32_t* err_out) {
   cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&ent.ws), L.total);
+  note_alloc();
   if (e != cudaSuccess) return e;
   ent.bytes = L.total;
   g_gbytes += L.total;
   Work w;
   bind_work(w, ent.ws, L, P, n, k, dtype);
+  w.err_out = err_out;
   if (!g_capture_stream[dev]) {
     e = cudaStreamCreateWithFlags(&g_capture_stream[dev], cudaStreamNonBlocking);
     if (e != cudaSuccess) return e;
@@ -362,8 +404,8 @@ cudaError_t build_entry(GraphEntry& ent, const Plan& P, const Layout& L, const v
 // Replays (building on a miss) the graph of this query. Returns false when
 // the graph path is not usable; the caller then runs the direct path.
 bool run_graph(const Plan& P, const void* keys, int dtype, int64_t n, int64_t k, bool topk,
-               void* out_keys, int32_t* out_idx, void* out_kth, int sms, cudaStream_t s,
-               drtopk_status* st) {
+               void* out_keys, int32_t* out_idx, void* out_kth, int sms, uint32_t* err_out,
+               cudaStream_t s, drtopk_status* st) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -398,8 +440,8 @@ bool run_graph(const Plan& P, const void* keys, int dtype, int64_t n, int64_t k,
     }
     GraphEntry fresh;
     fresh.key = key;
-    if (build_entry(fresh, P, L, keys, dtype, n, k, topk, out_keys, out_idx, out_kth, sms, dev) !=
-        cudaSuccess) {
+    if (build_entry(fresh, P, L, keys, dtype, n, k, topk, out_keys, out_idx, out_kth, sms, dev,
+                    err_out) != cudaSuccess) {
       cudaGetLastError();
       destroy_entry(fresh);
       return false;
@@ -415,9 +457,15 @@ bool run_graph(const Plan& P, const void* keys, int dtype, int64_t n, int64_t k,
   return true;
 }
 
+// Where a query's device error flags go: the device's report word (read by
+// the next call on the device and by drtopk_sync_status), a caller's word,
+// or nowhere (the call reads them itself).
+enum class Report { kDevice, kCaller, kNone };
+
 drtopk_status run_query(const void* keys, int dtype, int64_t n, int64_t k, int alpha, int beta,
                         void* out_keys, int32_t* out_idx, void* out_kth, drtopk_stats* stats,
-                        cudaStream_t s, bool allow_graph, int ablate = 0) {
+                        cudaStream_t s, bool allow_graph, int ablate = 0,
+                        Report report = Report::kDevice, uint32_t* caller_err = nullptr) {
   drtopk_status st = check_args(keys, dtype, n, k);
   if (st != DRTOPK_OK) return st;
   const bool topk = out_keys != nullptr || out_idx != nullptr;
@@ -427,14 +475,25 @@ drtopk_status run_query(const void* keys, int dtype, int64_t n, int64_t k, int a
   Plan P;
   if (!make_plan(n, k, alpha, beta, &P, ablate)) return DRTOPK_ERR_INVALID;
   int sms = 0;
-  st = dev_info(&sms);
+  DevInfo* dv = nullptr;
+  st = dev_info(&sms, &dv);
   if (st != DRTOPK_OK) return st;
+  if (stats) report = Report::kNone;  // read back below, with the statistics
+  uint32_t* err_out = nullptr;
+  if (report == Report::kDevice) {
+    // an earlier asynchronous call on this device reported a device-side
+    // error: return it now (this call does nothing)
+    if (const uint32_t prev = take_errors(dv)) return error_status(prev);
+    err_out = dv->err_dev;
+  } else if (report == Report::kCaller) {
+    err_out = caller_err;
+  }
   const bool prof = profiling_on();
   if (ablate) allow_graph = false;  // the graph cache keys on the method as stated
 
   // profiled calls run the direct path: its stage events sit between launches
-  if (allow_graph && !stats && !prof && graph_cache_enabled() &&
-      run_graph(P, keys, dtype, n, k, topk, out_keys, out_idx, out_kth, sms, s, &st))
+  if (allow_graph && !stats && !prof && graph_cache_enabled() && report == Report::kDevice &&
+      run_graph(P, keys, dtype, n, k, topk, out_keys, out_idx, out_kth, sms, err_out, s, &st))
     return st;
 
   const Layout L = layout(P, k, topk, false);
@@ -442,10 +501,19 @@ drtopk_status run_query(const void* keys, int dtype, int64_t n, int64_t k, int a
   StageTimer tm(s, prof);
   Work w;
   {
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ws), L.total, s);
+    // the library's own pool; under a caller's stream capture the workspace
+    // becomes a graph allocation node instead
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess) return cuda_status(e);
+    e = (cap == cudaStreamCaptureStatusNone)
+            ? cudaMallocFromPoolAsync(reinterpret_cast<void**>(&ws), L.total, dv->pool, s)
+            : cudaMallocAsync(reinterpret_cast<void**>(&ws), L.total, s);
+    note_alloc();
     if (e != cudaSuccess) return cuda_status(e);
   }
   bind_work(w, ws, L, P, n, k, dtype);
+  w.err_out = err_out;
   DRTOPK_CU(enqueue_query(w, P, keys, topk, out_keys, out_idx, out_kth, sms, s, tm));
   if (stats) {
     Ctl c;
@@ -464,7 +532,7 @@ drtopk_status run_query(const void* keys, int dtype, int64_t n, int64_t k, int a
     stats->survivors = c.stage_count[2];
     stats->emitted = c.w_count;
     stats->error = c.error;
-    if (c.error & kErrTimeout) st = DRTOPK_ERR_TIMEOUT;
+    st = error_status(c.error);
   }
 done:
   {
@@ -477,8 +545,17 @@ done:
 }  // namespace
 
 drtopk_status topk_kernel_by_kernel(const void* keys, int dtype, int64_t n, int64_t k,
-                                    void* out_keys, int32_t* out_idx, cudaStream_t s) {
-  return run_query(keys, dtype, n, k, 0, 0, out_keys, out_idx, nullptr, nullptr, s, false);
+                                    void* out_keys, int32_t* out_idx, uint32_t* err_out,
+                                    cudaStream_t s) {
+  return run_query(keys, dtype, n, k, 0, 0, out_keys, out_idx, nullptr, nullptr, s, false, 0,
+                   Report::kCaller, err_out);
+}
+
+cudaError_t enqueue_query_plain(const Work& w, const Plan& P, const void* keys, bool topk,
+                                void* out_keys, int32_t* out_idx, void* out_kth, int sms,
+                                cudaStream_t s) {
+  StageTimer tm(s, false);
+  return enqueue_query(w, P, keys, topk, out_keys, out_idx, out_kth, sms, s, tm);
 }
 
 }  // namespace drtopk
@@ -498,6 +575,7 @@ const char* drtopk_status_str(drtopk_status s) {
     case DRTOPK_ERR_BUDGET: return "DRTOPK_ERR_BUDGET";
     case DRTOPK_ERR_TIMEOUT: return "DRTOPK_ERR_TIMEOUT";
     case DRTOPK_PENDING: return "DRTOPK_PENDING";
+    case DRTOPK_ERR_INTERNAL: return "DRTOPK_ERR_INTERNAL";
   }
   return "DRTOPK_UNKNOWN_STATUS";
 }
@@ -557,12 +635,19 @@ drtopk_status drtopk_delegates(const void* keys, drtopk_dtype dtype, int64_t n, 
   Plan P;
   if (!make_plan(n, 1, alpha, beta, &P)) return DRTOPK_ERR_INVALID;
   int sms = 0;
-  st = dev_info(&sms);
+  DevInfo* dv = nullptr;
+  st = dev_info(&sms, &dv);
   if (st != DRTOPK_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t bytes = al(sizeof(Ctl)) + al(static_cast<size_t>(P.S) * beta * 2);
   char* ws = nullptr;
-  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ws), bytes, s);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(s, &cap);
+  if (e != cudaSuccess) return cuda_status(e);
+  e = (cap == cudaStreamCaptureStatusNone)
+          ? cudaMallocFromPoolAsync(reinterpret_cast<void**>(&ws), bytes, dv->pool, s)
+          : cudaMallocAsync(reinterpret_cast<void**>(&ws), bytes, s);
+  note_alloc();
   if (e != cudaSuccess) return cuda_status(e);
   Work w;
   std::memset(&w, 0, sizeof(w));
@@ -608,6 +693,7 @@ drtopk_status drtopk_topk_host(const void* keys, drtopk_dtype dtype, int64_t n, 
       if (e != cudaSuccess) return cuda_status(e);
     }
     cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&hs.d), kb + 2 * ob);
+    note_alloc();
     if (e != cudaSuccess) {
       hs.d = nullptr;
       return cuda_status(e);
@@ -629,7 +715,12 @@ drtopk_status drtopk_topk_host(const void* keys, drtopk_dtype dtype, int64_t n, 
   cudaError_t e3 = cudaStreamSynchronize(s);
   if (st != DRTOPK_OK) return st;
   if (e == cudaSuccess) e = e3;
-  return cuda_status(e);
+  if (e != cudaSuccess) return cuda_status(e);
+  // synchronous: the query's device-side errors are reported here
+  int sms = 0;
+  DevInfo* dv = nullptr;
+  if (dev_info(&sms, &dv) != DRTOPK_OK) return DRTOPK_ERR_CUDA;
+  return error_status(take_errors(dv));
 }
 
 drtopk_status drtopk_profile_begin(void) {
@@ -667,5 +758,29 @@ drtopk_status drtopk_profile_end(drtopk_profile* out) {
 }
 
 uint64_t drtopk_launch_count(void) { return g_launches.load(); }
+
+uint64_t drtopk_alloc_count(void) { return g_allocs.load(); }
+
+drtopk_status drtopk_sync_status(void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_status(e);
+  int sms = 0;
+  DevInfo* dv = nullptr;
+  if (dev_info(&sms, &dv) != DRTOPK_OK) return DRTOPK_ERR_CUDA;
+  uint32_t flags = take_errors(dv);
+  flags |= take_noalloc_errors();
+  return error_status(flags);
+}
+
+drtopk_status drtopk_wait_selftest(uint32_t timeout_us, void* stream) {
+  if (timeout_us < 1 || timeout_us > 10000000u) return DRTOPK_ERR_INVALID;
+  int sms = 0;
+  DevInfo* dv = nullptr;
+  drtopk_status st = dev_info(&sms, &dv);
+  if (st != DRTOPK_OK) return st;
+  return cuda_status(launch_wait_selftest(timeout_us, dv->err_dev,
+                                          static_cast<cudaStream_t>(stream)));
+}
 
 }  // extern "C"

@@ -1131,6 +1131,7 @@ drtopk_status drtopk_batch_plan_create(drtopk_dtype dtype, const int64_t* row_of
   pl->scap = std::max<int64_t>(scap, 1);
   pl->alpha = std::move(ra);
   pl->beta = std::move(rb);
+  note_alloc(4);  // rows, control words, phase counters, scratch
   cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&pl->d_rows), rd.size() * sizeof(RowDesc));
   if (e == cudaSuccess)
     e = cudaMemcpy(pl->d_rows, rd.data(), rd.size() * sizeof(RowDesc), cudaMemcpyHostToDevice);
@@ -1271,6 +1272,7 @@ drtopk_status drtopk_autotune_batched(drtopk_dtype dtype, int32_t min_log2n, int
   uint32_t* d_keys = nullptr;
   uint32_t* d_ok = nullptr;
   int32_t* d_oi = nullptr;
+  note_alloc(3);
   if (cudaMalloc(reinterpret_cast<void**>(&d_keys), total * 4) != cudaSuccess) return DRTOPK_ERR_NOMEM;
   if (cudaMalloc(reinterpret_cast<void**>(&d_ok), size_t(kBMaxK) * rows_per_shape * 4) != cudaSuccess ||
       cudaMalloc(reinterpret_cast<void**>(&d_oi), size_t(kBMaxK) * rows_per_shape * 4) != cudaSuccess) {

@@ -12,9 +12,11 @@ namespace drtopk {
 constexpr int kMaxBeta = 4;
 constexpr int kMinAlpha = 2;
 constexpr int kMaxAlpha = 16;
-// Bounded spin: a device-side wait gives up after this many polls and sets
-// kErrTimeout in the control block instead of hanging.
-constexpr uint32_t kSpinLimit = 1u << 24;
+// Bounded waits: an mbarrier wait gives up after kWaitNs nanoseconds of the
+// GPU's global timer (a bulk copy lands in microseconds), a look-back wait
+// after a bounded number of polls; either sets kErrTimeout in the control
+// block instead of hanging.
+constexpr uint64_t kWaitNs = 1000000000ull;  // 1 s
 
 // Device error flags (Ctl::error).
 constexpr uint32_t kErrTimeout = 1u;
@@ -145,7 +147,21 @@ struct Work {
   int beta;
   int dtype;
   int ablate;         // kAblate* flags, 0 for the method as stated
+  uint32_t* err_out;  // device-visible word the query's last kernel ORs its
+                      // error flags into (nullptr: not reported there)
 };
+
+// Called by one thread of the last kernel of a query, after every earlier
+// kernel of the query has finished: ORs the query's device error flags into
+// the caller-visible report word (host-mapped memory or a device word).
+__device__ __forceinline__ void report_errors(const Ctl* ctl, uint32_t* err_out) {
+  const uint32_t e = *reinterpret_cast<const volatile uint32_t*>(&ctl->error);
+  if (e && err_out) {
+    volatile uint32_t* q = err_out;
+    *q = *q | e;
+    __threadfence_system();
+  }
+}
 
 // -------------------------------------------------------- small helpers ---
 __host__ __device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
@@ -182,11 +198,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait on an mbarrier phase: false when kSpinLimit polls passed.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  for (uint32_t it = 0; it < kSpinLimit; ++it)
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait on an mbarrier phase: false once limit_ns nanoseconds passed
+// without the phase completing (the clock is read every 64 polls).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  uint64_t limit_ns = kWaitNs) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 1;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
-  return false;
+    if ((it & 63u) == 0 && global_ns() - t0 > limit_ns) return false;
+  }
 }
 __device__ __forceinline__ uint64_t l2_evict_first_policy() {
   uint64_t pol;

@@ -152,7 +152,15 @@ __global__ void __launch_bounds__(kThreads, 2) delegate_kernel(DelegParams p) {
       issue_chunk<false>(p, c, cb, nullptr, 0);
     }
     if (__syncthreads_or(!ok)) {
-      if (tid == 0) atomicOr(&p.ctl->error, kErrTimeout);
+      if (tid == 0) {
+        atomicOr(&p.ctl->error, kErrTimeout);
+        if constexpr (TMA) {
+          // copies still in flight land in this CTA's shared memory: let
+          // them complete (bounded) before the CTA exits
+          for (int64_t jj = j; jj < j + kStages && chunk_of(p, jj, cps_log) >= 0; ++jj)
+            mbar_wait_bounded(&full_bar[jj % kStages], static_cast<uint32_t>((jj / kStages) & 1));
+        }
+      }
       return;
     }
 

@@ -9,6 +9,40 @@ namespace drtopk {
 
 // Counts every kernel this library launches (drtopk_launch_count).
 void note_launch(int n = 1);
+// Counts every device or pinned-host allocation this library makes
+// (drtopk_alloc_count); called next to each allocating CUDA call.
+void note_alloc(int n = 1);
+
+// ------------------------------------------------------ single queries ---
+// Parameters of one query: alpha (Rule 4 / Eq. 9 unless forced), beta, the
+// subrange count S and the capacity of the candidates above tau.
+struct Plan {
+  int alpha;
+  int beta;
+  int64_t S;
+  int64_t g_cap;
+  bool fuse_hist;  // beta * S >= k: tau from the delegates, else tau = 0
+  int ablate = 0;
+};
+bool make_plan(int64_t n, int64_t k, int alpha, int beta, Plan* p, int ablate = 0);
+
+// Byte offsets of a query's workspace regions (256-byte aligned) and the
+// total. need_topk = false leaves out the regions only top-k uses;
+// external_dkeys leaves out the delegate keys (a caller's buffer).
+struct Layout {
+  size_t ctl, dkeys, dsegs, ds, scanq, rq, g, sv, w, w2, tstat, sstat, total;
+};
+Layout layout(const Plan& p, int64_t k, bool need_topk, bool external_dkeys);
+
+// Points the device views of `w` into the workspace `ws` laid out by L.
+void bind_work(Work& w, char* ws, const Layout& L, const Plan& P, int64_t n, int64_t k,
+               int dtype);
+
+// Every launch of one query, in order, on stream s (no allocation, no
+// host synchronization).
+cudaError_t enqueue_query_plain(const Work& w, const Plan& P, const void* keys, bool topk,
+                                void* out_keys, int32_t* out_idx, void* out_kth, int sms,
+                                cudaStream_t s);
 
 // Delegate pass (delegate.cu). fuse_hist: also histogram the first digit of
 // the threshold select and resolve it in the last block.
@@ -49,9 +83,23 @@ cudaError_t launch_resolve_delegates(const Work& w, const void* keys, int32_t* d
                                      cudaStream_t s);
 
 // drtopk_topk without the graph cache: every kernel launched on `s`
-// (api.cu). For one-off queries, e.g. those of the server.
+// (api.cu). For one-off queries, e.g. those of the server. The query's
+// device error flags are ORed into *err_out (a device-visible word).
 drtopk_status topk_kernel_by_kernel(const void* keys, int dtype, int64_t n, int64_t k,
-                                    void* out_keys, int32_t* out_idx, cudaStream_t s);
+                                    void* out_keys, int32_t* out_idx, uint32_t* err_out,
+                                    cudaStream_t s);
+
+// Status of a set of device error flags (0: DRTOPK_OK).
+drtopk_status error_status(uint32_t flags);
+
+// Takes (reads and clears) the error flags drtopk_kth_noalloc reported on
+// the current device (noalloc.cu); 0 when it never ran there. Synchronous.
+uint32_t take_noalloc_errors();
+
+// One CTA waits, bounded by timeout_us, on an mbarrier phase that nothing
+// completes, and ORs kErrTimeout into *err_out when the wait gives up
+// (select.cu).
+cudaError_t launch_wait_selftest(uint32_t timeout_us, uint32_t* err_out, cudaStream_t s);
 
 // ------------------------------------------------------------- batched ---
 // One row of a batch. Its keys, output keys and output indices sit at the

@@ -1549,12 +1549,31 @@ __global__ void __launch_bounds__(kThreads, 4) tie_place_kernel(TieParams p) {
 }
 
 // ----------------------------------------------------------- k-th output ---
-__global__ void write_kth_kernel(Ctl* ctl, int dtype, uint32_t* out) {
+__global__ void write_kth_kernel(Ctl* ctl, int dtype, uint32_t* out, uint32_t* err_out) {
+  report_errors(ctl, err_out);
   const uint32_t mode = __ldcg(&ctl->mode);
   const uint32_t m = (mode == kModeTies) ? __ldcg(&ctl->tau)
                                          : static_cast<uint32_t>(__ldcg(&ctl->gsel.prefix) >> 32);
   ctl->kth_mapped = m;
   if (out) *out = unmap_key(dtype, m);
+}
+
+// Self-test of the bounded waits: one CTA waits on an mbarrier phase that
+// nothing completes, with the wait the bulk-copy rings use, and reports the
+// timeout through the report word the way a query's last kernel does.
+__global__ void wait_selftest_kernel(uint64_t limit_ns, uint32_t* err_out) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const bool ok = mbar_wait_bounded(&bar, 0, limit_ns);
+  if (!ok && threadIdx.x == 0 && err_out) {
+    volatile uint32_t* q = err_out;
+    *q = *q | kErrTimeout;
+    __threadfence_system();
+  }
 }
 
 // ------------------------------------------------- delegate stage output ---
@@ -1737,7 +1756,13 @@ cudaError_t launch_gselect(const Work& w, bool kth_only, int sms, cudaStream_t s
 }
 
 cudaError_t launch_write_kth(const Work& w, void* out_kth, cudaStream_t s) {
-  write_kth_kernel<<<1, 1, 0, s>>>(w.ctl, w.dtype, static_cast<uint32_t*>(out_kth));
+  write_kth_kernel<<<1, 1, 0, s>>>(w.ctl, w.dtype, static_cast<uint32_t*>(out_kth), w.err_out);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wait_selftest(uint32_t timeout_us, uint32_t* err_out, cudaStream_t s) {
+  wait_selftest_kernel<<<1, 32, 0, s>>>(static_cast<uint64_t>(timeout_us) * 1000ull, err_out);
   note_launch();
   return cudaGetLastError();
 }

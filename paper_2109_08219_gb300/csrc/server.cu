@@ -58,7 +58,48 @@ struct BatchCtx {
 struct Unit {
   cudaEvent_t ev;
   std::vector<uint64_t> tickets;
-  int ctx;  // batch context, or -1 for a single query
+  int ctx;       // batch context, or -1 for a single query
+  int err_slot;  // single query: its report word, or -1
+};
+
+// Report words of single queries in flight: host-mapped pinned words in
+// blocks of 256, recycled as queries retire (scheduler thread only).
+struct ErrSlots {
+  static constexpr int kBlock = 256;
+  std::vector<uint32_t*> host_blocks, dev_blocks;
+  std::vector<int> free_slots;
+  cudaError_t take(int* slot) {
+    if (free_slots.empty()) {
+      uint32_t* h = nullptr;
+      uint32_t* d = nullptr;
+      cudaError_t e = cudaHostAlloc(reinterpret_cast<void**>(&h), kBlock * sizeof(uint32_t),
+                                    cudaHostAllocMapped);
+      note_alloc();
+      if (e != cudaSuccess) return e;
+      e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&d), h, 0);
+      if (e != cudaSuccess) {
+        cudaFreeHost(h);
+        return e;
+      }
+      const int b = static_cast<int>(host_blocks.size());
+      host_blocks.push_back(h);
+      dev_blocks.push_back(d);
+      for (int i = kBlock - 1; i >= 0; --i) free_slots.push_back(b * kBlock + i);
+    }
+    *slot = free_slots.back();
+    free_slots.pop_back();
+    host(*slot) = 0;
+    return cudaSuccess;
+  }
+  uint32_t& host(int slot) { return host_blocks[slot / kBlock][slot % kBlock]; }
+  uint32_t* dev(int slot) { return dev_blocks[slot / kBlock] + slot % kBlock; }
+  void give(int slot) { free_slots.push_back(slot); }
+  void release() {
+    for (uint32_t* h : host_blocks) cudaFreeHost(h);
+    host_blocks.clear();
+    dev_blocks.clear();
+    free_slots.clear();
+  }
 };
 
 size_t single_workspace(int64_t n, int64_t k) {
@@ -105,6 +146,7 @@ struct drtopk_server {
   cudaStream_t qs[kQueryStreams] = {};
   BatchCtx ctx[kBatchCtxs];
   std::vector<Unit> inflight;
+  ErrSlots err_slots;
   std::vector<cudaEvent_t> events;
   std::vector<uint64_t> ready_small;
   int next_qs = 0;
@@ -155,8 +197,13 @@ struct drtopk_server {
       if (q != cudaSuccess) cudaGetLastError();
       if (u.ctx >= 0) {
         const uint32_t e = *ctx[u.ctx].h_err;
-        if (st == DRTOPK_OK && e) st = (e & kErrTimeout) ? DRTOPK_ERR_TIMEOUT : DRTOPK_ERR_CUDA;
+        if (st == DRTOPK_OK && e) st = (e & kErrTimeout) ? DRTOPK_ERR_TIMEOUT : DRTOPK_ERR_INTERNAL;
         ctx[u.ctx].busy = false;
+      }
+      if (u.err_slot >= 0) {
+        const uint32_t e = *reinterpret_cast<volatile uint32_t*>(&err_slots.host(u.err_slot));
+        if (st == DRTOPK_OK) st = error_status(e);
+        err_slots.give(u.err_slot);
       }
       finish(u.tickets, st);
       events.push_back(u.ev);
@@ -169,15 +216,23 @@ struct drtopk_server {
 
   void launch_single(uint64_t t, const Req& r) {
     cudaStream_t s = qs[(flags & DRTOPK_SERVER_PLAIN) ? 0 : (next_qs++ % kQueryStreams)];
-    const drtopk_status st =
-        topk_kernel_by_kernel(r.keys, r.dtype, r.n, r.k, r.out_keys, r.out_idx, s);
+    int slot = -1;
+    if (err_slots.take(&slot) != cudaSuccess) {
+      cudaGetLastError();
+      finish({t}, DRTOPK_ERR_NOMEM);
+      return;
+    }
+    const drtopk_status st = topk_kernel_by_kernel(r.keys, r.dtype, r.n, r.k, r.out_keys,
+                                                   r.out_idx, err_slots.dev(slot), s);
     if (st != DRTOPK_OK) {
+      err_slots.give(slot);
       finish({t}, st);
       return;
     }
     Unit u;
     u.ev = get_event();
     u.ctx = -1;
+    u.err_slot = slot;
     u.tickets.push_back(t);
     if (cudaEventRecord(u.ev, s) != cudaSuccess) {
       cudaGetLastError();
@@ -240,6 +295,7 @@ struct drtopk_server {
     Unit u;
     u.ev = get_event();
     u.ctx = c;
+    u.err_slot = -1;
     u.tickets = take;
     if (e == cudaSuccess) e = cudaEventRecord(u.ev, bc.stream);
     if (e != cudaSuccess) {
@@ -314,6 +370,7 @@ struct drtopk_server {
     }
     for (auto& u : inflight) cudaEventDestroy(u.ev);
     inflight.clear();
+    err_slots.release();
     for (auto e : events) cudaEventDestroy(e);
     events.clear();
   }
@@ -343,6 +400,13 @@ drtopk_status drtopk_server_create_ex(size_t hbm_budget_bytes, int device, int f
     return DRTOPK_ERR_CUDA;
   }
   if (device >= ndev) return DRTOPK_ERR_INVALID;
+  // the set-up below runs on `device`; the caller's current device is
+  // restored before returning
+  int prev_dev = 0;
+  if (cudaGetDevice(&prev_dev) != cudaSuccess) {
+    cudaGetLastError();
+    return DRTOPK_ERR_CUDA;
+  }
   auto* S = new drtopk_server;
   S->device = device;
   S->budget = hbm_budget_bytes;
@@ -357,6 +421,7 @@ drtopk_status drtopk_server_create_ex(size_t hbm_budget_bytes, int device, int f
   for (int i = 0; i < kBatchCtxs && e == cudaSuccess && batching; ++i) {
     BatchCtx& c = S->ctx[i];
     e = cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking);
+    note_alloc(6);  // rows (device and pinned), control words, phases, scratch, error word
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&c.d_rows), kMaxBatchRows * sizeof(RowDesc));
     if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&c.h_rows), kMaxBatchRows * sizeof(RowDesc));
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&c.d_ctl), 2 * sizeof(uint32_t));
@@ -377,11 +442,12 @@ drtopk_status drtopk_server_create_ex(size_t hbm_budget_bytes, int device, int f
     cudaGetLastError();
     S->release();
     delete S;
+    cudaSetDevice(prev_dev);
     return st;
   }
   S->worker = std::thread([S] { S->run(); });
   *out = S;
-  return DRTOPK_OK;
+  return cudaSetDevice(prev_dev) == cudaSuccess ? DRTOPK_OK : DRTOPK_ERR_CUDA;
 }
 
 drtopk_status drtopk_server_create(size_t hbm_budget_bytes, int device, drtopk_server** out) {
@@ -475,9 +541,12 @@ drtopk_status drtopk_server_destroy(drtopk_server* S) {
   }
   S->cv_work.notify_all();
   if (S->worker.joinable()) S->worker.join();
+  int prev_dev = 0;
+  const bool restore = cudaGetDevice(&prev_dev) == cudaSuccess;
   cudaSetDevice(S->device);
   S->release();
   delete S;
+  if (restore) cudaSetDevice(prev_dev);
   return DRTOPK_OK;
 }
 

@@ -58,8 +58,10 @@ __device__ __forceinline__ int64_t sort_count(const Ctl* ctl, int64_t k) {
 
 __global__ void __launch_bounds__(1024) small_sort_kernel(const uint64_t* w, int k, int dtype,
                                                           uint32_t* out_keys, int32_t* out_idx,
-                                                          uint32_t* out_kth, Ctl* ctl) {
+                                                          uint32_t* out_kth, Ctl* ctl,
+                                                          uint32_t* err_out) {
   __shared__ uint64_t s[kSmallSort];
+  if (threadIdx.x == 0) report_errors(ctl, err_out);
   const int m = static_cast<int>(sort_count(ctl, k));
   int P = 1;
   while (P < m) P <<= 1;
@@ -92,6 +94,7 @@ struct SortParams {
   int64_t k;
   int64_t ntiles;
   Ctl* ctl;
+  uint32_t* err_out;
 };
 
 // pass p: digit p (0 = least significant byte) of ~c
@@ -287,6 +290,7 @@ __global__ void __launch_bounds__(kSortThreads, 1) sort_pass_kernel(SortParams p
 
 __global__ void finalize_kernel(SortParams p, int dtype, uint32_t* out_keys, int32_t* out_idx,
                                 uint32_t* out_kth) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) report_errors(p.ctl, p.err_out);
   uint32_t skip[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) skip[q] = __ldcg(&p.ctl->sort_skip[q]);
@@ -313,7 +317,7 @@ cudaError_t launch_sort_output(const Work& w, void* out_keys, int32_t* out_idx, 
   if (w.k <= kSmallSort) {
     small_sort_kernel<<<1, 1024, 0, s>>>(w.w, static_cast<int>(w.k), w.dtype,
                                          static_cast<uint32_t*>(out_keys), out_idx,
-                                         static_cast<uint32_t*>(out_kth), w.ctl);
+                                         static_cast<uint32_t*>(out_kth), w.ctl, w.err_out);
     note_launch();
     return cudaGetLastError();
   }
@@ -324,6 +328,7 @@ cudaError_t launch_sort_output(const Work& w, void* out_keys, int32_t* out_idx, 
   p.k = w.k;
   p.ntiles = (w.k + kTile - 1) / kTile;
   p.ctl = w.ctl;
+  p.err_out = w.err_out;
   cudaError_t e = cudaMemsetAsync(p.status, 0, sort_status_words(w.k) * 8, s);
   if (e != cudaSuccess) return e;
   const int gh = static_cast<int>(std::min<int64_t>((w.k + kHistThreads * 16 - 1) / (kHistThreads * 16),

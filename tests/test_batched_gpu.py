@@ -284,6 +284,13 @@ def test_batched_plan_graph_replay_and_device_row_arrays():
     assert torch.equal(oi2, oi)
 
 
+def ordered(f):
+    """float32 tensor -> int64 keys in the library's total order (-0.0 below
+    +0.0), computed from the bits with plain torch integer ops."""
+    b = f.view(torch.int32).to(torch.int64) & 0xFFFFFFFF
+    return torch.where(b >= (1 << 31), 0xFFFFFFFF - b, b + (1 << 31))
+
+
 def test_batched_full_ragged_workload():
     """4096 float32 rows, lengths round(2^U[10, 22]), k_r uniform in
     [1, min(1024, n_r)], keys N(0, 1): the oracle on 160 rows (the 32 longest
@@ -297,7 +304,7 @@ def test_batched_full_ragged_workload():
     ok, oi = plan.run(x)
     plan.status()
     # every row: indices in range, keys read back at them, sorted by
-    # (key desc, index asc), and no key above the k-th key left out
+    # (key desc, index asc)
     out_off = torch.from_numpy(plan.out_off).cuda()
     row_of = torch.repeat_interleave(torch.arange(4096, device="cuda"),
                                      torch.from_numpy(ks.astype(np.int64)).cuda())
@@ -311,6 +318,33 @@ def test_batched_full_ragged_workload():
     assert bool((~same_row | (kd <= 0)).all())
     tie = same_row & (ok[1:] == ok[:-1])
     assert bool((~tie | (idx[1:] > idx[:-1])).all())
+    # completeness, row by row: with kth_r the row's last output key, the
+    # row holds exactly as many keys above kth_r as were returned above it,
+    # and its keys equal to kth_r at indices up to the largest returned tie
+    # index are exactly the returned ties (so the smallest indices won)
+    ks_t = torch.from_numpy(ks.astype(np.int64)).cuda()
+    last = out_off[1:] - 1
+    kth_m = ordered(ok)[last]
+    tmax = idx[last]
+    out_gt = torch.zeros(4096, dtype=torch.int64, device="cuda")
+    out_gt.scatter_add_(0, row_of, (ordered(ok) > kth_m[row_of]).to(torch.int64))
+    in_gt = torch.zeros_like(out_gt)
+    in_eq = torch.zeros_like(out_gt)
+    r0 = 0
+    while r0 < 4096:  # chunks of rows, about 2^26 keys each
+        r1 = r0 + 1
+        while r1 < 4096 and row_off[r1 + 1] - row_off[r0] <= (1 << 26):
+            r1 += 1
+        a, b = int(row_off[r0]), int(row_off[r1])
+        seg = torch.repeat_interleave(torch.arange(r0, r1, device="cuda"),
+                                      torch.from_numpy(np.diff(row_off[r0:r1 + 1])).cuda())
+        m = ordered(x[a:b])
+        pos = torch.arange(a, b, device="cuda") - torch.from_numpy(row_off).cuda()[seg]
+        in_gt.scatter_add_(0, seg, (m > kth_m[seg]).to(torch.int64))
+        in_eq.scatter_add_(0, seg, ((m == kth_m[seg]) & (pos <= tmax[seg])).to(torch.int64))
+        r0 = r1
+    assert torch.equal(in_gt, out_gt)
+    assert torch.equal(in_eq, ks_t - out_gt)
     del out_off
     bits = None
     order = np.argsort(-np.array(lens))
@@ -327,3 +361,50 @@ def test_batched_full_ragged_workload():
     plan.close()
     del x, bits
     torch.cuda.empty_cache()
+
+
+def test_autotuned_table_stays_exact():
+    """drtopk_autotune_batched measures (alpha, beta) per (log2 n, log2 k)
+    bucket and fills the tuning table; plans built from that table must give
+    the oracle's answer row by row. The table is restored afterwards."""
+    lo, hi = 12, 16
+    saved = {(ln, lk): drtopk.tune_get(ln, lk) for ln in range(lo, hi + 1) for lk in range(13)}
+    try:
+        drtopk.autotune_batched("f32", lo, hi, rows_per_shape=8)
+        tuned = {key: drtopk.tune_get(*key) for key in saved}
+        # every bucket the tuner covers (n > 4096, 2^lk <= min(4096, n / 2)) holds
+        # a valid choice: the direct select or alpha in [5, 16] with beta in [1, 4]
+        for (ln, lk), (a, b) in tuned.items():
+            if ln > 12 and (1 << lk) <= min(4096, (1 << ln) // 2):
+                assert a == 1 or (5 <= a <= 16 and 1 <= b <= 4), (ln, lk, a, b)
+        rng = np.random.default_rng(23)
+        lens, ks = [], []
+        for ln in range(13, hi + 1):
+            for lk in range(0, 13):
+                if (1 << lk) > min(4096, (1 << ln) // 2):
+                    continue
+                for _ in range(2):
+                    n = int(rng.integers(1 << ln, 1 << (ln + 1)))
+                    lens.append(n)
+                    ks.append(int(min(n, 4096, rng.integers(1 << lk, 1 << (lk + 1)))))
+        row_off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+        for kind in ("normal", "few"):
+            bits = np.concatenate([row_bits(kind, n, rng, "f32") for n in lens])
+            x = torch.from_numpy(bits.view(np.float32)).cuda()
+            plan = drtopk.BatchPlan(row_off, ks, "f32")
+            pa, pb = plan.params()
+            used = {(int(a), int(b)) for a, b in zip(pa, pb)}
+            ok, oi = plan.run(x)
+            plan.status()
+            gk, gi = host_bits(ok), oi.cpu().numpy()
+            for r, n in enumerate(lens):
+                a, b = int(row_off[r]), int(row_off[r + 1])
+                rk, ri = oracle.topk(bits[a:b], oracle.F32, ks[r])
+                o0 = int(plan.out_off[r])
+                assert np.array_equal(gk[o0:o0 + ks[r]], rk), (kind, r, n, ks[r], pa[r], pb[r])
+                assert np.array_equal(gi[o0:o0 + ks[r]], ri), (kind, r, n, ks[r], pa[r], pb[r])
+            plan.close()
+            assert len(used) > 1, used  # the table steered rows to different parameters
+    finally:
+        for (ln, lk), (a, b) in saved.items():
+            drtopk.tune_set(ln, lk, a, b)
