@@ -44,6 +44,10 @@ def _load():
         lib.oracle_candidates.restype = i64
         lib.oracle_drtopk.argtypes = [i32, p, i64, i64, i32, i32, p, p, p]
         lib.oracle_alpha_rule4.argtypes = [i64, i64, ctypes.c_double]
+        lib.oracle_bottomk.argtypes = [i32, p, i64, i64, p, p]
+        lib.oracle_kth_smallest.argtypes = [i32, p, i64, i64, p]
+        lib.oracle_topk_merge.argtypes = [i32, p, p, i64, i64, i32, p, p]
+        lib.oracle_topk_omp.argtypes = [i32, p, i64, i64, i32, p, p, p]
         _lib = lib
     return _lib
 
@@ -102,6 +106,55 @@ def kth(bits, dtype, k):
     if rc != 0:
         raise ValueError("oracle_kth rc=%d" % rc)
     return int(out[0])
+
+
+def bottomk(bits, dtype, k):
+    """Plain smallest-k (Sec. 1, Sec. 2): (key bits, int32 indices), sorted
+    (key asc, idx asc)."""
+    bits = np.ascontiguousarray(bits, dtype=np.uint32)
+    ok = np.empty(k, np.uint32)
+    oi = np.empty(k, np.int32)
+    rc = _load().oracle_bottomk(dtype, _ptr(bits), bits.size, k, _ptr(ok), _ptr(oi))
+    if rc != 0:
+        raise ValueError("oracle_bottomk rc=%d" % rc)
+    return ok, oi
+
+
+def kth_smallest(bits, dtype, k):
+    """Raw bits of the k-th smallest key."""
+    bits = np.ascontiguousarray(bits, dtype=np.uint32)
+    out = np.zeros(1, np.uint32)
+    rc = _load().oracle_kth_smallest(dtype, _ptr(bits), bits.size, k, _ptr(out))
+    if rc != 0:
+        raise ValueError("oracle_kth_smallest rc=%d" % rc)
+    return int(out[0])
+
+
+def topk_merge(bits, gidx, dtype, k, smallest=False):
+    """Distributed form's final step (Sec. 4.4): top-k of (key bits, int64
+    global index) pairs in any order -> (key bits, int64 global indices)."""
+    bits = np.ascontiguousarray(bits, dtype=np.uint32)
+    gidx = np.ascontiguousarray(gidx, dtype=np.int64)
+    ok = np.empty(k, np.uint32)
+    og = np.empty(k, np.int64)
+    rc = _load().oracle_topk_merge(dtype, _ptr(bits), _ptr(gidx), bits.size, k,
+                                   1 if smallest else 0, _ptr(ok), _ptr(og))
+    if rc != 0:
+        raise ValueError("oracle_topk_merge rc=%d" % rc)
+    return ok, og
+
+
+def topk_omp(bits, dtype, k, threads=0):
+    """Multi-core chunked top-k (same result as topk): (keys, idx, threads used)."""
+    bits = np.ascontiguousarray(bits, dtype=np.uint32)
+    ok = np.empty(k, np.uint32)
+    oi = np.empty(k, np.int32)
+    used = np.zeros(1, np.int32)
+    rc = _load().oracle_topk_omp(dtype, _ptr(bits), bits.size, k, threads, _ptr(ok),
+                                 _ptr(oi), _ptr(used))
+    if rc != 0:
+        raise ValueError("oracle_topk_omp rc=%d" % rc)
+    return ok, oi, int(used[0])
 
 
 def delegates(mapped, alpha, beta):

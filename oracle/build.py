@@ -1,8 +1,9 @@
 """Build the CPU oracle shared library (test infrastructure only).
 
 Compiles ``drtopk_oracle.cpp`` with the host C++ compiler into
-``oracle/_build/liboracle.so``. Plain portable C++17: no architecture flags,
-so the same source builds on x86_64 and aarch64.
+``oracle/_build/liboracle.so``. Plain portable C++17 with OpenMP (used only
+by the chunked multi-core variant): no architecture flags, so the same
+source builds on x86_64 and aarch64.
 """
 
 import os
@@ -21,7 +22,7 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(LIB) >= os.path.getmtime(SRC)):
         return LIB
     tmp = LIB + ".tmp.%d" % os.getpid()
-    cmd = ["g++", "-std=c++17", "-O2", "-fPIC", "-shared", SRC, "-o", tmp]
+    cmd = ["g++", "-std=c++17", "-O2", "-fPIC", "-fopenmp", "-shared", SRC, "-o", tmp]
     subprocess.check_call(cmd)
     os.replace(tmp, LIB)
     return LIB

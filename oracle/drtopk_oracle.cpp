@@ -29,6 +29,14 @@
 //     first top-k, concatenation, second top-k; Eq. 1).
 //   * oracle_alpha_rule4 : Rule 4 / Eq. 9 with const = 3 and floor rounding
 //     (Sec. 4.2; the paper's worked value alpha(2^30, 2^24) = 4).
+//   * oracle_bottomk / oracle_kth_smallest : the other criterion of the
+//     problem statement (Sec. 1, Sec. 2: "the k largest or smallest"): the k
+//     smallest elements ordered by (key asc, idx asc), and the k-th smallest.
+//   * oracle_topk_merge : the distributed form's final step (Sec. 4.4): the
+//     plain top-k of a set of (key, global index) pairs, whatever their order.
+//   * oracle_topk_omp : the same result as oracle_topk computed by chunks on
+//     several threads (each thread's local top-k, then the top-k of their
+//     union); only the timed multi-core CPU baseline uses it.
 //
 // Library primitives used as single steps: std::nth_element (selection) and
 // std::sort / std::stable_sort.
@@ -38,6 +46,10 @@
 #include <cstdint>
 #include <cstring>
 #include <vector>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 namespace {
 
@@ -69,6 +81,12 @@ struct Pair {
 // The total order of the problem statement: larger key first, then smaller index.
 bool before(const Pair& a, const Pair& b) {
   if (a.key != b.key) return a.key > b.key;
+  return a.idx < b.idx;
+}
+
+// The smallest criterion: smaller key first, then smaller index.
+bool before_smallest(const Pair& a, const Pair& b) {
+  if (a.key != b.key) return a.key < b.key;
   return a.idx < b.idx;
 }
 
@@ -120,6 +138,96 @@ int oracle_kth(int dtype, const uint32_t* keys, int64_t n, int64_t k,
   std::nth_element(m.begin(), m.begin() + (k - 1), m.end(),
                    [](uint32_t a, uint32_t b) { return a > b; });
   *out_kth = unmap_key(dtype, m[k - 1]);
+  return 0;
+}
+
+// Plain definition of the smallest criterion (Sec. 1, Sec. 2): order all
+// positions by (key asc, idx asc) and return the first k, in that order.
+int oracle_bottomk(int dtype, const uint32_t* keys, int64_t n, int64_t k,
+                   uint32_t* out_keys, int32_t* out_idx) {
+  if (!valid_dtype(dtype)) return 3;
+  if (k < 1 || k > n) return 2;
+  std::vector<Pair> p(static_cast<size_t>(n));
+  for (int64_t i = 0; i < n; ++i) p[i] = Pair{map_key(dtype, keys[i]), i};
+  std::nth_element(p.begin(), p.begin() + (k - 1), p.end(), before_smallest);
+  std::sort(p.begin(), p.begin() + k, before_smallest);
+  for (int64_t j = 0; j < k; ++j) {
+    out_keys[j] = unmap_key(dtype, p[j].key);
+    out_idx[j] = static_cast<int32_t>(p[j].idx);
+  }
+  return 0;
+}
+
+// The k-th smallest key (original bits).
+int oracle_kth_smallest(int dtype, const uint32_t* keys, int64_t n, int64_t k,
+                        uint32_t* out_kth) {
+  if (!valid_dtype(dtype)) return 3;
+  if (k < 1 || k > n) return 2;
+  std::vector<uint32_t> m(static_cast<size_t>(n));
+  for (int64_t i = 0; i < n; ++i) m[i] = map_key(dtype, keys[i]);
+  std::nth_element(m.begin(), m.begin() + (k - 1), m.end());
+  *out_kth = unmap_key(dtype, m[k - 1]);
+  return 0;
+}
+
+// Final step of the distributed form (Sec. 4.4): the top-k of m pairs
+// (key bits, int64 global index) in any order, by (key desc, idx asc), or
+// by (key asc, idx asc) when smallest != 0.
+int oracle_topk_merge(int dtype, const uint32_t* keys, const int64_t* gidx, int64_t m,
+                      int64_t k, int smallest, uint32_t* out_keys, int64_t* out_gidx) {
+  if (!valid_dtype(dtype)) return 3;
+  if (k < 1 || k > m) return 2;
+  std::vector<Pair> p(static_cast<size_t>(m));
+  for (int64_t i = 0; i < m; ++i) p[i] = Pair{map_key(dtype, keys[i]), gidx[i]};
+  auto order = smallest ? before_smallest : before;
+  std::nth_element(p.begin(), p.begin() + (k - 1), p.end(), order);
+  std::sort(p.begin(), p.begin() + k, order);
+  for (int64_t j = 0; j < k; ++j) {
+    out_keys[j] = unmap_key(dtype, p[j].key);
+    out_gidx[j] = p[j].idx;
+  }
+  return 0;
+}
+
+// Multi-core variant of oracle_topk, for the timed CPU baseline only: the
+// positions are split into one contiguous chunk per thread; each thread
+// keeps its chunk's top-min(k, chunk) by nth_element; the union of these
+// holds the answer (an element of the top-k is in its own chunk's top-k),
+// and one nth_element + sort over the union gives it. threads <= 0: all
+// available. *used receives the thread count.
+int oracle_topk_omp(int dtype, const uint32_t* keys, int64_t n, int64_t k, int threads,
+                    uint32_t* out_keys, int32_t* out_idx, int* used) {
+  if (!valid_dtype(dtype)) return 3;
+  if (k < 1 || k > n) return 2;
+  int T = 1;
+#ifdef _OPENMP
+  T = threads > 0 ? threads : omp_get_max_threads();
+#endif
+  if (T < 1) T = 1;
+  if (used) *used = T;
+  std::vector<std::vector<Pair>> local(static_cast<size_t>(T));
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(T) schedule(static, 1)
+#endif
+  for (int t = 0; t < T; ++t) {
+    const int64_t lo = n * t / T, hi = n * (t + 1) / T;
+    std::vector<Pair>& p = local[static_cast<size_t>(t)];
+    p.resize(static_cast<size_t>(hi - lo));
+    for (int64_t i = lo; i < hi; ++i) p[i - lo] = Pair{map_key(dtype, keys[i]), i};
+    const int64_t kk = std::min<int64_t>(k, hi - lo);
+    if (kk > 0 && kk < hi - lo) {
+      std::nth_element(p.begin(), p.begin() + (kk - 1), p.end(), before);
+      p.resize(static_cast<size_t>(kk));
+    }
+  }
+  std::vector<Pair> u;
+  for (auto& p : local) u.insert(u.end(), p.begin(), p.end());
+  std::nth_element(u.begin(), u.begin() + (k - 1), u.end(), before);
+  std::sort(u.begin(), u.begin() + k, before);
+  for (int64_t j = 0; j < k; ++j) {
+    out_keys[j] = unmap_key(dtype, u[j].key);
+    out_idx[j] = static_cast<int32_t>(u[j].idx);
+  }
   return 0;
 }
 

@@ -372,3 +372,113 @@ def test_batched_recipe():
     mean = sum(lens) / len(lens)
     # E[2^U[10,22]] = (2^22 - 2^10) / (12 ln 2) ~ 5.04e5
     assert 4.0e5 < mean < 6.2e5
+
+
+# ------------------------------------------- smallest criterion, merge, omp ---
+
+def brute_order_smallest(x):
+    """Positions sorted by (value asc, index asc); -0.0 ranks below +0.0."""
+    vals = x.tolist()
+    if x.dtype == np.float32:
+        def key(i):
+            v = vals[i]
+            poszero = 1 if (v == 0.0 and math.copysign(1.0, v) > 0) else 0
+            return (v, poszero, i)
+    else:
+        def key(i):
+            return (int(vals[i]), 0, i)
+    return sorted(range(len(vals)), key=key)
+
+
+@pytest.mark.parametrize("dtype", [np.uint32, np.int32, np.float32])
+def test_bottomk_matches_brute_force_every_k(dtype):
+    rng = _rng(61)
+    for n in (1, 2, 3, 9, 40):
+        for kind in ("few", "equal", "asc", "desc", "rand"):
+            x = small_input(rng, n, kind, dtype)
+            bits, dt = oracle.as_bits(x)
+            order = brute_order_smallest(x)
+            for k in range(1, n + 1):
+                ok, oi = oracle.bottomk(bits, dt, k)
+                assert oi.tolist() == order[:k], (n, kind, k)
+                assert same_bits(ok, bits[order[:k]])
+                assert oracle.kth_smallest(bits, dt, k) == int(bits[order[k - 1]])
+
+
+def test_bottomk_special_cases():
+    n = 50
+    asc = np.arange(n, dtype=np.uint32) * 3
+    ok, oi = oracle.bottomk(asc, oracle.U32, 7)
+    assert oi.tolist() == list(range(7))
+    ok, oi = oracle.bottomk(asc[::-1].copy(), oracle.U32, 7)
+    assert oi.tolist() == list(range(n - 1, n - 8, -1))
+    ok, oi = oracle.bottomk(np.full(n, 5, np.uint32), oracle.U32, 9)
+    assert oi.tolist() == list(range(9))
+    # k = 1 is the minimum at its first index
+    x = np.array([4, 1, 9, 1, 0, 0, 3], np.uint32)
+    ok, oi = oracle.bottomk(x, oracle.U32, 1)
+    assert ok.tolist() == [0] and oi.tolist() == [4]
+
+
+def test_bottomk_values_against_torch_on_distinct_keys():
+    x = np.random.default_rng(62).permutation(5000).astype(np.int32) - 2500
+    bits, dt = oracle.as_bits(x)
+    for k in (1, 10, 999):
+        ok, _ = oracle.bottomk(bits, dt, k)
+        ref = torch.topk(torch.from_numpy(x.astype(np.int64)), k, largest=False).values
+        assert oracle.from_bits(ok, dt).astype(np.int64).tolist() == sorted(ref.tolist())
+
+
+def test_topk_merge_matches_brute_force():
+    rng = _rng(63)
+    for smallest in (False, True):
+        for m in (1, 5, 60):
+            keys = rng.integers(0, 4, m).astype(np.uint32)
+            gidx = rng.permutation(10 * m)[:m].astype(np.int64)
+            sign = 1 if smallest else -1
+            order = sorted(range(m), key=lambda i: (sign * int(keys[i]), int(gidx[i])))
+            for k in range(1, m + 1):
+                ok, og = oracle.topk_merge(keys, gidx, oracle.U32, k, smallest)
+                assert og.tolist() == [int(gidx[i]) for i in order[:k]], (m, k, smallest)
+                assert ok.tolist() == [int(keys[i]) for i in order[:k]]
+
+
+@pytest.mark.parametrize("smallest", [False, True])
+def test_shard_topk_union_holds_the_answer(smallest):
+    """The distributed form (Sec. 4.4): the top-k of the union of every
+    shard's top-k equals the top-k of the whole vector, ties included."""
+    rng = _rng(64)
+    pick = oracle.bottomk if smallest else oracle.topk
+    for kind in ("few", "rand"):
+        n = 3001
+        bits = (rng.integers(0, 6, n) if kind == "few"
+                else rng.integers(0, 2**32, n, dtype=np.uint64)).astype(np.uint32)
+        cuts = [0, 1, 700, 701, 1500, 3001]
+        for k in (1, 5, 400, 1000):
+            ck, cg = [], []
+            for a, b in zip(cuts[:-1], cuts[1:]):
+                kk = min(k, b - a)
+                lk, li = pick(bits[a:b], oracle.U32, kk)
+                ck.append(lk)
+                cg.append(li.astype(np.int64) + a)
+            ok, og = oracle.topk_merge(np.concatenate(ck), np.concatenate(cg), oracle.U32, k,
+                                       smallest)
+            rk, ri = pick(bits, oracle.U32, k)
+            assert np.array_equal(ok, rk) and np.array_equal(og, ri.astype(np.int64)), (kind, k)
+
+
+def test_topk_omp_equals_single_thread():
+    rng = _rng(65)
+    for n, kind in ((1, "rand"), (7, "few"), (1000, "few"), (100003, "rand"), (50000, "equal")):
+        if kind == "few":
+            bits = rng.integers(0, 3, n).astype(np.uint32)
+        elif kind == "equal":
+            bits = np.full(n, 9, np.uint32)
+        else:
+            bits = rng.integers(0, 2**32, n, dtype=np.uint64).astype(np.uint32)
+        for threads in (1, 3, 8):
+            for k in sorted({1, min(n, 5), max(1, n // 3), n}):
+                rk, ri = oracle.topk(bits, oracle.U32, k)
+                ok, oi, used = oracle.topk_omp(bits, oracle.U32, k, threads)
+                assert used == threads
+                assert np.array_equal(ok, rk) and np.array_equal(oi, ri), (n, kind, threads, k)
