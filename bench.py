@@ -32,9 +32,13 @@ Extra measurements in the same line:
                 (64 GB HBM budget) and through its plain mode (one launch
                 sequence per request, one stream): throughput, p50 / p99 latency.
 
---impl reference times the CPU oracle instead (rank 0 only).
-Multi-GPU (torchrun): every rank runs the same workload on its own GPU
-(independent replicas, weak scaling); value sums all ranks over the max time.
+--impl reference times the CPU oracle instead (the chunked multi-core
+variant on all host cores, rank 0 only).
+Multi-GPU (torchrun): the distributed form of Sec. 4.4. Rank r holds the r-th
+2^log2n-key sub-vector of each query's vector; per query every rank computes
+its local top-k, the lists are all-gathered (NCCL) and rank 0 computes the
+exact final top-k with drtopk_topk_merge. Weak scaling: value = keys of all
+ranks over the slowest rank's time.
 """
 
 import argparse
@@ -54,10 +58,12 @@ DISTS = ["ascending", "descending", "all_equal", "distinct16", "zipf"]
 KS = [1024, 1 << 20]
 SEED = 3
 PAPER_UD_MS = 6.4  # Dr. Top-k radix, |V| = 2^30 UD, k = 1024, V100S (Sec. 5.1)
-# DRAM bytes (read + write) per key of one delegate-pass launch, from the ncu
-# capture in profiles/delegate_kernel_zipf_u32_2p27_k1024.md (scaled by keys).
-# Must be re-measured (or set to None) whenever the delegate kernel changes.
-DELEG_DRAM_BYTES_PER_KEY = (536.93e6 + 3.38e6) / (1 << 27)
+# DRAM bytes (read + write) per key of one delegate-pass launch, by alpha
+# (the subrange size sets the delegate writes), from one ncu capture per
+# alpha of the delegate kernel at n = 2^28 (scaled by keys to a launch).
+# None where no capture of the current kernel exists; must be re-measured
+# (or set to None) whenever the delegate kernel changes.
+DELEG_DRAM_BYTES_PER_KEY = {11: None, 6: None}
 
 
 def parse():
@@ -175,6 +181,11 @@ def max_over_ranks(v, world):
     return float(t.item())
 
 
+def shard_seed(rank):
+    """Seed of rank r's sub-vector (rank 0: the one-GPU workload's seed)."""
+    return SEED + 1000 * rank
+
+
 def aggregate_value(n, queries, steps, world, ms_max):
     """Whole-job Gkeys/s: keys of all ranks over the slowest rank's time."""
     return float(n) * queries * steps * world / (ms_max * 1e-3) / 1e9
@@ -205,6 +216,73 @@ def oracle_sample(dists, ks, sample_log2, reps=1, data=None):
     return keys, t
 
 
+def oracle_sample_omp(dists, ks, data, reps=1):
+    """The chunked multi-core oracle (all host cores) on the same samples."""
+    import oracle
+    keys, t, used = 0, 0.0, 1
+    first = next(iter(data.values()))
+    oracle.topk_omp(first[:4096], oracle.U32, 1)  # start the thread pool
+    for _ in range(reps):
+        for d in dists:
+            for k in ks:
+                x = data[d]
+                t0 = time.perf_counter()
+                _, _, used = oracle.topk_omp(x, oracle.U32, min(k, x.size))
+                t += time.perf_counter() - t0
+                keys += x.size
+    return keys, t, used
+
+
+def cpu_model():
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for ln in r.stdout.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return None
+
+
+def e2e_sharded(drtopk, shard, x_dev, ks, n, world, rank, dev, args):
+    """End to end on several ranks through the public API: every step copies
+    each rank's sub-vector from pinned host memory to its GPU, runs the
+    sharded top-k (local drtopk_select, all-gather, drtopk_topk_merge on
+    rank 0) and reads the merged result back to the host on rank 0. One
+    distribution (the first), every k; max over ranks."""
+    import torch
+    host = torch.empty(n, dtype=torch.int32, pin_memory=True)
+    host.copy_(x_dev)
+    dbuf = torch.empty(n, dtype=torch.int32, device=dev)
+    outs_h = {k: (torch.empty(k, dtype=torch.int32, pin_memory=True),
+                  torch.empty(k, dtype=torch.int64, pin_memory=True)) for k in ks}
+
+    def estep():
+        for k in ks:
+            dbuf.copy_(host, non_blocking=True)
+            r = shard.shard_topk(dbuf, k, dtype="u32")
+            if r is not None:
+                outs_h[k][0].copy_(r[0], non_blocking=True)
+                outs_h[k][1].copy_(r[1], non_blocking=True)
+        torch.cuda.synchronize()
+
+    estep()
+    esteps = max(2, min(args.steps, 5))
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(esteps):
+        estep()
+    et = max_over_ranks(time.perf_counter() - t0, world)
+    del dbuf, host
+    torch.cuda.empty_cache()
+    return {"value": float(n) * world * len(ks) * esteps / et / 1e9, "unit": "Gkeys/s",
+            "h2d_bytes_per_step": 4 * n * world * len(ks),
+            "d2h_bytes_per_step": 12 * sum(ks), "steps": esteps,
+            "api": "per rank: pinned H2D copy of the sub-vector, drtopk_select, all-gather, "
+                   "drtopk_topk_merge on rank 0, D2H of the merged keys and int64 indices",
+            "workload": "first distribution only, every k"}
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -216,11 +294,12 @@ def run_reference(args, world, rank):
     m = 1 << sample_log2
     data = {d: inputs.DISTRIBUTIONS[d](m, SEED).numpy().view(np.uint32) for d in dists}
     for _ in range(args.warmup):
-        oracle_sample(dists, ks, sample_log2, data=data)
-    keys, t = oracle_sample(dists, ks, sample_log2, reps=args.steps, data=data)
+        oracle_sample_omp(dists, ks, data)
+    keys, t, used = oracle_sample_omp(dists, ks, data, reps=args.steps)
     gk = keys / t / 1e9
-    sample = ("first 2^%d keys of each of the %d (distribution, k) queries, %d steps"
-              % (sample_log2, len(dists) * len(ks), args.steps))
+    sample = ("first 2^%d keys of each of the %d (distribution, k) queries, %d steps; chunked "
+              "oracle (per-thread nth_element, then the union), %d threads"
+              % (sample_log2, len(dists) * len(ks), args.steps, used))
     out = {
         "impl": "reference",
         "metric": "top-k throughput (n=2^%d u32, adversarial distributions)" % args.log2n,
@@ -228,21 +307,29 @@ def run_reference(args, world, rank):
         "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic",
-        "config": workload_config(args, dists, ks),
-        "cpu_baseline": {"value": gk, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
-                         "sample": sample},
+        "config": workload_config(args, dists, ks, world),
+        "cpu_baseline": {"value": gk, "unit": "Gkeys/s", "cores": used, "kind": "oracle",
+                         "sample": sample, "cpu_model": cpu_model()},
         "e2e": {"value": gk, "unit": "Gkeys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))
 
 
-def workload_config(args, dists, ks):
-    return {"workload": "top-k, n=2^%d uint32 keys, distributions %s, k in %s, 1 query per "
-                        "(distribution, k) per step" % (args.log2n, "/".join(dists),
-                                                       "/".join(str(k) for k in ks)),
-            "n": 1 << args.log2n, "k": ks, "distributions": dists, "seed": SEED,
-            "queries_per_step": len(dists) * len(ks),
-            "l2": "inputs larger than L2 (%d MiB each); no flush" % ((4 << args.log2n) >> 20)}
+def workload_config(args, dists, ks, world=1):
+    cfg = {"workload": "top-k, n=2^%d uint32 keys, distributions %s, k in %s, 1 query per "
+                       "(distribution, k) per step" % (args.log2n, "/".join(dists),
+                                                      "/".join(str(k) for k in ks)),
+           "n": 1 << args.log2n, "k": ks, "distributions": dists, "seed": SEED,
+           "queries_per_step": len(dists) * len(ks),
+           "l2": "inputs larger than L2 (%d MiB each); no flush" % ((4 << args.log2n) >> 20),
+           "parallelism": "single GPU"}
+    if world > 1:
+        cfg["parallelism"] = ("shard + gather over %d GPUs (Sec. 4.4): rank r holds the r-th "
+                              "sub-vector (2^%d keys, seed %d + 1000 r) of a %d x 2^%d-key "
+                              "vector; per query a local top-k, one all-gather of the k-entry "
+                              "lists and the exact merge on rank 0"
+                              % (world, args.log2n, SEED, world, args.log2n))
+    return cfg
 
 
 # ----------------------------------------------------------------- main ----
@@ -386,18 +473,43 @@ def ablations_measure(drtopk, inputs, dev, reps=3):
     variants = [("method", {}), ("beta1_rules_1_2", {"beta": 1}),
                 ("rule2_filter_off", {"no_filter": True}),
                 ("first_select_skips_last_digit", {"skip_last_digit": True})]
+    s = torch.cuda.Stream(dev)
     for name, x in (("UD", ud), ("ND", nd)):
         for k in (1024, 1 << 20):
+            ok = torch.empty(k, dtype=torch.int32, device=dev)
+            oi = torch.empty(k, dtype=torch.int32, device=dev)
             for vname, kw in variants:
-                ms, r = timed(lambda: drtopk.drtopk_topk_ablate(x, k, dtype="u32", **kw))
-                st = r[2]
+                # every variant the same way: its launches captured in one CUDA
+                # graph and replayed; statistics read by a separate call
+                def call():
+                    drtopk.drtopk_topk_ablate(x, k, dtype="u32", stats=False, out_keys=ok,
+                                              out_idx=oi, stream=s, **kw)
+                with torch.cuda.stream(s):
+                    call()
+                s.synchronize()
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=s):
+                    call()
+                with torch.cuda.stream(s):
+                    g.replay()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(s)
+                    for _ in range(reps):
+                        g.replay()
+                    e1.record(s)
+                s.synchronize()
+                ms = e0.elapsed_time(e1) / reps
+                del g
+                st = drtopk.drtopk_topk_ablate(x, k, dtype="u32", **kw)[2]
                 cand = st["greater"] + st["ties_needed"]
                 out["ablations"].append({
                     "input": name, "k": k, "variant": vname, "ms": ms,
                     "alpha": st["alpha"], "beta": st["beta"], "tau": st["tau"],
                     "candidate_fraction": cand / x.numel(),
-                    "scanned_subranges": st["scanned"], "note": "each call synchronizes "
-                    "(statistics read back); times include that"})
+                    "scanned_subranges": st["scanned"]})
+    out["ablations_timing"] = ("each variant's call captured in one CUDA graph and replayed "
+                               "(mean of %d replays); statistics read outside the timed loop" % reps)
     del ud, nd
     torch.cuda.empty_cache()
     return out
@@ -484,6 +596,7 @@ def main():
     import paper_2109_08219_gb300 as drtopk
     from paper_2109_08219_gb300 import build as libbuild
     from paper_2109_08219_gb300 import inputs
+    from paper_2109_08219_gb300 import shard
 
     libbuild.build()
     dev = torch.device("cuda", local if world > 1 else torch.cuda.current_device())
@@ -491,7 +604,9 @@ def main():
     dists = args.dists.split(",")
     ks = [int(x) for x in args.ks.split(",")]
     n = 1 << args.log2n
-    xs = {d: inputs.DISTRIBUTIONS[d](n, SEED, device=dev) for d in dists}
+    # one GPU: the whole vector of each query; several (torchrun): rank r
+    # holds the r-th contiguous sub-vector of a vector of world * n keys
+    xs = {d: inputs.DISTRIBUTIONS[d](n, shard_seed(rank), device=dev) for d in dists}
     outs = {k: (torch.empty(k, dtype=torch.int32, device=dev),
                 torch.empty(k, dtype=torch.int32, device=dev)) for k in ks}
     torch.cuda.synchronize()
@@ -500,8 +615,12 @@ def main():
     def step():
         for d in dists:
             for k in ks:
-                drtopk.drtopk_topk(xs[d], k, out_keys=outs[k][0], out_idx=outs[k][1],
-                                   dtype="u32", stream=stream)
+                if world == 1:
+                    drtopk.drtopk_topk(xs[d], k, out_keys=outs[k][0], out_idx=outs[k][1],
+                                       dtype="u32", stream=stream)
+                else:
+                    # Sec. 4.4: local top-k, all-gather of the lists, merge on rank 0
+                    shard.shard_topk(xs[d], k, dtype="u32", stream=stream)
 
     for _ in range(args.warmup):
         step()
@@ -546,6 +665,9 @@ def main():
     queries = len(dists) * len(ks)
     value = aggregate_value(n, queries, args.steps, world, ms_max)
 
+    e2e_dist = None
+    if world > 1 and not args.no_e2e:
+        e2e_dist = e2e_sharded(drtopk, shard, xs[dists[0]], ks, n, world, rank, dev, args)
     if rank != 0:
         return
 
@@ -561,11 +683,20 @@ def main():
         peak = 6800.0
     dms, dl = prof["delegate"]
     achieved = (4.0 * n) / ((dms / max(dl, 1)) * 1e-3) / 1e9 if dl else None
-    traffic = DELEG_DRAM_BYTES_PER_KEY * n if DELEG_DRAM_BYTES_PER_KEY else None
+    # DRAM traffic of the timed delegate launches: each query's alpha (Rule 4
+    # at its k) picks the measured bytes per key; the launch-weighted mean
+    alphas = [drtopk.drtopk_plan(n, k)[0] for d in dists for k in ks]
+    by_alpha = {a: (DELEG_DRAM_BYTES_PER_KEY.get(a) or 0) * n or None for a in sorted(set(alphas))}
+    traffic = (sum(by_alpha[a] for a in alphas) / len(alphas)
+               if all(by_alpha[a] for a in alphas) else None)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum at n=2^27, "
-                                  "scaled by keys to one launch",
+                "traffic_by_alpha": {str(a): v for a, v in by_alpha.items()},
+                "traffic_ratio_to_4n_by_alpha": {str(a): (v / (4.0 * n) if v else None)
+                                                 for a, v in by_alpha.items()},
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the "
+                                  "delegate kernel at n=2^28 per alpha, scaled by keys to one "
+                                  "launch; launch-weighted mean over the timed queries",
                 "kernel": "delegate_kernel (TMA-streamed delegate pass)",
                 "algorithmic_bytes_per_launch": 4 * n, "launches": dl,
                 "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs, copy burst)" % peak_src,
@@ -578,7 +709,7 @@ def main():
         "value": value, "unit": "Gkeys/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": workload_config(args, dists, ks),
+        "config": workload_config(args, dists, ks, world),
         "roofline": roofline,
         "gpu_launches": launches,
         "stage_ms_per_query": stage_ms,
@@ -646,14 +777,20 @@ def main():
         m = 1 << sample_log2
         data = {d: xs[d][:m].cpu().numpy().view(np.uint32) for d in dists}
         keys, t = oracle_sample(dists, ks, sample_log2, data=data)
-        out["cpu_baseline"] = {"value": keys / t / 1e9, "unit": "Gkeys/s", "cores": 1,
-                               "kind": "oracle",
-                               "sample": "first 2^%d keys of each of the %d (distribution, k) "
-                                         "queries, once (std::nth_element + sort, 1 thread)"
-                                         % (sample_log2, queries)}
+        mkeys, mt, used = oracle_sample_omp(dists, ks, data)
+        out["cpu_baseline"] = {
+            "value": mkeys / mt / 1e9, "unit": "Gkeys/s", "cores": used, "kind": "oracle",
+            "sample": "first 2^%d keys of each of the %d (distribution, k) queries, once "
+                      "(chunked oracle: per-thread nth_element, then nth_element + sort of "
+                      "the union, %d threads)" % (sample_log2, queries, used),
+            "cpu_model": cpu_model(), "host_cores": os.cpu_count(),
+            "single_thread": {"value": keys / t / 1e9, "unit": "Gkeys/s", "cores": 1,
+                              "sample": "same keys, std::nth_element + sort, 1 thread"}}
 
+    if e2e_dist is not None:
+        out["e2e"] = e2e_dist
     # end to end through the host entry point
-    if not args.no_e2e:
+    if not args.no_e2e and world == 1:
         hosts = {}
         for d in dists:
             h = torch.empty(n, dtype=torch.int32, pin_memory=True)

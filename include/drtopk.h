@@ -143,6 +143,54 @@ drtopk_status drtopk_topk(const void* keys, drtopk_dtype dtype, int64_t n,
                           int64_t k, void* out_keys, int32_t* out_idx,
                           void* stream);
 
+/* Criterion flag of drtopk_select and drtopk_topk_merge. */
+#define DRTOPK_SMALLEST 1
+
+/*
+ * Top-k and / or k-selection by either criterion of the problem statement
+ * (Sec. 1 and Sec. 2: "the k largest or smallest"; the paper describes the
+ * largest). flags = 0: the k largest keys, sorted by (key descending, index
+ * ascending), and the k-th largest: the results of drtopk_topk /
+ * drtopk_kth. flags = DRTOPK_SMALLEST: the k smallest keys, sorted by (key
+ * ascending, index ascending), and the k-th smallest; among equal keys the
+ * smallest indices win. Same method: the smallest criterion complements
+ * the order-mapped key, so delegates, threshold and filter keep the k
+ * smallest. Give out_keys and out_idx (top-k), out_kth (k-selection), or
+ * all three. keys, outputs: device pointers. Graph-cached like
+ * drtopk_topk.
+ */
+drtopk_status drtopk_select(const void* keys, drtopk_dtype dtype, int64_t n,
+                            int64_t k, int flags, void* out_keys,
+                            int32_t* out_idx, void* out_kth, void* stream);
+
+/*
+ * Exchange step of the distributed form (Sec. 4.4, "Distributed Dr. Top-k":
+ * each GPU computes the top-k of its own contiguous sub-vector, the lists
+ * are gathered on the primary GPU, which computes the final top-k). Given
+ * `parts` lists concatenated in keys / idx, list p at positions
+ * [part_off[p], part_off[p+1]) holding the result of drtopk_select (same
+ * flags) on a sub-vector whose position i has global index
+ * part_base[p] + i, writes the final top-k: out_keys[0..k) (dtype) and
+ * out_gidx[0..k) (int64 global indices), sorted and tie-broken as
+ * drtopk_select does over the whole vector. Requirements (not checked):
+ * each list is sorted as drtopk_select returns it, and the lists appear in
+ * increasing order of disjoint global index ranges (part_base[p] + its
+ * largest index < part_base[p+1]). Then among equal keys the order of
+ * positions is the order of global indices, and the single-query path over
+ * the concatenation is the exact merge; a list shorter than k (a
+ * sub-vector with fewer than k keys) is allowed. The union holds the
+ * answer: an element of the global top-k is in its own sub-vector's
+ * top-k. part_off, part_base: HOST arrays (parts + 1 and parts entries,
+ * 1 <= parts <= 256, part_off nondecreasing, part_off[0] >= 0);
+ * keys, idx (int32, as drtopk_select writes them), out_keys, out_gidx:
+ * device pointers. 1 <= k <= part_off[parts] - part_off[0] <= 2^31 - 1.
+ */
+drtopk_status drtopk_topk_merge(const void* keys, const int32_t* idx,
+                                drtopk_dtype dtype, const int64_t* part_off,
+                                const int64_t* part_base, int32_t parts,
+                                int64_t k, int flags, void* out_keys,
+                                int64_t* out_gidx, void* stream);
+
 /* Per-query statistics of the delegate-centric path (Sec. 5.2 workload
  * statistics: delegate and concatenated vector sizes). */
 typedef struct {

@@ -90,6 +90,9 @@ def lib():
         L.drtopk_topk_host.argtypes = [p, i32, i64, i64, p, p, p]
         L.drtopk_kth_noalloc.argtypes = [p, i32, i64, i64, p, p]
         L.drtopk_kth_noalloc.restype = i32
+        L.drtopk_select.argtypes = [p, i32, i64, i64, i32, p, p, p, p]
+        L.drtopk_topk_merge.argtypes = [p, p, i32, ctypes.POINTER(ctypes.c_int64),
+                                        ctypes.POINTER(ctypes.c_int64), i32, i64, i32, p, p, p]
         L.drtopk_sync_status.argtypes = [p]
         L.drtopk_wait_selftest.argtypes = [ctypes.c_uint32, p]
         L.drtopk_profile_begin.argtypes = []
@@ -121,7 +124,7 @@ def lib():
         L.drtopk_tune_get.argtypes = [i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
         L.drtopk_tune_set.argtypes = [i32, i32, i32, i32]
         L.drtopk_autotune_batched.argtypes = [i32, i32, i32, i32, p]
-        for fn in ("drtopk_sync_status", "drtopk_wait_selftest", "drtopk_plan", "drtopk_kth", "drtopk_topk", "drtopk_topk_ex", "drtopk_topk_ablate",
+        for fn in ("drtopk_select", "drtopk_topk_merge", "drtopk_sync_status", "drtopk_wait_selftest", "drtopk_plan", "drtopk_kth", "drtopk_topk", "drtopk_topk_ex", "drtopk_topk_ablate",
                    "drtopk_delegates", "drtopk_topk_host", "drtopk_profile_begin",
                    "drtopk_profile_end", "drtopk_batch_plan_create", "drtopk_batch_plan_run",
                    "drtopk_batch_plan_status", "drtopk_batch_plan_params",
@@ -237,6 +240,57 @@ def drtopk_topk(keys, k, out_keys=None, out_idx=None, dtype=None, stream=None):
     return out_keys, out_idx
 
 
+SMALLEST = 1
+
+
+def drtopk_select(keys, k, smallest=False, want_topk=True, want_kth=False, dtype=None,
+                  stream=None):
+    """Top-k and / or k-th of a 1-D CUDA tensor by the largest (default) or
+    smallest criterion (drtopk_select). Returns (keys, int32 indices, kth),
+    None for what was not asked; sorted by (key desc or asc, index asc)."""
+    import torch
+    code = _dtype_code(keys, dtype)
+    ok = oi = ot = None
+    if want_topk:
+        ok = torch.empty(k, dtype=keys.dtype, device=keys.device)
+        oi = torch.empty(k, dtype=torch.int32, device=keys.device)
+    if want_kth:
+        ot = torch.empty(1, dtype=keys.dtype, device=keys.device)
+    _check(lib().drtopk_select(_dev(keys), code, keys.numel(), k, SMALLEST if smallest else 0,
+                               _dev(ok) if ok is not None else None,
+                               _dev(oi) if oi is not None else None,
+                               _dev(ot) if ot is not None else None, _stream(stream)),
+           "drtopk_select")
+    return ok, oi, ot
+
+
+def drtopk_topk_merge(keys, idx, part_off, part_base, k, smallest=False, dtype=None,
+                      stream=None):
+    """Final top-k of gathered per-shard lists (drtopk_topk_merge): keys /
+    idx are the concatenated results of drtopk_select on each shard (in
+    shard order), part_off the list boundaries (parts + 1) and part_base
+    each shard's global index base. Returns (keys, int64 global indices)."""
+    import numpy as np
+    import torch
+    code = _dtype_code(keys, dtype)
+    off = np.ascontiguousarray(np.asarray(part_off, dtype=np.int64))
+    base = np.ascontiguousarray(np.asarray(part_base, dtype=np.int64))
+    if off.size != base.size + 1:
+        raise ValueError("part_off needs parts + 1 entries and part_base parts entries")
+    if idx.dtype != torch.int32:
+        raise ValueError("idx must be int32")
+    if keys.numel() < int(off[-1]) or idx.numel() < int(off[-1]):
+        raise ValueError("keys / idx shorter than part_off[-1]")
+    ok = torch.empty(k, dtype=keys.dtype, device=keys.device)
+    og = torch.empty(k, dtype=torch.int64, device=keys.device)
+    _check(lib().drtopk_topk_merge(_dev(keys), _dev(idx), code,
+                                   off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                   base.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                   int(base.size), k, SMALLEST if smallest else 0, _dev(ok),
+                                   _dev(og), _stream(stream)), "drtopk_topk_merge")
+    return ok, og
+
+
 def drtopk_topk_ex(keys, k, alpha=0, beta=0, want_topk=True, want_kth=True, dtype=None,
                    stats=True, stream=None):
     """Extended query with forced alpha/beta and statistics.
@@ -266,20 +320,25 @@ ABLATE_SKIP_LAST_DIGIT = 2
 
 
 def drtopk_topk_ablate(keys, k, alpha=0, beta=0, no_filter=False, skip_last_digit=False,
-                       dtype=None, stream=None):
+                       dtype=None, stats=True, out_keys=None, out_idx=None, stream=None):
     """Top-k with an ablation of the method (drtopk_topk_ablate): Rule 2's
     filtering off and/or the first select stopped one digit early. Returns
-    (out_keys, out_idx, stats dict); synchronizes the stream."""
+    (out_keys, out_idx, stats dict or None); with stats=True the call
+    synchronizes the stream, without it the call is asynchronous (and may
+    be captured in a CUDA graph)."""
     import torch
     code = _dtype_code(keys, dtype)
-    out_keys = torch.empty(k, dtype=keys.dtype, device=keys.device)
-    out_idx = torch.empty(k, dtype=torch.int32, device=keys.device)
-    st = Stats()
+    if out_keys is None:
+        out_keys = torch.empty(k, dtype=keys.dtype, device=keys.device)
+    if out_idx is None:
+        out_idx = torch.empty(k, dtype=torch.int32, device=keys.device)
+    st = Stats() if stats else None
     flags = (ABLATE_NO_FILTER if no_filter else 0) | (ABLATE_SKIP_LAST_DIGIT if skip_last_digit else 0)
     _check(lib().drtopk_topk_ablate(_dev(keys), code, keys.numel(), k, alpha, beta, flags,
-                                    _dev(out_keys), _dev(out_idx), ctypes.byref(st),
+                                    _dev(out_keys), _dev(out_idx),
+                                    ctypes.byref(st) if st is not None else None,
                                     _stream(stream)), "drtopk_topk_ablate")
-    return out_keys, out_idx, st.as_dict()
+    return out_keys, out_idx, (st.as_dict() if st is not None else None)
 
 
 def drtopk_delegates(keys, alpha, beta, dtype=None, stream=None):

@@ -233,8 +233,10 @@ drtopk_status cuda_status(cudaError_t e) {
   return DRTOPK_ERR_CUDA;
 }
 
+// dtype: a drtopk_dtype, optionally with kSmallest (the smallest-k criterion)
 drtopk_status check_args(const void* keys, int dtype, int64_t n, int64_t k) {
-  if (dtype != DRTOPK_U32 && dtype != DRTOPK_I32 && dtype != DRTOPK_F32) return DRTOPK_ERR_DTYPE;
+  const int b = dtype & ~kSmallest;
+  if (b != DRTOPK_U32 && b != DRTOPK_I32 && b != DRTOPK_F32) return DRTOPK_ERR_DTYPE;
   if (n < 1 || n > 0x7FFFFFFFLL) return DRTOPK_ERR_INVALID;
   if (k < 1 || k > n) return DRTOPK_ERR_K;
   if (!keys || (reinterpret_cast<uintptr_t>(keys) & 3u)) return DRTOPK_ERR_INVALID;
@@ -612,6 +614,67 @@ drtopk_status drtopk_topk_ex(const void* keys, drtopk_dtype dtype, int64_t n, in
   if (alpha < 0 || beta < 0) return DRTOPK_ERR_INVALID;
   return run_query(keys, dtype, n, k, alpha, beta, out_keys, out_idx, out_kth, stats,
                    static_cast<cudaStream_t>(stream), true);
+}
+
+drtopk_status drtopk_select(const void* keys, drtopk_dtype dtype, int64_t n, int64_t k,
+                            int flags, void* out_keys, int32_t* out_idx, void* out_kth,
+                            void* stream) {
+  if ((out_keys == nullptr) != (out_idx == nullptr)) return DRTOPK_ERR_INVALID;
+  if (!out_keys && !out_kth) return DRTOPK_ERR_INVALID;
+  if (flags & ~DRTOPK_SMALLEST) return DRTOPK_ERR_INVALID;
+  if (dtype != DRTOPK_U32 && dtype != DRTOPK_I32 && dtype != DRTOPK_F32) return DRTOPK_ERR_DTYPE;
+  const int dt = static_cast<int>(dtype) | ((flags & DRTOPK_SMALLEST) ? kSmallest : 0);
+  return run_query(keys, dt, n, k, 0, 0, out_keys, out_idx, out_kth, nullptr,
+                   static_cast<cudaStream_t>(stream), true);
+}
+
+drtopk_status drtopk_topk_merge(const void* keys, const int32_t* idx, drtopk_dtype dtype,
+                                const int64_t* part_off, const int64_t* part_base,
+                                int32_t parts, int64_t k, int flags, void* out_keys,
+                                int64_t* out_gidx, void* stream) {
+  if (!keys || !idx || !part_off || !part_base || !out_keys || !out_gidx)
+    return DRTOPK_ERR_INVALID;
+  if (parts < 1 || parts > kMaxMergeParts || (flags & ~DRTOPK_SMALLEST)) return DRTOPK_ERR_INVALID;
+  if (dtype != DRTOPK_U32 && dtype != DRTOPK_I32 && dtype != DRTOPK_F32) return DRTOPK_ERR_DTYPE;
+  if (part_off[0] < 0) return DRTOPK_ERR_INVALID;
+  MergeParts mp;
+  mp.parts = parts;
+  for (int p = 0; p < parts; ++p) {
+    if (part_off[p + 1] < part_off[p] || part_base[p] < 0) return DRTOPK_ERR_INVALID;
+    mp.off[p] = part_off[p] - part_off[0];
+    mp.base[p] = part_base[p];
+  }
+  const int64_t m = part_off[parts] - part_off[0];
+  if (m < 1 || m > 0x7FFFFFFFLL) return DRTOPK_ERR_INVALID;
+  if (k < 1 || k > m) return DRTOPK_ERR_K;
+  const int dt = static_cast<int>(dtype) | ((flags & DRTOPK_SMALLEST) ? kSmallest : 0);
+  const char* kbase = static_cast<const char*>(keys) + part_off[0] * 4;
+  const int32_t* ibase = idx + part_off[0];
+  int sms = 0;
+  DevInfo* dv = nullptr;
+  drtopk_status st = dev_info(&sms, &dv);
+  if (st != DRTOPK_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // positions of the winners in the concatenated lists (stream-ordered)
+  int32_t* pos = nullptr;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(s, &cap);
+  if (e != cudaSuccess) return cuda_status(e);
+  const size_t pb = static_cast<size_t>(k) * 4;
+  e = (cap == cudaStreamCaptureStatusNone)
+          ? cudaMallocFromPoolAsync(reinterpret_cast<void**>(&pos), pb, dv->pool, s)
+          : cudaMallocAsync(reinterpret_cast<void**>(&pos), pb, s);
+  note_alloc();
+  if (e != cudaSuccess) return cuda_status(e);
+  // The lists are sorted as drtopk_select returns them and concatenated in
+  // increasing order of their global index ranges, so among equal keys the
+  // position order is the global index order: the single-query path over
+  // the concatenation (ties to the smallest position) is the exact merge.
+  st = run_query(kbase, dt, m, k, 0, 0, out_keys, pos, nullptr, nullptr, s, true);
+  if (st == DRTOPK_OK) st = cuda_status(launch_merge_gather(mp, pos, ibase, k, out_gidx, sms, s));
+  const cudaError_t e2 = cudaFreeAsync(pos, s);
+  if (st == DRTOPK_OK && e2 != cudaSuccess) st = cuda_status(e2);
+  return st;
 }
 
 drtopk_status drtopk_topk_ablate(const void* keys, drtopk_dtype dtype, int64_t n, int64_t k,

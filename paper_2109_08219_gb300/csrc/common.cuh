@@ -32,20 +32,34 @@ constexpr uint32_t kModeTies = 1;    // |{x > tau}| < k: k-th key is tau
 // Order-preserving map of a raw 32-bit key to u32 (unsigned order == key
 // order). u32: identity. i32: flip the sign bit. f32: negative floats flip
 // all bits, non-negative floats set the sign bit.
+//
+// Internal key types: the dtype (DRTOPK_U32 / I32 / F32) plus kSmallest for
+// the smallest-k criterion (Sec. 1 and Sec. 2 name "largest or smallest"):
+// the mapped key is complemented, so the k largest mapped keys are the k
+// smallest keys, and the tie rule (smallest index first) is unchanged.
+constexpr int kSmallest = 4;
+__host__ __device__ constexpr int base_dtype(int dt) { return dt & 3; }
+
 template <int DT>
 __device__ __forceinline__ uint32_t map_key(uint32_t b) {
-  if constexpr (DT == DRTOPK_U32) {
-    return b;
-  } else if constexpr (DT == DRTOPK_I32) {
-    return b ^ 0x80000000u;
+  constexpr int B = DT & 3;
+  uint32_t m;
+  if constexpr (B == DRTOPK_U32) {
+    m = b;
+  } else if constexpr (B == DRTOPK_I32) {
+    m = b ^ 0x80000000u;
   } else {
-    return b ^ (static_cast<uint32_t>(static_cast<int32_t>(b) >> 31) | 0x80000000u);
+    m = b ^ (static_cast<uint32_t>(static_cast<int32_t>(b) >> 31) | 0x80000000u);
   }
+  if constexpr ((DT & kSmallest) != 0) m = ~m;
+  return m;
 }
 
 __host__ __device__ __forceinline__ uint32_t unmap_key(int dt, uint32_t m) {
-  if (dt == DRTOPK_U32) return m;
-  if (dt == DRTOPK_I32) return m ^ 0x80000000u;
+  if (dt & kSmallest) m = ~m;
+  const int b = dt & 3;
+  if (b == DRTOPK_U32) return m;
+  if (b == DRTOPK_I32) return m ^ 0x80000000u;
   return (m & 0x80000000u) ? (m & 0x7FFFFFFFu) : ~m;
 }
 

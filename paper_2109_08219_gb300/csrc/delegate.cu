@@ -350,6 +350,9 @@ cudaError_t launch_delegates(const Work& w, const void* keys, bool fuse_hist, in
     case DRTOPK_U32: return launch_deleg_b<DRTOPK_U32>(p, w.beta, tma, sms, s);
     case DRTOPK_I32: return launch_deleg_b<DRTOPK_I32>(p, w.beta, tma, sms, s);
     case DRTOPK_F32: return launch_deleg_b<DRTOPK_F32>(p, w.beta, tma, sms, s);
+    case DRTOPK_U32 | kSmallest: return launch_deleg_b<DRTOPK_U32 | kSmallest>(p, w.beta, tma, sms, s);
+    case DRTOPK_I32 | kSmallest: return launch_deleg_b<DRTOPK_I32 | kSmallest>(p, w.beta, tma, sms, s);
+    case DRTOPK_F32 | kSmallest: return launch_deleg_b<DRTOPK_F32 | kSmallest>(p, w.beta, tma, sms, s);
   }
   return cudaErrorInvalidValue;
 }

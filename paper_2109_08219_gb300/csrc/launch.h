@@ -101,6 +101,19 @@ uint32_t take_noalloc_errors();
 // (select.cu).
 cudaError_t launch_wait_selftest(uint32_t timeout_us, uint32_t* err_out, cudaStream_t s);
 
+// ---------------------------------------------------------------- merge ---
+// Parts of a merge (drtopk_topk_merge), passed by value: part p occupies
+// positions [off[p], off[p+1]) of the concatenated lists (off[0] = 0) and
+// its local index i is the global index base[p] + i.
+constexpr int kMaxMergeParts = 256;
+struct MergeParts {
+  int64_t off[kMaxMergeParts];
+  int64_t base[kMaxMergeParts];
+  int parts;
+};
+cudaError_t launch_merge_gather(const MergeParts& mp, const int32_t* pos, const int32_t* idx,
+                                int64_t k, int64_t* out_gidx, int sms, cudaStream_t s);
+
 // ------------------------------------------------------------- batched ---
 // One row of a batch. Its keys, output keys and output indices sit at the
 // byte offsets keys / out_keys / out_idx from the launch's three base

@@ -1661,7 +1661,11 @@ cudaError_t launch_filter(const Work& w, const void* keys, bool kth_only, int sm
   switch (w.dtype) {
     case DRTOPK_U32: DRTOPK_FILTER_CASE(DRTOPK_U32); break;
     case DRTOPK_I32: DRTOPK_FILTER_CASE(DRTOPK_I32); break;
-    default: DRTOPK_FILTER_CASE(DRTOPK_F32); break;
+    case DRTOPK_F32: DRTOPK_FILTER_CASE(DRTOPK_F32); break;
+    case DRTOPK_U32 | kSmallest: DRTOPK_FILTER_CASE(DRTOPK_U32 | kSmallest); break;
+    case DRTOPK_I32 | kSmallest: DRTOPK_FILTER_CASE(DRTOPK_I32 | kSmallest); break;
+    case DRTOPK_F32 | kSmallest: DRTOPK_FILTER_CASE(DRTOPK_F32 | kSmallest); break;
+    default: return cudaErrorInvalidValue;
   }
 #undef DRTOPK_FILTER_CASE
   note_launch(3);
@@ -1726,7 +1730,11 @@ cudaError_t launch_ties(const Work& w, const void* keys, int sms, cudaStream_t s
   switch (w.dtype) {
     case DRTOPK_U32: DRTOPK_TIE_BETA(DRTOPK_U32); break;
     case DRTOPK_I32: DRTOPK_TIE_BETA(DRTOPK_I32); break;
-    default: DRTOPK_TIE_BETA(DRTOPK_F32); break;
+    case DRTOPK_F32: DRTOPK_TIE_BETA(DRTOPK_F32); break;
+    case DRTOPK_U32 | kSmallest: DRTOPK_TIE_BETA(DRTOPK_U32 | kSmallest); break;
+    case DRTOPK_I32 | kSmallest: DRTOPK_TIE_BETA(DRTOPK_I32 | kSmallest); break;
+    case DRTOPK_F32 | kSmallest: DRTOPK_TIE_BETA(DRTOPK_F32 | kSmallest); break;
+    default: return cudaErrorInvalidValue;
   }
 #undef DRTOPK_TIE_BETA
 #undef DRTOPK_TIE_CASE
