@@ -128,7 +128,33 @@ struct Ctl {
   uint32_t tie_nlist;        // tiles listed for the tie emission
   uint32_t tie_dense;        // the listed tiles are read whole (bulk copies)
   uint32_t g_total;          // |G| = |{x > tau}| at the mode decision
+  uint32_t key_max;          // largest mapped key of V (from the delegate pass)
+  uint32_t g_lvl0;           // first composite digit of G that can vary
+  // two-pass filter scan of large scan sets: counting pass, then a cut key
+  uint32_t two_pass;         // the scan set was counted first
+  uint32_t scan_total;       // scanned keys > tau (counting pass)
+  uint32_t g_all;            // |{x > tau}| when counted first
+  uint32_t cut_key;          // the writing pass keeps keys >= cut_key (and > tau)
+  uint32_t cnt_ticket;
+  uint32_t scan_ticket;
+  uint32_t fhist[2048];      // keys > tau by their 11 bits below the common prefix
 };
+
+// First digit level (byte of the (key, ~idx) composite, 0 = top) that can
+// differ between the composites of G: G's keys lie in (tau, key_max] (in
+// [0, key_max] when Rule 2's filtering is off), so the leading bytes that
+// the interval's ends share are the same for all of them; 4 when the key
+// itself is fixed. The second select starts at this digit.
+__device__ __forceinline__ int g_first_level(const Ctl* ctl, bool no_filter) {
+  const uint32_t hi = *reinterpret_cast<const volatile uint32_t*>(&ctl->key_max);
+  const uint32_t tau = *reinterpret_cast<const volatile uint32_t*>(&ctl->tau);
+  const uint32_t lo = (no_filter || tau == 0xFFFFFFFFu) ? 0u : tau + 1;
+  const uint32_t x = lo ^ hi;
+  return x == 0 ? 4 : (__clz(x) >> 3);
+}
+__device__ __forceinline__ uint32_t comp_digit(uint64_t c, int level) {
+  return static_cast<uint32_t>(c >> (56 - 8 * level)) & 255u;
+}
 
 // Ablations of the method (drtopk_topk_ablate): Rule 2's filtering off
 // (every subrange whose maximum delegate reaches tau is concatenated whole),

@@ -51,8 +51,10 @@ struct DelegParams {
 
 template <int B>
 __device__ __forceinline__ void write_delegates(const DelegParams& p, int64_t sub,
-                                                const uint64_t* c, uint32_t* sh_hist) {
-  // c: descending composites (B entries)
+                                                const uint64_t* c, uint32_t* sh_hist,
+                                                uint32_t& kmax) {
+  // c: descending composites (B entries); kmax: running maximum key
+  kmax = max(kmax, dc_key(c[0]));
 #pragma unroll
   for (int j = 0; j < B; ++j) {
     const uint32_t key = dc_key(c[j]);
@@ -135,6 +137,7 @@ __global__ void __launch_bounds__(kThreads, 2) delegate_kernel(DelegParams p) {
     }
   }
 
+  uint32_t kmax = 0;  // largest delegate key this thread wrote
   // running list across chunks (alpha > 13)
   uint64_t run[P];
 #pragma unroll
@@ -199,7 +202,7 @@ __global__ void __launch_bounds__(kThreads, 2) delegate_kernel(DelegParams p) {
         uint64_t cc[B];
 #pragma unroll
         for (int i = 0; i < B; ++i) cc[i] = (i < r) ? make_dc(m[i], 0) : 0;
-        write_delegates<B>(p, sub, cc, sh_hist);
+        write_delegates<B>(p, sub, cc, sh_hist, kmax);
       }
     } else {
       // value-only top-B of the thread's 32-key segment
@@ -232,7 +235,7 @@ __global__ void __launch_bounds__(kThreads, 2) delegate_kernel(DelegParams p) {
         const int wl = g_log < 5 ? g_log : 5;
         for (int l = 0; l < wl; ++l) shfl_merge<P>(a, 1 << l);
         if (g_log <= 5) {
-          if ((lane & ((1 << g_log) - 1)) == 0 && sub < p.S) write_delegates<B>(p, sub, a, sh_hist);
+          if ((lane & ((1 << g_log) - 1)) == 0 && sub < p.S) write_delegates<B>(p, sub, a, sh_hist, kmax);
         } else {
           // 2^(g_log-5) warps per subrange: merge their lists in shared memory
           if (lane == 0) {
@@ -249,7 +252,7 @@ __global__ void __launch_bounds__(kThreads, 2) delegate_kernel(DelegParams p) {
             for (int i = 0; i < P; ++i) b[i] = sh_lists[src][i];
             for (int l = 0; l < wps_log; ++l) shfl_merge<P>(b, 1 << l);
             const int64_t sub2 = (cstart >> alpha) + warp;
-            if (lane == 0 && sub2 < p.S) write_delegates<B>(p, sub2, b, sh_hist);
+            if (lane == 0 && sub2 < p.S) write_delegates<B>(p, sub2, b, sh_hist, kmax);
           }
         }
       } else {
@@ -269,7 +272,7 @@ __global__ void __launch_bounds__(kThreads, 2) delegate_kernel(DelegParams p) {
 #pragma unroll
             for (int i = 0; i < P; ++i) b[i] = sh_lists[lane & 7][i];
             for (int l = 0; l < 3; ++l) shfl_merge<P>(b, 1 << l);
-            if (lane == 0) write_delegates<B>(p, c >> cps_log, b, sh_hist);
+            if (lane == 0) write_delegates<B>(p, c >> cps_log, b, sh_hist, kmax);
           }
 #pragma unroll
           for (int i = 0; i < P; ++i) run[i] = 0;
@@ -285,6 +288,11 @@ __global__ void __launch_bounds__(kThreads, 2) delegate_kernel(DelegParams p) {
     }
   }
 
+  {
+    // the largest key of V is the largest delegate
+    const uint32_t wm = __reduce_max_sync(0xFFFFFFFFu, kmax);
+    if (lane == 0 && wm) atomicMax(&p.ctl->key_max, wm);
+  }
   if (p.fuse_hist) {
     __syncthreads();
     for (int i = tid; i < 256; i += kThreads) {

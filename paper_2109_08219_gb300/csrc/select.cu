@@ -393,6 +393,59 @@ __global__ void __launch_bounds__(kThreads) filter_classify_kernel(FilterParams 
   if ((threadIdx.x & 31) == 0 && nscan) atomicAdd(&p.ctl->scanned, nscan);
 }
 
+// Fine digit of the keys above tau for the counting pass of large scan
+// sets: the 11 bits just below the bits that every key in (tau, key_max]
+// shares. cut(b) = the smallest key whose fine digit is b.
+constexpr int kFineBins = 2048;
+struct FineGeom {
+  uint32_t sh;    // digit = (key >> sh) & (kFineBins - 1)
+  uint32_t pref;  // the shared leading bits
+};
+__device__ __forceinline__ FineGeom fine_geom(const Ctl* ctl) {
+  const uint32_t hi = __ldcg(&ctl->key_max);
+  const uint32_t tau = __ldcg(&ctl->tau);
+  const uint32_t lo = tau == 0xFFFFFFFFu ? hi : tau + 1;
+  const uint32_t x = lo ^ hi;
+  const int pb = x ? __clz(x) : 32;
+  FineGeom g;
+  g.sh = static_cast<uint32_t>(32 - pb - 11 > 0 ? 32 - pb - 11 : 0);
+  g.pref = pb ? (hi & (0xFFFFFFFFu << (32 - pb))) : 0u;
+  return g;
+}
+
+// Counting pass first when the scan set is large (sorted inputs with large
+// k): then only the keys from the bucket holding the k-th key upwards are
+// written, not every key above tau.
+__device__ __forceinline__ bool two_pass_wanted(int no_filter, int64_t total, int64_t k) {
+  const int64_t lim = 4 * k > (int64_t(1) << 22) ? 4 * k : (int64_t(1) << 22);
+  return !no_filter && total > lim;
+}
+
+// The query mode, decided once G is complete (warp 0 of the filter's last
+// block): select the k-th of G when |{x > tau}| >= k, else ties at tau.
+__device__ __forceinline__ void decide_mode(Ctl* ctl, int64_t k, int lvl0, bool kth_only) {
+  const uint32_t g = __ldcg(&ctl->two_pass) ? __ldcg(&ctl->g_all) : __ldcg(&ctl->g_count);
+  if (threadIdx.x == 0) ctl->g_total = g;
+  if (static_cast<int64_t>(g) >= k) {
+    if (threadIdx.x == 0) {
+      ctl->mode = kModeSelect;
+      ctl->gsel.k_rem = static_cast<uint32_t>(k);
+      // the leading digits common to all of G are known: they are the
+      // first lvl0 bytes of key_max; the selection starts after them
+      const uint64_t km = static_cast<uint64_t>(__ldcg(&ctl->key_max)) << 32;
+      ctl->gsel.prefix = lvl0 ? (km & (~0ull << (64 - 8 * lvl0))) : 0ull;
+      ctl->g_lvl0 = static_cast<uint32_t>(lvl0);
+    }
+    __syncwarp();
+    __threadfence();
+    select_digit<8>(&ctl->gsel, lvl0, 64, !kth_only);
+  } else if (threadIdx.x == 0) {
+    ctl->mode = kModeTies;
+    ctl->need = static_cast<uint32_t>(k - g);
+    ctl->kth_mapped = __ldcg(&ctl->tau);
+  }
+}
+
 // Positions of the queued delegates: the occurrence-th key equal to the
 // delegate in its 32-key segment, found by one coalesced read per request
 // and a vote. A warp takes 32 requests (lane u decodes request u), then
@@ -405,9 +458,11 @@ constexpr int kResCap = kThreads * 4;
 template <int DT, int B>
 __global__ void __launch_bounds__(kThreads) filter_resolve_kernel(FilterParams p) {
   __shared__ uint32_t sh[256];
+  __shared__ uint32_t fh[kFineBins];
   __shared__ uint64_t gbuf[kResCap];
   __shared__ uint32_t g_fill;
   zero_hist(sh);
+  for (int i = threadIdx.x; i < kFineBins; i += kThreads) fh[i] = 0;
   if (threadIdx.x == 0) g_fill = 0;
   __syncthreads();
   Ctl* ctl = p.ctl;
@@ -415,6 +470,10 @@ __global__ void __launch_bounds__(kThreads) filter_resolve_kernel(FilterParams p
   const int alpha = p.alpha;
   const uint32_t lane = lane_id();
   const int warp = threadIdx.x >> 5;
+  const int lvl0 = g_first_level(ctl, p.no_filter != 0);
+  const FineGeom fg = fine_geom(ctl);
+  // the counting pass of a large scan set needs these keys in its histogram
+  const bool fine = two_pass_wanted(p.no_filter, int64_t(__ldcg(&ctl->scanq_count)) << alpha, p.k);
   for (int64_t b0 = int64_t(blockIdx.x) * kThreads; b0 < nq; b0 += int64_t(gridDim.x) * kThreads) {
     const int64_t q = b0 + threadIdx.x;  // this lane's request
     uint32_t key = 0;
@@ -477,30 +536,17 @@ __global__ void __launch_bounds__(kThreads) filter_resolve_kernel(FilterParams p
         &ctl->error, kErrOverflowG);
     if (has) {
       gbuf[slot] = item;
-      atomicAdd(&sh[static_cast<uint32_t>(item >> 56)], 1u);
+      atomicAdd(&sh[comp_digit(item, lvl0)], 1u);
+      if (fine) atomicAdd(&fh[(comp_key(item) >> fg.sh) & (kFineBins - 1)], 1u);
     }
   }
   stage_flush<uint64_t, kThreads>(gbuf, &g_fill, &ctl->g_count, p.g, static_cast<uint64_t>(p.g_cap),
                                   &ctl->error, kErrOverflowG);
-  flush_hist(sh, ctl->gsel.hist[0]);
-  if (last_block(&ctl->filter_ticket)) {
-    if (threadIdx.x < 32) {
-      const uint32_t g = __ldcg(&ctl->g_count);
-      const uint64_t k = static_cast<uint64_t>(p.k);
-      if (threadIdx.x == 0) ctl->g_total = g;
-      if (g >= k) {
-        if (threadIdx.x == 0) {
-          ctl->mode = kModeSelect;
-          ctl->gsel.k_rem = static_cast<uint32_t>(k);
-        }
-        __syncwarp();
-        __threadfence();
-        select_digit<8>(&ctl->gsel, 0, 64, !p.kth_only);
-      } else if (threadIdx.x == 0) {
-        ctl->mode = kModeTies;
-        ctl->need = static_cast<uint32_t>(k - g);
-        ctl->kth_mapped = __ldcg(&ctl->tau);
-      }
+  flush_hist(sh, ctl->gsel.hist[lvl0]);
+  if (fine) {
+    for (int i = threadIdx.x; i < kFineBins; i += kThreads) {
+      const uint32_t v = fh[i];
+      if (v) atomicAdd(&ctl->fhist[i], v);
     }
   }
 }
@@ -544,12 +590,112 @@ struct ScanQ {
   }
 };
 
+// Counting pass over a large scan set (two_pass_wanted): the keys > tau by
+// their fine digit (with the delegates the resolve kernel placed, already
+// counted there). The last block finds the bucket b holding the k-th key
+// from the top and sets cut_key = cut(b): the writing pass then keeps only
+// keys >= cut_key, a superset of the answer. With fewer than k keys above
+// tau every one of them is kept (ties at tau follow).
+template <int DT>
+__global__ void __launch_bounds__(kThreads) filter_count_kernel(FilterParams p) {
+  __shared__ uint32_t fh[kFineBins];
+  __shared__ uint32_t s_q[2][kScanQ];
+  __shared__ uint32_t s_cnt;
+  Ctl* ctl = p.ctl;
+  const int64_t nq = __ldcg(&ctl->scanq_count);
+  const int64_t total = nq << p.alpha;
+  if (!two_pass_wanted(p.no_filter, total, p.k)) return;  // uniform over the grid
+  const uint32_t nact = active_blocks(total, kScanStep);
+  if (blockIdx.x >= nact) return;
+  for (int i = threadIdx.x; i < kFineBins; i += kThreads) fh[i] = 0;
+  if (threadIdx.x == 0) s_cnt = 0;
+  const uint32_t tau = __ldcg(&ctl->tau);
+  const FineGeom fg = fine_geom(ctl);
+  const int64_t step = int64_t(nact) * kScanStep;
+  const int64_t b0 = int64_t(blockIdx.x) * kScanStep;
+  ScanQ sq{s_q, {}, nq, p.alpha};
+  if (b0 < total) {
+    sq.fetch(p.scanq, b0);
+    sq.put(0);
+  }
+  __syncthreads();
+  uint32_t cnt = 0;
+  int cur = 0;
+  for (int64_t base = b0; base < total; base += step) {
+    uint32_t x[kScanKPT];
+    uint32_t hit = 0;
+#pragma unroll
+    for (int u = 0; u < kScanKPT; ++u) {
+      const int64_t v = base + threadIdx.x + int64_t(u) * kThreads;
+      const int64_t gi = v < total ? sq.pos(cur, base, v) : p.n;
+      const bool ok = gi < p.n;
+      x[u] = __ldg(p.keys + (ok ? gi : 0));
+      if (ok) hit |= 1u << u;
+    }
+    const bool more = base + step < total;
+    if (more) sq.fetch(p.scanq, base + step);
+#pragma unroll
+    for (int u = 0; u < kScanKPT; ++u) {
+      const uint32_t m = map_key<DT>(x[u]);
+      if (((hit >> u) & 1u) && m > tau) {
+        atomicAdd(&fh[(m >> fg.sh) & (kFineBins - 1)], 1u);
+        ++cnt;
+      }
+    }
+    if (more) sq.put(cur ^ 1);
+    __syncthreads();
+    cur ^= 1;
+  }
+  cnt = __reduce_add_sync(0xFFFFFFFFu, cnt);
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&s_cnt, cnt);
+  __syncthreads();
+  for (int i = threadIdx.x; i < kFineBins; i += kThreads) {
+    const uint32_t v = fh[i];
+    if (v) atomicAdd(&ctl->fhist[i], v);
+  }
+  if (threadIdx.x == 0 && s_cnt) atomicAdd(&ctl->scan_total, s_cnt);
+  if (last_block_of(&ctl->cnt_ticket, nact)) {
+    // the placed delegates (resolve kernel, earlier on the stream) are in
+    // g_count and in fhist already
+    const uint64_t g_all = uint64_t(__ldcg(&ctl->g_count)) + __ldcg(&ctl->scan_total);
+    const uint64_t k = static_cast<uint64_t>(p.k);
+    // thread t owns the 8 bins from the top [2047 - 8t - 7, 2047 - 8t]
+    constexpr int per = kFineBins / kThreads;
+    uint32_t c[per];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int j = 0; j < per; ++j) {
+      c[j] = __ldcg(&ctl->fhist[kFineBins - 1 - (threadIdx.x * per + j)]);
+      sum += c[j];
+    }
+    const uint32_t above = block_scan_excl<kThreads>(sum, nullptr);
+    if (g_all >= k && above < k && uint64_t(above) + sum >= k) {
+      uint32_t acc = above;
+      int j = 0;
+      for (; j < per - 1; ++j) {
+        if (uint64_t(acc) + c[j] >= k) break;
+        acc += c[j];
+      }
+      const uint32_t b = static_cast<uint32_t>(kFineBins - 1 - (threadIdx.x * per + j));
+      ctl->cut_key = fg.pref | (b << fg.sh);
+    }
+    if (threadIdx.x == 0) {
+      if (g_all < k) ctl->cut_key = 0u;  // every key > tau is needed
+      ctl->g_all = static_cast<uint32_t>(g_all);
+      ctl->two_pass = 1;
+    }
+  }
+}
+
 template <int DT>
 __global__ void __launch_bounds__(kThreads) filter_scan_kernel(FilterParams p) {
   __shared__ uint32_t sh[256];
   __shared__ uint32_t s_q[2][kScanQ];
   zero_hist(sh);
+  const int lvl0 = g_first_level(p.ctl, p.no_filter != 0);
   const uint32_t tau = __ldcg(&p.ctl->tau);
+  // after a counting pass only keys >= cut_key are written
+  const uint32_t cut = __ldcg(&p.ctl->two_pass) ? __ldcg(&p.ctl->cut_key) : 0u;
   const int64_t nq = __ldcg(&p.ctl->scanq_count);
   const int64_t total = nq << p.alpha;
   const uint32_t nact = active_blocks(total, kScanStep);
@@ -581,7 +727,7 @@ __global__ void __launch_bounds__(kThreads) filter_scan_kernel(FilterParams p) {
 #pragma unroll
     for (int u = 0; u < kScanKPT; ++u) {
       x[u] = map_key<DT>(x[u]);
-      if (!(x[u] > tau || p.no_filter)) hit &= ~(1u << u);
+      if (!((x[u] > tau && x[u] >= cut) || p.no_filter)) hit &= ~(1u << u);
     }
     const uint32_t wt = __reduce_add_sync(0xFFFFFFFFu, __popc(hit));
     uint32_t wb, unused;
@@ -594,9 +740,10 @@ __global__ void __launch_bounds__(kThreads) filter_scan_kernel(FilterParams p) {
       if (h) {
         const int64_t v = base + threadIdx.x + int64_t(u) * kThreads;
         const uint32_t slot = wb + run + __popc(bal & lt);
-        if (slot < p.g_cap) p.g[slot] = make_comp(x[u], static_cast<uint32_t>(sq.pos(cur, base, v)));
+        const uint64_t cmp = make_comp(x[u], static_cast<uint32_t>(sq.pos(cur, base, v)));
+        if (slot < p.g_cap) p.g[slot] = cmp;
         else atomicOr(&p.ctl->error, kErrOverflowG);
-        rh.add(sh, x[u] >> 24);
+        rh.add(sh, comp_digit(cmp, lvl0));
       }
       run += __popc(bal);
     }
@@ -606,12 +753,17 @@ __global__ void __launch_bounds__(kThreads) filter_scan_kernel(FilterParams p) {
   }
   rh.flush(sh);
   __syncthreads();
-  flush_hist(sh, p.ctl->gsel.hist[0]);
+  flush_hist(sh, p.ctl->gsel.hist[lvl0]);
+  // G is complete once every active block is here: decide the mode
+  if (last_block_of(&p.ctl->scan_ticket, nact)) {
+    if (threadIdx.x < 32) decide_mode(p.ctl, p.k, lvl0, p.kth_only != 0);
+  }
 }
 
 // --------------------------------------------------------- second select ---
 // Stage s (1..8) reads the composites that match the digits selected so far
-// (stage 1: all of G) and decides digit level s-1: larger digit -> winner
+// (stage 1: all of G) and decides digit level lvl0 + s - 1, where lvl0
+// leading digits are common to all of G: larger digit -> winner
 // (written to W), equal -> survivor for stage s+1 (or winner when the
 // bucket is exactly what is still needed), smaller -> dropped. The last
 // block selects the next digit from the survivors' histogram.
@@ -630,7 +782,10 @@ constexpr int kGCap = kThreads * kGIpt;  // one step's worth per buffer
 __global__ void __launch_bounds__(kThreads) gstage_kernel(GSelParams p, int s) {
   Ctl* ctl = p.ctl;
   if (__ldcg(&ctl->mode) != kModeSelect) return;
-  const int level = s - 1;
+  // stage s decides digit lvl0 + s - 1 (the digits before lvl0 are common
+  // to all of G); k-selection stops once the four key digits are known
+  const int level = static_cast<int>(__ldcg(&ctl->g_lvl0)) + s - 1;
+  if (level > 7 || (p.kth_only && level > 2)) return;
   const int64_t count = (s == 1) ? imin64(__ldcg(&ctl->g_count), p.g_cap)
                                  : static_cast<int64_t>(__ldcg(&ctl->stage_count[s]));
   if (count == 0) return;  // uniform over the grid: nothing survived
@@ -1624,8 +1779,9 @@ cudaError_t launch_threshold(const Work& w, int sms, cudaStream_t s) {
 template <int DT, int B>
 static void filter_t(const FilterParams& p, int g1, int g2, int g3, cudaStream_t s) {
   filter_classify_kernel<DT, B><<<g1, kThreads, 0, s>>>(p);
-  filter_scan_kernel<DT><<<g2, kThreads, 0, s>>>(p);
   filter_resolve_kernel<DT, B><<<g3, kThreads, 0, s>>>(p);
+  filter_count_kernel<DT><<<g2, kThreads, 0, s>>>(p);
+  filter_scan_kernel<DT><<<g2, kThreads, 0, s>>>(p);
 }
 
 cudaError_t launch_filter(const Work& w, const void* keys, bool kth_only, int sms,
@@ -1668,7 +1824,7 @@ cudaError_t launch_filter(const Work& w, const void* keys, bool kth_only, int sm
     default: return cudaErrorInvalidValue;
   }
 #undef DRTOPK_FILTER_CASE
-  note_launch(3);
+  note_launch(4);
   return cudaGetLastError();
 }
 

@@ -336,10 +336,13 @@ def test_large_scan_sets():
     for dt, kind in (("u32", "asc"), ("u32", "desc"), ("f32", "asc")):
         bits = make(kind, n, 41, dt)
         x = to_dev(bits, dt)
+        mapped = oracle.map_keys(bits, DT[dt])
         for k, alpha in ((1 << 20, 0), (1 << 18, 6), (300001, 8)):
             st = check_topk(bits, dt, k, alpha=alpha)
             large += (st["scanned"] << st["alpha"]) > (1 << 22)
             assert st["greater"] >= k, st
+            # |{x > tau}| stays exact when the scan set is counted first
+            assert st["greater"] == int((mapped > st["tau"]).sum()), st
         got = drtopk.drtopk_kth(x, 1 << 20, dtype=dt)
         torch.cuda.synchronize()
         assert int(host_bits(got)[0]) == oracle.kth(bits, DT[dt], 1 << 20), (dt, kind)
@@ -360,3 +363,25 @@ def test_large_scan_sets():
     got = drtopk.drtopk_kth(to_dev(bits, "u32"), k, dtype="u32")
     torch.cuda.synchronize()
     assert int(host_bits(got)[0]) == 0
+
+
+def test_output_sort_clustered_winners():
+    """Winners that share their high bits: many copies of the largest keys
+    packed into a few subranges (so few delegates see them and the query
+    stays in select mode). The output sort's buckets then hold more entries
+    than one CTA sorts in shared memory, which takes its chunked merge path;
+    the result must still equal the oracle's."""
+    rng = np.random.default_rng(91)
+    n = 1 << 22
+    for copies, k, spread in ((20000, 30000, False), (70000, 100000, False),
+                              (9000, 50000, True), (300000, 400000, False)):
+        bits = rng.integers(0, 0xF0000000, n, dtype=np.uint64).astype(np.uint32)
+        if spread:  # a few clusters of two top values
+            for c0 in (1000, 2000000, 3000000):
+                bits[c0:c0 + copies] = 0xFFFFFFF0
+                bits[c0 + copies:c0 + 2 * copies] = 0xFFFFFFE0
+        else:
+            bits[5000:5000 + copies] = 0xFFFFFFF0
+        st = check_topk(bits, "u32", k)
+        assert st["greater"] >= k, st  # select mode: the sort covers all k
+        check_topk(bits, "u32", k, alpha=4, beta=1)
