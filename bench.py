@@ -59,11 +59,13 @@ KS = [1024, 1 << 20]
 SEED = 3
 PAPER_UD_MS = 6.4  # Dr. Top-k radix, |V| = 2^30 UD, k = 1024, V100S (Sec. 5.1)
 # DRAM bytes (read + write) per key of one delegate-pass launch, by alpha
-# (the subrange size sets the delegate writes), from one ncu capture per
-# alpha of the delegate kernel at n = 2^28 (scaled by keys to a launch).
-# None where no capture of the current kernel exists; must be re-measured
-# (or set to None) whenever the delegate kernel changes.
-DELEG_DRAM_BYTES_PER_KEY = {11: None, 6: None}
+# (the subrange size sets the delegate writes): ncu dram__bytes_read.sum +
+# dram__bytes_write.sum of the delegate kernel in this benchmark's own
+# launches at n = 2^30 (Zipf input, k = 1024 -> alpha 11, k = 2^20 ->
+# alpha 6; mean of two launches each). Must be re-measured (or set to None)
+# whenever the delegate kernel changes.
+DELEG_DRAM_BYTES_PER_KEY = {11: (4295.1e6 + 6.15e6) / (1 << 30),
+                            6: (4295.1e6 + 151.0e6) / (1 << 30)}
 
 
 def parse():
@@ -695,8 +697,9 @@ def main():
                 "traffic_ratio_to_4n_by_alpha": {str(a): (v / (4.0 * n) if v else None)
                                                  for a, v in by_alpha.items()},
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the "
-                                  "delegate kernel at n=2^28 per alpha, scaled by keys to one "
-                                  "launch; launch-weighted mean over the timed queries",
+                                  "delegate kernel per alpha, captured in this benchmark's "
+                                  "launches at n=2^30; launch-weighted mean over the timed "
+                                  "queries",
                 "kernel": "delegate_kernel (TMA-streamed delegate pass)",
                 "algorithmic_bytes_per_launch": 4 * n, "launches": dl,
                 "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs, copy burst)" % peak_src,

@@ -31,7 +31,7 @@ namespace drtopk {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kScanKPT = 8;  // virtual keys per thread per filter-scan step
+constexpr int kScanKPT = 16;  // virtual keys per thread per filter-scan step
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
   uint32_t m;
@@ -596,7 +596,60 @@ struct ScanQ {
 // from the top and sets cut_key = cut(b): the writing pass then keeps only
 // keys >= cut_key, a superset of the answer. With fewer than k keys above
 // tau every one of them is kept (ties at tau follow).
-template <int DT>
+// Slot u of this thread in the scan step at virtual key `base`. VEC (key
+// array 16-byte aligned): four consecutive virtual keys per 16-byte load
+// (they lie in one subrange, at a multiple of 4 from its start, since
+// subranges hold at least 4 keys); else one key per slot, strided.
+template <bool VEC>
+__device__ __forceinline__ int64_t scan_vkey(int64_t base, int u) {
+  if constexpr (VEC)
+    return base + 4 * (int64_t(threadIdx.x) + int64_t(kThreads) * (u >> 2)) + (u & 3);
+  else
+    return base + threadIdx.x + int64_t(u) * kThreads;
+}
+
+// Loads this thread's keys of the step (raw bits); bit u of *hit marks a
+// slot that holds a key of the array.
+template <bool VEC>
+__device__ __forceinline__ void scan_load(const uint32_t* keys, int64_t n, const ScanQ& sq,
+                                          int cur, int64_t base, int64_t total,
+                                          uint32_t (&x)[kScanKPT], uint32_t& hit) {
+  hit = 0;
+  if constexpr (VEC) {
+#pragma unroll
+    for (int j = 0; j < kScanKPT / 4; ++j) {
+      const int64_t v0 = scan_vkey<true>(base, 4 * j);
+      const int64_t g0 = v0 < total ? sq.pos(cur, base, v0) : n;
+      if (g0 + 3 < n) {
+        const uint4 w = __ldg(reinterpret_cast<const uint4*>(keys + g0));
+        x[4 * j + 0] = w.x;
+        x[4 * j + 1] = w.y;
+        x[4 * j + 2] = w.z;
+        x[4 * j + 3] = w.w;
+        hit |= 0xFu << (4 * j);
+      } else {
+        // the ragged end of the array (or beyond the step)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const bool ok = g0 + e < n;
+          x[4 * j + e] = ok ? __ldg(keys + g0 + e) : 0u;
+          if (ok) hit |= 1u << (4 * j + e);
+        }
+      }
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < kScanKPT; ++u) {
+      const int64_t v = scan_vkey<false>(base, u);
+      const int64_t gi = v < total ? sq.pos(cur, base, v) : n;
+      const bool ok = gi < n;
+      x[u] = __ldg(keys + (ok ? gi : 0));
+      if (ok) hit |= 1u << u;
+    }
+  }
+}
+
+template <int DT, bool VEC>
 __global__ void __launch_bounds__(kThreads) filter_count_kernel(FilterParams p) {
   __shared__ uint32_t fh[kFineBins];
   __shared__ uint32_t s_q[2][kScanQ];
@@ -623,15 +676,8 @@ __global__ void __launch_bounds__(kThreads) filter_count_kernel(FilterParams p) 
   int cur = 0;
   for (int64_t base = b0; base < total; base += step) {
     uint32_t x[kScanKPT];
-    uint32_t hit = 0;
-#pragma unroll
-    for (int u = 0; u < kScanKPT; ++u) {
-      const int64_t v = base + threadIdx.x + int64_t(u) * kThreads;
-      const int64_t gi = v < total ? sq.pos(cur, base, v) : p.n;
-      const bool ok = gi < p.n;
-      x[u] = __ldg(p.keys + (ok ? gi : 0));
-      if (ok) hit |= 1u << u;
-    }
+    uint32_t hit;
+    scan_load<VEC>(p.keys, p.n, sq, cur, base, total, x, hit);
     const bool more = base + step < total;
     if (more) sq.fetch(p.scanq, base + step);
 #pragma unroll
@@ -687,7 +733,7 @@ __global__ void __launch_bounds__(kThreads) filter_count_kernel(FilterParams p) 
   }
 }
 
-template <int DT>
+template <int DT, bool VEC>
 __global__ void __launch_bounds__(kThreads) filter_scan_kernel(FilterParams p) {
   __shared__ uint32_t sh[256];
   __shared__ uint32_t s_q[2][kScanQ];
@@ -713,15 +759,8 @@ __global__ void __launch_bounds__(kThreads) filter_scan_kernel(FilterParams p) {
   int cur = 0;
   for (int64_t base = b0; base < total; base += step) {
     uint32_t x[kScanKPT];
-    uint32_t hit = 0;
-#pragma unroll
-    for (int u = 0; u < kScanKPT; ++u) {
-      const int64_t v = base + threadIdx.x + int64_t(u) * kThreads;
-      const int64_t gi = v < total ? sq.pos(cur, base, v) : p.n;
-      const bool ok = gi < p.n;
-      x[u] = __ldg(p.keys + (ok ? gi : 0));
-      if (ok) hit |= 1u << u;
-    }
+    uint32_t hit;
+    scan_load<VEC>(p.keys, p.n, sq, cur, base, total, x, hit);
     const bool more = base + step < total;
     if (more) sq.fetch(p.scanq, base + step);  // in flight with this step's keys
 #pragma unroll
@@ -738,7 +777,7 @@ __global__ void __launch_bounds__(kThreads) filter_scan_kernel(FilterParams p) {
       const bool h = (hit >> u) & 1u;
       const uint32_t bal = __ballot_sync(0xFFFFFFFFu, h);
       if (h) {
-        const int64_t v = base + threadIdx.x + int64_t(u) * kThreads;
+        const int64_t v = scan_vkey<VEC>(base, u);
         const uint32_t slot = wb + run + __popc(bal & lt);
         const uint64_t cmp = make_comp(x[u], static_cast<uint32_t>(sq.pos(cur, base, v)));
         if (slot < p.g_cap) p.g[slot] = cmp;
@@ -1780,8 +1819,13 @@ template <int DT, int B>
 static void filter_t(const FilterParams& p, int g1, int g2, int g3, cudaStream_t s) {
   filter_classify_kernel<DT, B><<<g1, kThreads, 0, s>>>(p);
   filter_resolve_kernel<DT, B><<<g3, kThreads, 0, s>>>(p);
-  filter_count_kernel<DT><<<g2, kThreads, 0, s>>>(p);
-  filter_scan_kernel<DT><<<g2, kThreads, 0, s>>>(p);
+  if ((reinterpret_cast<uintptr_t>(p.keys) & 15u) == 0) {
+    filter_count_kernel<DT, true><<<g2, kThreads, 0, s>>>(p);
+    filter_scan_kernel<DT, true><<<g2, kThreads, 0, s>>>(p);
+  } else {
+    filter_count_kernel<DT, false><<<g2, kThreads, 0, s>>>(p);
+    filter_scan_kernel<DT, false><<<g2, kThreads, 0, s>>>(p);
+  }
 }
 
 cudaError_t launch_filter(const Work& w, const void* keys, bool kth_only, int sms,
@@ -1806,7 +1850,7 @@ cudaError_t launch_filter(const Work& w, const void* keys, bool kth_only, int sm
   // requests to resolve: at most rq_cap, one per thread per block step
   const int g3 = grid_for(w.rq_cap, kThreads, sms, 4);
   // scanned keys are bounded by the G capacity (or n when tau = 0)
-  const int g2 = grid_for(w.g_cap, kScanStep, sms, 4);
+  const int g2 = grid_for(w.g_cap, kScanStep, sms, 6);
 #define DRTOPK_FILTER_CASE(DTV)                              \
   switch (w.beta) {                                          \
     case 1: filter_t<DTV, 1>(p, g1, g2, g3, s); break;       \
