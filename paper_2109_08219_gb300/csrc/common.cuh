@@ -113,8 +113,8 @@ struct Ctl {
   uint32_t kth_mapped;
   uint32_t ds_count;       // delegate keys surviving the first threshold digit
   uint32_t scanq_count;    // subranges queued for the filter scan
-  uint32_t tie_ticket;     // next tile of the tie path
-  uint32_t tie_cut_inv;    // ~(first tile whose tie prefix reaches `need`); 0: none yet
+  uint32_t tie_ticket;     // next listed tile of the dense tie count
+  uint32_t tie_cut_inv;    // ~(first listed tile not needed); 0: none yet
   uint32_t stage_count[10];  // survivors entering each second-select stage
   uint32_t ds_inplace;       // threshold passes 2-3 read the delegate keys in place
   uint32_t sort_ticket;
@@ -138,6 +138,7 @@ struct Ctl {
   uint32_t cnt_ticket;
   uint32_t scan_ticket;
   uint32_t fhist[2048];      // keys > tau by their 11 bits below the common prefix
+  uint32_t tie_sum;          // ties counted so far by the dense tie count
 };
 
 // First digit level (byte of the (key, ~idx) composite, 0 = top) that can

@@ -915,23 +915,22 @@ __global__ void __launch_bounds__(kThreads) gstage_kernel(GSelParams p, int s) {
 // ------------------------------------------------------------ tie path ----
 // Mode kModeTies (|G| < k, the k-th key is tau): the answer is G plus the
 // `need` smallest indices holding tau (reading R1). The subranges are cut
-// into tiles of consecutive subranges, and three kernels place the ties:
+// into tiles of consecutive subranges:
 //   A  per tile, a lower bound of its ties from the delegates alone (exact
 //      unless some subrange's beta delegates all reach tau: "inexact");
 //   B  one block: exclusive prefixes of the lower bounds, the last tile that
 //      can matter (the first whose lower-bound prefix reaches `need`), and
 //      the list, in index order, of the tiles up to it that hold ties or are
-//      inexact;
-//   C  the listed tiles in order (an atomic ticket): exact counts (inexact
-//      subranges read), the tile's prefix = its lower-bound prefix plus the
-//      corrections (exact - lower bound) of the earlier listed tiles, found
-//      by a decoupled look-back (warp-wide window, bounded waits) unless no
-//      inexact tile precedes it; then its ties go to W[|G| + prefix + rank]
-//      in index order. The first tile whose prefix reaches `need` is the
-//      cut; later tiles stop.
+//      inexact; dense when most of their subranges must be read;
+//   C  exact tie counts of the listed tiles (dense: whole tiles by bulk
+//      copies, handed out in index order until the counted ones hold
+//      `need`; sparse: the few subranges of interest, a warp each), one-block
+//      prefixes of the counts in list order and the cut, then the tiles
+//      before the cut write their ties to W[|G| + prefix + rank] in index
+//      order, in parallel.
 // Sparse ties (one tie needed among distinct keys) touch one tile; dense
-// ties (all keys equal) read only the tiles before the cut plus those in
-// flight.
+// ties (all keys equal) read the tiles before the cut plus at most one
+// round of tiles in flight, twice.
 struct TieParams {
   const uint32_t* keys;
   int64_t n, S, k;
@@ -954,22 +953,10 @@ constexpr int kTieTileKeys = 32768;     // keys per tile (at least one subrange)
 constexpr int kTieTileMaxSub = 1024;    // subranges per tile at most
 constexpr int kTieMaxSeg = 2048;        // 32-key segments per tile at most (alpha = 16)
 constexpr int kTiePlanChunk = 8192;     // tiles per shared-memory pass of the plan
-constexpr uint64_t kTieAgg = uint64_t(1) << 32;
-constexpr uint64_t kTieIncl = uint64_t(2) << 32;
-constexpr uint32_t kTieSpin = 1u << 22;
 constexpr uint32_t kTieInexact = 0x80000000u;
 // tile word: bits 0-15 lower bound, 16-29 inexact subranges, 31 inexact flag
 __device__ __forceinline__ uint32_t tlb_lb(uint32_t v) { return v & 0xFFFFu; }
 __device__ __forceinline__ uint32_t tlb_ninex(uint32_t v) { return (v >> 16) & 0x3FFFu; }
-
-__device__ __forceinline__ void st_relaxed_u64(uint64_t* p, uint64_t v) {
-  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t* p) {
-  uint64_t v;
-  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
 
 // Ties at tau a subrange holds by its delegates, and whether non-delegates
 // may hold more (all beta delegates reach tau and the subrange is longer).
@@ -1158,227 +1145,6 @@ __global__ void __launch_bounds__(1024) tie_plan_kernel(TieParams p) {
   }
 }
 
-// The ties of a tile are ranked per 32-key segment. The tile's keys (when
-// some subrange must be read) come into shared memory by one bulk copy
-// (TMA, bounded wait) per chunk of kTieTileKeys; a warp vote per segment
-// gives its tie bitmask (subranges that may hold non-delegate ties, and for
-// alpha < 5 every subrange that may hold a tie at all). A subrange whose
-// ties are all delegates has its count at its first segment. Exclusive
-// prefixes over the segments rank every tie; the bitmasks place them
-// without reading the keys again.
-constexpr int kTieBufBytes = kTieTileKeys * 4 + 32;
-
-__device__ __forceinline__ void tie_issue_copy(const uint32_t* keys, int64_t n, int64_t x0,
-                                               int64_t cnt, unsigned char* buf, uint64_t* bar,
-                                               uint64_t pol, int* shift) {
-  // keys [x0, x0 + cnt) -> buf at word `shift` (= the key's offset in its
-  // 16-byte block); the bulk copy starts at that block and stops at the last
-  // 16-byte boundary of the array, the rest by plain loads
-  const int64_t base = static_cast<int64_t>(reinterpret_cast<uintptr_t>(keys + x0));
-  const int s = static_cast<int>((base & 15) >> 2);
-  const int64_t a0 = base & ~int64_t(15);
-  const int64_t end16 = static_cast<int64_t>(reinterpret_cast<uintptr_t>(keys + n)) & ~int64_t(15);
-  const int64_t a1 = imin64((base + cnt * 4 + 15) & ~int64_t(15), end16);
-  const int64_t bytes = a1 > a0 ? a1 - a0 : 0;
-  uint32_t* dst = reinterpret_cast<uint32_t*>(buf);
-  const int64_t covered = bytes / 4 - s;  // keys [0, covered) come by the bulk copy
-  for (int64_t e = (covered > 0 ? covered : 0); e < cnt; ++e) dst[s + e] = keys[x0 + e];
-  if (bytes > 0) {
-    fence_proxy_async_smem();
-    mbar_arrive_expect_tx(bar, static_cast<uint32_t>(bytes));
-    tma_load_1d(buf, reinterpret_cast<const void*>(a0), static_cast<uint32_t>(bytes), bar, pol);
-  } else {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-  }
-  *shift = s;
-}
-
-// Shared memory of one tile's tie work.
-struct TieTileSmem {
-  uint32_t seg[kTieMaxSeg];     // counts, then exclusive prefixes
-  uint32_t bits[kTieMaxSeg];    // tie bitmask per segment
-  uint32_t dc[kTieTileMaxSub];  // ties known from the delegates
-  uint8_t rd[kTieTileMaxSub];   // subrange read from its keys
-};
-
-// Counts the ties of tile t per 32-key segment and turns the counts into
-// exclusive prefixes; returns the tile's total (block-wide, all threads).
-// kTma: the tile comes whole by bulk copies (bounded waits; *timed_out set
-// on failure), else only the keys of the subranges read are loaded.
-template <int DT, int B, bool kTma, int NT>
-__device__ uint32_t tie_tile_count(const TieParams& p, int64_t t, uint32_t tau, TieTileSmem& sm,
-                                   unsigned char* tbuf, uint64_t* bar, uint32_t& phase,
-                                   uint64_t pol, uint32_t* s_shift, uint32_t& read_subs,
-                                   bool* timed_out) {
-  const int tid = threadIdx.x;
-  const uint32_t lane = lane_id();
-  const int alpha = p.alpha;
-  const int64_t i_lo = t * p.tsub;
-  const int64_t nsub = imin64(p.tsub, p.S - i_lo);
-  const int64_t klo = i_lo << alpha;
-  const int64_t khi = imin64(p.n, (i_lo + nsub) << alpha);
-  const int nseg = static_cast<int>((khi - klo + 31) >> 5);
-  *timed_out = false;
-  for (int q = tid; q < nseg; q += NT) {
-    sm.seg[q] = 0;
-    sm.bits[q] = 0;
-  }
-  __syncthreads();
-  uint32_t nread = 0;
-  for (int64_t ii = tid; ii < nsub; ii += NT) {
-    bool x;
-    const uint32_t c = tie_lb_of<B>(p, i_lo + ii, tau, &x);
-    const bool rd = alpha < 5 ? (c > 0 || x) : x;
-    sm.rd[ii] = rd ? 1 : 0;
-    sm.dc[ii] = rd ? 0u : c;
-    if (!rd && c > 0) sm.seg[static_cast<int>((ii << alpha) >> 5)] = c;  // alpha >= 5 here
-    nread += rd ? 1u : 0u;
-  }
-  read_subs += nread;
-  const int anyread = __syncthreads_or(nread > 0);
-  if (!kTma && anyread) {
-    // direct loads over the tile as one array, 4 in flight per thread, only
-    // the keys of subranges read (block-uniform trip count; a segment is one
-    // warp step)
-    for (int64_t xb = klo; xb < khi; xb += int64_t(NT) * 4) {
-      uint32_t v[4];
-      bool on[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int64_t x = xb + tid + int64_t(u) * NT;
-        on[u] = x < khi && sm.rd[(x >> alpha) - i_lo];
-        v[u] = on[u] ? __ldg(p.keys + x) : 0u;
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int64_t x = xb + tid + int64_t(u) * NT;
-        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, on[u] && map_key<DT>(v[u]) == tau);
-        if (lane == 0 && bal) {
-          const int seg = static_cast<int>((x - klo) >> 5);
-          sm.seg[seg] = __popc(bal);
-          sm.bits[seg] = bal;
-        }
-      }
-    }
-    __syncthreads();
-  }
-  for (int64_t c0 = klo; kTma && anyread && c0 < khi; c0 += kTieTileKeys) {
-    const int64_t cn = imin64(kTieTileKeys, khi - c0);
-    if (tid == 0) {
-      int sh;
-      tie_issue_copy(p.keys, p.n, c0, cn, tbuf, bar, pol, &sh);
-      *s_shift = static_cast<uint32_t>(sh);
-    }
-    const bool ok = mbar_wait_bounded(bar, phase & 1u);
-    ++phase;
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) {
-        atomicOr(&p.ctl->error, kErrTimeout);
-        mbar_wait_bounded(bar, (phase - 1) & 1u);  // let the copy land (bounded)
-      }
-      *timed_out = true;
-      return 0;
-    }
-    const uint32_t* kb = reinterpret_cast<const uint32_t*>(tbuf) + *s_shift;
-    for (int64_t xb = 0; xb < cn; xb += NT) {
-      const int64_t e = xb + tid;
-      const int64_t x = c0 + e;
-      const bool on = e < cn && sm.rd[(x >> alpha) - i_lo];
-      const uint32_t bal = __ballot_sync(0xFFFFFFFFu, on && map_key<DT>(kb[e]) == tau);
-      if (lane == 0 && bal) {
-        const int seg = static_cast<int>((x - klo) >> 5);
-        sm.seg[seg] = __popc(bal);
-        sm.bits[seg] = bal;
-      }
-    }
-    __syncthreads();  // the buffer is reused by the next copy
-    fence_proxy_async_smem();
-  }
-  // exclusive prefixes over the segments (8 consecutive per thread)
-  uint32_t tot = 0;
-  constexpr int kPer = kTieMaxSeg / NT;
-  uint32_t c[kPer];
-  uint32_t sum = 0;
-#pragma unroll
-  for (int e = 0; e < kPer; ++e) {
-    const int q = tid * kPer + e;
-    c[e] = q < nseg ? sm.seg[q] : 0u;
-    sum += c[e];
-  }
-  uint32_t run = block_scan_excl<NT>(sum, &tot);
-#pragma unroll
-  for (int e = 0; e < kPer; ++e) {
-    const int q = tid * kPer + e;
-    if (q < nseg) sm.seg[q] = run;
-    run += c[e];
-  }
-  __syncthreads();
-  return tot;
-}
-
-// Writes the ties of tile t whose ranks E + (prefix in the tile) are below
-// `need`, from the segment bitmasks and the delegates (block-wide).
-template <int DT, int B, int NT>
-__device__ void tie_tile_emit(const TieParams& p, int64_t t, uint32_t tau, uint32_t need,
-                              uint32_t g, uint32_t E, const TieTileSmem& sm, uint32_t& emitted) {
-  const int tid = threadIdx.x;
-  const uint32_t lane = lane_id();
-  const int warp = tid >> 5;
-  const int alpha = p.alpha;
-  const int64_t i_lo = t * p.tsub;
-  const int64_t nsub = imin64(p.tsub, p.S - i_lo);
-  const int64_t klo = i_lo << alpha;
-  const int64_t khi = imin64(p.n, (i_lo + nsub) << alpha);
-  const int nseg = static_cast<int>((khi - klo + 31) >> 5);
-  // from the bitmasks: a warp per segment, coalesced writes
-  for (int q = warp; q < nseg; q += NT / 32) {
-    const uint32_t bits = sm.bits[q];
-    const uint32_t r0 = E + sm.seg[q];
-    if (bits == 0 || r0 >= need) continue;
-    if ((bits >> lane) & 1u) {
-      const uint32_t r = r0 + __popc(bits & lanemask_lt());
-      if (r < need) {
-        p.w[g + r] = make_comp(tau, static_cast<uint32_t>(klo + int64_t(q) * 32 + lane));
-        ++emitted;
-      }
-    }
-  }
-  // subranges whose ties are all delegates (alpha >= 5), a warp each: D
-  // lists equal keys in index order (segment, then occurrence); the position
-  // is the occurrence-th key equal to tau in the 32-key segment, found by
-  // one coalesced read and a vote
-  for (int64_t ii = warp; ii < nsub; ii += NT / 32) {
-    if (sm.rd[ii] || sm.dc[ii] == 0) continue;
-    uint32_t r = E + sm.seg[static_cast<int>((ii << alpha) >> 5)];
-    if (r >= need) continue;
-    const int64_t i = i_lo + ii;
-    uint32_t dk[B];
-    uint16_t ds[B];
-#pragma unroll
-    for (int q = 0; q < B; ++q) {
-      dk[q] = p.dkeys[i * B + q];
-      ds[q] = p.dsegs[i * B + q];
-    }
-#pragma unroll
-    for (int q = 0; q < B; ++q) {
-      if (dk[q] == tau && ds[q] != kNoSeg && r < need) {
-        const int o = occ_rank<B>(dk, ds, q);
-        const int64_t lo = (i << alpha) + int64_t(ds[q]) * 32;
-        const int64_t hi = imin64(imin64(p.n, lo + 32), (i + 1) << alpha);
-        const bool m = lo + lane < hi && map_key<DT>(__ldg(p.keys + lo + lane)) == tau;
-        uint32_t bal = __ballot_sync(0xFFFFFFFFu, m);
-        for (int z = 0; z < o; ++z) bal &= bal - 1;
-        if (lane == 0) {
-          if (bal == 0) atomicOr(&p.ctl->error, kErrTieRank);
-          p.w[g + r] = make_comp(tau, static_cast<uint32_t>(lo + (bal ? __ffs(bal) - 1 : 0)));
-          ++emitted;
-        }
-        ++r;
-      }
-    }
-  }
-}
-
 __device__ __forceinline__ void tie_copy_g(const TieParams& p, uint32_t g) {
   // G is part of the answer, in front of the ties
   for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < g;
@@ -1396,108 +1162,158 @@ __device__ __forceinline__ void tie_finish(const TieParams& p, uint32_t read_sub
   if (lane == 0 && emitted) atomicAdd(&p.ctl->w_count, emitted);
 }
 
-// Dense ties: the listed tiles walked in order (ticket), each read whole by
-// bulk copies; its prefix = lower-bound prefix + corrections of the earlier
-// listed tiles (decoupled look-back); the first tile reaching `need` cuts.
-constexpr int kWalkThreads = 512;
+// Dense ties (most listed subranges must be read), in three kernels:
+//   1. tie_dcount: the listed tiles are handed out in index order (ticket)
+//      and their keys equal to tau counted, whole tiles streamed with
+//      16-byte loads; a CTA stops once the tiles counted so far hold `need`
+//      ties (every tile handed out after that lies past the cut, since the
+//      counted ones all precede it);
+//   2. tie_scan (shared with the sparse path): exclusive prefixes of the
+//      counts in list order and the cut;
+//   3. tie_dplace: the tiles before the cut, in parallel: a ballot per
+//      32-key segment read straight from global memory (many segments in
+//      flight per warp), prefixes over the segments, ties written from the
+//      bitmasks.
+constexpr int kDenseThreads = 1024;
 
-template <int DT, int B>
-__global__ void __launch_bounds__(kWalkThreads, 1) tie_walk_kernel(TieParams p) {
+__device__ __forceinline__ void tie_tile_range(const TieParams& p, int64_t t, int64_t* klo,
+                                               int64_t* khi) {
+  const int64_t i_lo = t * p.tsub;
+  const int64_t nsub = imin64(p.tsub, p.S - i_lo);
+  *klo = i_lo << p.alpha;
+  *khi = imin64(p.n, (i_lo + nsub) << p.alpha);
+}
+
+template <int DT>
+__global__ void __launch_bounds__(kDenseThreads) tie_dcount_kernel(TieParams p) {
+  Ctl* ctl = p.ctl;
+  if (__ldcg(&ctl->mode) != kModeTies || __ldcg(&ctl->tie_dense) == 0) return;
+  const uint32_t tau = __ldcg(&ctl->tau);
+  const uint32_t need = __ldcg(&ctl->need);
+  const int64_t nl = __ldcg(&ctl->tie_nlist);
+  const bool vec = (reinterpret_cast<uintptr_t>(p.keys) & 15u) == 0;
+  __shared__ int64_t s_j;
+  __shared__ uint32_t s_w[kDenseThreads / 32];
+  const int tid = threadIdx.x;
+  uint32_t read_subs = 0;
+  for (;;) {
+    if (tid == 0) {
+      s_j = -1;
+      if (__ldcg(&ctl->tie_sum) < need) {
+        const int64_t j = atomicAdd(&ctl->tie_ticket, 1u);
+        if (j < nl) s_j = j;
+      }
+    }
+    __syncthreads();
+    const int64_t j = s_j;
+    if (j < 0) break;
+    int64_t klo, khi;
+    tie_tile_range(p, p.list[j] & ~kTieInexact, &klo, &khi);
+    uint32_t c = 0;
+    // 8 words of 4 keys per thread in flight (a 32768-key tile in one round)
+    for (int64_t x0 = klo + int64_t(tid) * 4; x0 < khi; x0 += int64_t(kDenseThreads) * 32) {
+      uint4 w[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int64_t x = x0 + int64_t(u) * kDenseThreads * 4;
+        if (vec && x + 3 < khi) {
+          w[u] = __ldg(reinterpret_cast<const uint4*>(p.keys + x));  // kept for tie_dplace
+        } else {
+          w[u].x = x < khi ? p.keys[x] : 0u;
+          w[u].y = x + 1 < khi ? p.keys[x + 1] : 0u;
+          w[u].z = x + 2 < khi ? p.keys[x + 2] : 0u;
+          w[u].w = x + 3 < khi ? p.keys[x + 3] : 0u;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int64_t x = x0 + int64_t(u) * kDenseThreads * 4;
+        c += (x < khi && map_key<DT>(w[u].x) == tau) ? 1u : 0u;
+        c += (x + 1 < khi && map_key<DT>(w[u].y) == tau) ? 1u : 0u;
+        c += (x + 2 < khi && map_key<DT>(w[u].z) == tau) ? 1u : 0u;
+        c += (x + 3 < khi && map_key<DT>(w[u].w) == tau) ? 1u : 0u;
+      }
+    }
+    c = __reduce_add_sync(0xFFFFFFFFu, c);
+    if (lane_id() == 0) s_w[tid >> 5] = c;
+    __syncthreads();
+    if (tid < 32) {
+      uint32_t tot = __reduce_add_sync(0xFFFFFFFFu, s_w[tid]);
+      if (tid == 0) {
+        p.tstat[j] = tot;
+        __threadfence();
+        atomicAdd(&ctl->tie_sum, tot);
+        read_subs += static_cast<uint32_t>((khi - klo + (int64_t(1) << p.alpha) - 1) >> p.alpha);
+      }
+    }
+    __syncthreads();
+  }
+  tie_finish(p, read_subs, 0u);
+}
+
+template <int DT>
+__global__ void __launch_bounds__(kDenseThreads) tie_dplace_kernel(TieParams p) {
   Ctl* ctl = p.ctl;
   if (__ldcg(&ctl->mode) != kModeTies || __ldcg(&ctl->tie_dense) == 0) return;
   const uint32_t tau = __ldcg(&ctl->tau);
   const uint32_t need = __ldcg(&ctl->need);
   const uint32_t g = __ldcg(&ctl->g_count);
-  const int64_t nl = __ldcg(&ctl->tie_nlist);
+  const int64_t cut = ~__ldcg(&ctl->tie_cut_inv);
+  const int64_t nl = imin64(__ldcg(&ctl->tie_nlist), cut);
   tie_copy_g(p, g);
-  extern __shared__ __align__(128) unsigned char tbuf[];  // kTieBufBytes
-  __shared__ TieTileSmem sm;
-  __shared__ __align__(8) uint64_t s_bar;
-  __shared__ int64_t s_j, s_t;
-  __shared__ uint32_t s_clean, s_go, s_E, s_shift;
+  __shared__ uint32_t s_bits[kTieMaxSeg];
+  __shared__ uint32_t s_pre[kTieMaxSeg];
+  constexpr int kWarpsD = kDenseThreads / 32;
+  constexpr int kInFlight = 32;  // segments per warp per round: a 32768-key tile in one
   const int tid = threadIdx.x;
-  const uint32_t lane = lane_id();
   const int warp = tid >> 5;
-  const uint64_t pol = l2_evict_first_policy();
-  if (tid == 0) {
-    mbar_init(&s_bar, 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-  uint32_t phase = 0, read_subs = 0, emitted = 0;
-  for (;;) {
-    if (tid == 0) {
-      const int64_t j = atomicAdd(&ctl->tie_ticket, 1u);
-      s_j = j;
-      s_go = 0;
-      if (j < nl) {
-        const uint32_t e = p.list[j];
-        s_t = e & ~kTieInexact;
-        s_clean = (e & kTieInexact) ? 1u : 0u;
-        s_go = (s_t <= static_cast<int64_t>(~__ldcg(&ctl->tie_cut_inv))) ? 1u : 0u;
+  const uint32_t lane = lane_id();
+  const uint32_t lt = lanemask_lt();
+  uint32_t emitted = 0;
+  for (int64_t j = blockIdx.x; j < nl; j += gridDim.x) {
+    int64_t klo, khi;
+    tie_tile_range(p, p.list[j] & ~kTieInexact, &klo, &khi);
+    const uint32_t E = static_cast<uint32_t>(p.tstat[j]);
+    const int nseg = static_cast<int>((khi - klo + 31) >> 5);
+    // segment warp + kWarpsD * q of the tile (all warps, interleaved)
+    for (int q0 = 0; q0 * kWarpsD < nseg; q0 += kInFlight) {
+      uint32_t v[kInFlight];
+#pragma unroll
+      for (int q = 0; q < kInFlight; ++q) {
+        const int64_t x = klo + int64_t(warp + kWarpsD * (q0 + q)) * 32 + lane;
+        v[q] = x < khi ? __ldcs(p.keys + x) : 0u;
+      }
+#pragma unroll
+      for (int q = 0; q < kInFlight; ++q) {
+        const int sg = warp + kWarpsD * (q0 + q);
+        const int64_t x = klo + int64_t(sg) * 32 + lane;
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, x < khi && map_key<DT>(v[q]) == tau);
+        if (lane == 0 && sg < nseg) s_bits[sg] = bal;
       }
     }
     __syncthreads();
-    if (!s_go) break;
-    const int64_t j = s_j, t = s_t;
-    bool timed_out;
-    const uint32_t tot = tie_tile_count<DT, B, true, kWalkThreads>(p, t, tau, sm, tbuf, &s_bar,
-                                                                   phase, pol, &s_shift, read_subs,
-                                                                   &timed_out);
-    if (timed_out) break;
-    if (warp == 0) {
-      const uint32_t corr = tot - tlb_lb(p.tlb[t]);
-      uint32_t C = 0;
-      bool skip = false;
-      if (s_clean) {
-        if (lane == 0) st_relaxed_u64(&p.tstat[j], kTieIncl | corr);
-      } else {
-        if (lane == 0) st_relaxed_u64(&p.tstat[j], kTieAgg | corr);
-        int64_t base = j - 1;
-        uint32_t spins = 0;
-        for (;;) {
-          const int64_t idx = base - lane;
-          const uint64_t v = idx >= 0 ? ld_relaxed_u64(&p.tstat[idx]) : kTieIncl;
-          const uint64_t f = v & ~uint64_t(0xFFFFFFFFu);
-          const uint32_t ready = __ballot_sync(0xFFFFFFFFu, f != 0);
-          const uint32_t incl = __ballot_sync(0xFFFFFFFFu, f == kTieIncl);
-          if (incl) {
-            const int L = __ffs(incl) - 1;  // nearest inclusive word
-            const uint32_t upto = (L == 31) ? 0xFFFFFFFFu : ((2u << L) - 1u);
-            if ((ready & upto) == upto) {
-              C += __reduce_add_sync(0xFFFFFFFFu,
-                                     static_cast<int>(lane) <= L ? static_cast<uint32_t>(v) : 0u);
-              break;
-            }
-          } else if (ready == 0xFFFFFFFFu) {
-            C += __reduce_add_sync(0xFFFFFFFFu, static_cast<uint32_t>(v));
-            base -= 32;
-            continue;
-          }
-          // a word not yet published: a tile past the cut may never publish
-          // (the decision is warp-uniform: any lane that sees the cut)
-          const bool past =
-              __any_sync(0xFFFFFFFFu, t > static_cast<int64_t>(~__ldcg(&ctl->tie_cut_inv)));
-          if (past || ++spins > kTieSpin) {
-            if (spins > kTieSpin && lane == 0) atomicOr(&ctl->error, kErrTimeout);
-            skip = true;
-            break;
-          }
+    // exclusive prefixes of the segment counts (2 consecutive per thread)
+    const uint32_t c0 = 2 * tid < nseg ? __popc(s_bits[2 * tid]) : 0u;
+    const uint32_t c1 = 2 * tid + 1 < nseg ? __popc(s_bits[2 * tid + 1]) : 0u;
+    const uint32_t ex = block_scan_excl<kDenseThreads>(c0 + c1, nullptr);
+    if (2 * tid < nseg) s_pre[2 * tid] = ex;
+    if (2 * tid + 1 < nseg) s_pre[2 * tid + 1] = ex + c0;
+    __syncthreads();
+    for (int sg = warp; sg < nseg; sg += kDenseThreads / 32) {
+      const uint32_t bits = s_bits[sg];
+      const uint32_t r0 = E + s_pre[sg];
+      if (bits == 0 || r0 >= need) continue;
+      if ((bits >> lane) & 1u) {
+        const uint32_t r = r0 + __popc(bits & lt);
+        if (r < need) {
+          p.w[g + r] = make_comp(tau, static_cast<uint32_t>(klo + int64_t(sg) * 32 + lane));
+          ++emitted;
         }
-        if (!skip && lane == 0) st_relaxed_u64(&p.tstat[j], kTieIncl | (C + corr));
-      }
-      if (lane == 0) {
-        const uint32_t E = p.lbpre[t] + C;
-        if (!skip && E >= need) atomicMax(&ctl->tie_cut_inv, ~static_cast<uint32_t>(t));
-        s_E = skip ? need : E;
       }
     }
-    __syncthreads();
-    const uint32_t E = s_E;
-    if (E < need) tie_tile_emit<DT, B, kWalkThreads>(p, t, tau, need, g, E, sm, emitted);
-    __syncthreads();
+    __syncthreads();  // the bitmasks are rebuilt for the next tile
   }
-  tie_finish(p, read_subs, emitted);
+  tie_finish(p, 0u, emitted);
 }
 
 // Sparse ties work per tile on its few "interesting" subranges (ties among
@@ -1610,11 +1426,11 @@ __global__ void __launch_bounds__(kThreads, 4) tie_count_kernel(TieParams p) {
   }
 }
 
-// Sparse ties, step 2 (one block): exclusive prefixes of the tiles' exact
-// counts in list order (in place), and the cut.
+// Ties, step 2 (one block, dense and sparse): exclusive prefixes of the
+// tiles' exact counts in list order (in place), and the cut.
 __global__ void __launch_bounds__(1024) tie_scan_kernel(TieParams p) {
   Ctl* ctl = p.ctl;
-  if (__ldcg(&ctl->mode) != kModeTies || __ldcg(&ctl->tie_dense) != 0) return;
+  if (__ldcg(&ctl->mode) != kModeTies) return;
   const uint32_t need = __ldcg(&ctl->need);
   const int64_t nl = __ldcg(&ctl->tie_nlist);
   constexpr int kPer = kTiePlanChunk / 1024;
@@ -1909,16 +1725,15 @@ cudaError_t launch_ties(const Work& w, const void* keys, int sms, cudaStream_t s
   const int64_t lb_chunks = (p.S + std::max<int64_t>(p.tsub, 32) - 1) / std::max<int64_t>(p.tsub, 32);
   const int ga = static_cast<int>(
       std::min<int64_t>((lb_chunks + kThreads / 32 - 1) / (kThreads / 32), int64_t(sms) * 8));
-  const int gc = static_cast<int>(std::min<int64_t>(p.ntiles, int64_t(sms)));
+  const int gd = static_cast<int>(std::min<int64_t>(p.ntiles, int64_t(sms) * 2));
   const int gs = static_cast<int>(std::min<int64_t>(p.ntiles, int64_t(sms) * 4));
 #define DRTOPK_TIE_CASE(DTV, BV)                                                       \
   tie_lb_kernel<BV><<<ga, kThreads, 0, s>>>(p);                                        \
   tie_plan_kernel<<<1, 1024, 0, s>>>(p);                                               \
-  cudaFuncSetAttribute(tie_walk_kernel<DTV, BV>,                                       \
-                       cudaFuncAttributeMaxDynamicSharedMemorySize, kTieBufBytes);     \
-  tie_walk_kernel<DTV, BV><<<gc, kWalkThreads, kTieBufBytes, s>>>(p);                  \
+  tie_dcount_kernel<DTV><<<gd, kDenseThreads, 0, s>>>(p);                              \
   tie_count_kernel<DTV, BV><<<gs, kThreads, 0, s>>>(p);                                \
   tie_scan_kernel<<<1, 1024, 0, s>>>(p);                                               \
+  tie_dplace_kernel<DTV><<<gd, kDenseThreads, 0, s>>>(p);                              \
   tie_place_kernel<DTV, BV><<<gs, kThreads, 0, s>>>(p);
 #define DRTOPK_TIE_BETA(DTV)                    \
   switch (w.beta) {                             \
@@ -1938,7 +1753,7 @@ cudaError_t launch_ties(const Work& w, const void* keys, int sms, cudaStream_t s
   }
 #undef DRTOPK_TIE_BETA
 #undef DRTOPK_TIE_CASE
-  note_launch(6);
+  note_launch(7);
   return cudaGetLastError();
 }
 
