@@ -96,6 +96,12 @@ struct SelState {
   uint64_t prefix;   // resolved digits, most significant first, left-aligned
 };
 
+// Capacities of the direct tie path's lists (Ctl::ts, tc) and the largest
+// set of scanned subranges it reads again.
+constexpr uint32_t kTieSCap = 1024;
+constexpr uint32_t kTieCandCap = 1024;
+constexpr uint32_t kTieScanMax = 4096;
+
 // Control block of one query, zeroed by the host before the first launch.
 struct Ctl {
   SelState<4> dsel;  // threshold select over the delegate keys
@@ -139,6 +145,15 @@ struct Ctl {
   uint32_t scan_ticket;
   uint32_t fhist[2048];      // keys > tau by their 11 bits below the common prefix
   uint32_t tie_sum;          // ties counted so far by the dense tie count
+  // direct tie path: where ties at tau can be, collected by the filter
+  uint32_t ts_count;         // subranges outside the scan holding a delegate == tau
+  uint32_t tc_count;         // positions of keys equal to tau found
+  uint32_t tie_fast_bad;     // a list overflowed: use the tile pipeline
+  uint32_t tie_fast;         // the ties were placed directly
+  uint32_t tie_reads;        // subranges read for the direct tie path
+  uint32_t tie_dticket;
+  uint32_t ts[kTieSCap];     // subranges
+  uint32_t tc[kTieCandCap];  // positions
 };
 
 // First digit level (byte of the (key, ~idx) composite, 0 = top) that can

@@ -297,9 +297,38 @@ struct FilterParams {
   Ctl* ctl;
   uint32_t* rq;   // delegates > tau to place: subrange << 2 | delegate slot
   int64_t rq_cap;
+  uint64_t* w;    // winners (top-k only): the direct tie path writes its ties
   int kth_only;
   int no_filter;  // ablation: Rule 2 off
 };
+
+// The direct tie path is tried for top-k with Rule 2's filtering as stated.
+__device__ __forceinline__ bool tie_direct_on(const FilterParams& p) {
+  return !p.kth_only && !p.no_filter;
+}
+
+
+// Appends this lane's value (when `has`) to one of the direct tie path's
+// capped lists, one atomic per warp (all lanes call it). Past the cap the
+// entry is dropped, tie_fast_bad is set and `stop` makes the warp skip its
+// later appends.
+__device__ __forceinline__ void tie_append(bool has, uint32_t v, uint32_t* count, uint32_t* buf,
+                                           uint32_t cap, Ctl* ctl, bool& stop) {
+  const uint32_t m = __ballot_sync(0xFFFFFFFFu, has && !stop);
+  if (m == 0) return;
+  const int leader = __ffs(m) - 1;
+  uint32_t base = 0;
+  if (static_cast<int>(lane_id()) == leader) base = atomicAdd(count, __popc(m));
+  base = __shfl_sync(0xFFFFFFFFu, base, leader);
+  if (base + __popc(m) > cap) {
+    stop = true;
+    if (static_cast<int>(lane_id()) == leader) ctl->tie_fast_bad = 1;
+  }
+  if ((m >> lane_id()) & 1u) {
+    const uint32_t slot = base + __popc(m & lanemask_lt());
+    if (slot < cap) buf[slot] = v;
+  }
+}
 
 // Each thread classifies 4 subranges per step: skip (m^0 <= tau), queue
 // for a scan (m^{beta-1} > tau: Rule 3 says every element may qualify) or
@@ -589,6 +618,147 @@ struct ScanQ {
     return (int64_t(s[buf][(v >> alpha) - (b >> alpha)]) << alpha) + (v & ((int64_t(1) << alpha) - 1));
   }
 };
+
+// Direct tie path, placement (block-wide, in the last block of the
+// collection kernel below): every key equal to tau was listed (delegates
+// equal to tau, keys of the subranges read); when the lists did not
+// overflow, the `need` smallest positions go to W after G in index order
+// (rank = number of listed positions below), and the tile pipeline of the
+// tie path is skipped.
+__device__ __noinline__ void tie_direct(Ctl* ctl, uint64_t* w) {
+  __shared__ uint32_t s_pos[kTieCandCap];
+  if (__ldcg(&ctl->mode) != kModeTies || __ldcg(&ctl->tie_fast_bad)) return;  // uniform
+  const uint32_t T = __ldcg(&ctl->tc_count);
+  const uint32_t need = __ldcg(&ctl->need);
+  if (T > kTieCandCap || T < need) return;  // uniform; the tile pipeline decides
+  const uint32_t g = __ldcg(&ctl->g_count);
+  const uint32_t tau = __ldcg(&ctl->tau);
+  for (uint32_t e = threadIdx.x; e < T; e += blockDim.x) s_pos[e] = __ldcg(&ctl->tc[e]);
+  __syncthreads();
+  for (uint32_t e = threadIdx.x; e < T; e += blockDim.x) {
+    const uint32_t pe = s_pos[e];
+    uint32_t rank = 0;
+    for (uint32_t f = 0; f < T; ++f) rank += s_pos[f] < pe ? 1u : 0u;
+    if (rank < need) w[g + rank] = make_comp(tau, pe);
+  }
+  if (threadIdx.x == 0) {
+    ctl->tie_fast = 1;
+    atomicAdd(&ctl->w_count, need);
+    const uint32_t nr = __ldcg(&ctl->tie_reads);
+    if (nr) atomicAdd(&ctl->tie_scanned, nr);
+  }
+}
+
+// Direct tie path, step 1 (after the filter, mode ties only): the
+// subranges outside the scan that hold a delegate equal to tau, from one
+// pass over the delegate keys. Skipped from the start when the threshold
+// select counted more delegates equal to tau than the list can take
+// (dense ties: the tile pipeline takes them).
+template <int B>
+__global__ void __launch_bounds__(kThreads) filter_tfind_kernel(FilterParams p) {
+  Ctl* ctl = p.ctl;
+  if (!tie_direct_on(p) || __ldcg(&ctl->mode) != kModeTies) return;
+  if (__ldcg(&ctl->tau_ready) &&
+      uint64_t(__ldcg(&ctl->dsel.bucket)) > uint64_t(kTieSCap) * B) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->tie_fast_bad = 1;
+    return;
+  }
+  const uint32_t tau = __ldcg(&ctl->tau);
+  bool tstop = false;
+  for (int64_t b0 = int64_t(blockIdx.x) * kThreads + (threadIdx.x & ~31u); b0 < p.S && !tstop;
+       b0 += int64_t(gridDim.x) * kThreads) {
+    const int64_t i = b0 + lane_id();
+    bool in = false;
+    if (i < p.S) {
+      uint32_t dk[B];
+      load_dkeys<B>(p.dkeys, i, dk);
+      bool eq = false;
+#pragma unroll
+      for (int j = 0; j < B; ++j) eq |= dk[j] == tau;
+      const bool scanned = dk[B - 1] > tau && sub_len(i, p.alpha, p.n) > B;
+      in = eq && !scanned;
+    }
+    tie_append(in, static_cast<uint32_t>(i), &ctl->ts_count, ctl->ts, kTieSCap, ctl, tstop);
+  }
+}
+
+// Direct tie path, step 2 (one warp per subrange): every key equal to tau
+// lies in a listed subrange (one holding a delegate equal to tau, outside
+// the scan) or in a scanned one. A listed subrange whose beta-th delegate is below
+// tau (or that holds at most beta keys) has all its ties among its
+// delegates: each is placed by a vote over its 32-key segment; any other
+// listed subrange, and every scanned one, is read whole (8 loads per lane
+// in flight). Positions go to Ctl::tc; an overflow leaves the ties to the
+// tile pipeline. The last block ranks the positions (tie_direct).
+template <int DT, int B>
+__global__ void __launch_bounds__(kThreads) filter_ties_kernel(FilterParams p) {
+  Ctl* ctl = p.ctl;
+  if (!tie_direct_on(p) || __ldcg(&ctl->mode) != kModeTies || __ldcg(&ctl->tie_fast_bad)) return;
+  const int64_t nts = __ldcg(&ctl->ts_count);
+  const int64_t nsc = __ldcg(&ctl->scanq_count);
+  if (nsc > kTieScanMax) return;  // uniform: the tile pipeline takes the ties
+  const uint32_t tau = __ldcg(&ctl->tau);
+  const int alpha = p.alpha;
+  const uint32_t lane = lane_id();
+  const int64_t gw = (int64_t(blockIdx.x) * kThreads + threadIdx.x) >> 5;
+  const int64_t nw = int64_t(gridDim.x) * (kThreads / 32);
+  bool tstop = false;
+  uint32_t reads = 0;
+  for (int64_t e = gw; e < nts + nsc && !tstop; e += nw) {
+    const int64_t i = e < nts ? __ldcg(&ctl->ts[e]) : __ldg(p.scanq + (e - nts));
+    const int64_t lo = i << alpha;
+    const int64_t len = sub_len(i, alpha, p.n);
+    uint32_t dk[B];
+    uint16_t ds[B];
+    bool rd = e >= nts;
+    if (!rd) {
+#pragma unroll
+      for (int z = 0; z < B; ++z) {
+        dk[z] = p.dkeys[i * B + z];
+        ds[z] = p.dsegs[i * B + z];
+      }
+      rd = dk[B - 1] == tau && len > B;
+    }
+    if (rd) {
+      ++reads;
+      for (int64_t off = 0; off < len && !tstop; off += 256) {
+        uint32_t x[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int64_t o = off + q * 32 + lane;
+          x[q] = o < len ? __ldg(p.keys + lo + o) : 0u;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int64_t o = off + q * 32 + lane;
+          tie_append(o < len && map_key<DT>(x[q]) == tau, static_cast<uint32_t>(lo + o),
+                     &ctl->tc_count, ctl->tc, kTieCandCap, ctl, tstop);
+        }
+      }
+    } else {
+      // the delegates equal to tau: the occurrence-th such key of the segment
+      const int64_t gran = alpha < 5 ? (int64_t(1) << alpha) : 32;
+#pragma unroll
+      for (int j = 0; j < B; ++j) {
+        if (j < len && dk[j] == tau) {  // uniform over the warp
+          int occ = 0;
+#pragma unroll
+          for (int z = 0; z < B; ++z) occ += (z < j && dk[z] == tau && ds[z] == ds[j]) ? 1 : 0;
+          const int64_t s0 = lo + int64_t(ds[j]) * gran;
+          const int64_t s1 = imin64(imin64(p.n, s0 + gran), lo + (int64_t(1) << alpha));
+          uint32_t bal = __ballot_sync(
+              0xFFFFFFFFu, s0 + lane < s1 && map_key<DT>(__ldg(p.keys + s0 + lane)) == tau);
+          for (int z = 0; z < occ; ++z) bal &= bal - 1;
+          if (bal == 0 && lane == 0) atomicOr(&ctl->error, kErrTieRank);
+          tie_append(lane == 0 && bal != 0, static_cast<uint32_t>(s0 + __ffs(bal) - 1),
+                     &ctl->tc_count, ctl->tc, kTieCandCap, ctl, tstop);
+        }
+      }
+    }
+  }
+  if (lane == 0 && reads) atomicAdd(&ctl->tie_reads, reads);
+  if (last_block(&ctl->tie_dticket)) tie_direct(ctl, p.w);
+}
 
 // Counting pass over a large scan set (two_pass_wanted): the keys > tau by
 // their fine digit (with the delegates the resolve kernel placed, already
@@ -988,7 +1158,7 @@ __device__ __forceinline__ uint32_t tie_lb_of(const TieParams& p, int64_t i, uin
 template <int B>
 __global__ void __launch_bounds__(kThreads) tie_lb_kernel(TieParams p) {
   Ctl* ctl = p.ctl;
-  if (__ldcg(&ctl->mode) != kModeTies) return;
+  if (__ldcg(&ctl->mode) != kModeTies || __ldcg(&ctl->tie_fast)) return;
   const uint32_t tau = __ldcg(&ctl->tau);
   const uint32_t lane = lane_id();
   constexpr int kU = 8;
@@ -1045,7 +1215,7 @@ __global__ void __launch_bounds__(kThreads) tie_lb_kernel(TieParams p) {
 // global reads and writes); each thread scans 8 consecutive tiles of a chunk.
 __global__ void __launch_bounds__(1024) tie_plan_kernel(TieParams p) {
   Ctl* ctl = p.ctl;
-  if (__ldcg(&ctl->mode) != kModeTies) return;
+  if (__ldcg(&ctl->mode) != kModeTies || __ldcg(&ctl->tie_fast)) return;
   const uint32_t need = __ldcg(&ctl->need);
   constexpr int kPer = kTiePlanChunk / 1024;
   __shared__ uint32_t buf[kTiePlanChunk + kTiePlanChunk / 32];  // padded: no bank conflicts
@@ -1414,7 +1584,8 @@ __device__ uint32_t tie_sparse_tile(const TieParams& p, int64_t t, uint32_t tau,
 template <int DT, int B>
 __global__ void __launch_bounds__(kThreads, 4) tie_count_kernel(TieParams p) {
   Ctl* ctl = p.ctl;
-  if (__ldcg(&ctl->mode) != kModeTies || __ldcg(&ctl->tie_dense) != 0) return;
+  if (__ldcg(&ctl->mode) != kModeTies || __ldcg(&ctl->tie_dense) != 0 || __ldcg(&ctl->tie_fast))
+    return;
   const uint32_t tau = __ldcg(&ctl->tau);
   const int64_t nl = __ldcg(&ctl->tie_nlist);
   __shared__ TieSparseSmem sm;
@@ -1430,7 +1601,7 @@ __global__ void __launch_bounds__(kThreads, 4) tie_count_kernel(TieParams p) {
 // tiles' exact counts in list order (in place), and the cut.
 __global__ void __launch_bounds__(1024) tie_scan_kernel(TieParams p) {
   Ctl* ctl = p.ctl;
-  if (__ldcg(&ctl->mode) != kModeTies) return;
+  if (__ldcg(&ctl->mode) != kModeTies || __ldcg(&ctl->tie_fast)) return;
   const uint32_t need = __ldcg(&ctl->need);
   const int64_t nl = __ldcg(&ctl->tie_nlist);
   constexpr int kPer = kTiePlanChunk / 1024;
@@ -1486,6 +1657,10 @@ template <int DT, int B>
 __global__ void __launch_bounds__(kThreads, 4) tie_place_kernel(TieParams p) {
   Ctl* ctl = p.ctl;
   if (__ldcg(&ctl->mode) != kModeTies || __ldcg(&ctl->tie_dense) != 0) return;
+  if (__ldcg(&ctl->tie_fast)) {  // ties placed by the filter: G goes in front
+    tie_copy_g(p, __ldcg(&ctl->g_count));
+    return;
+  }
   const uint32_t tau = __ldcg(&ctl->tau);
   const uint32_t need = __ldcg(&ctl->need);
   const uint32_t g = __ldcg(&ctl->g_count);
@@ -1632,7 +1807,8 @@ cudaError_t launch_threshold(const Work& w, int sms, cudaStream_t s) {
 }
 
 template <int DT, int B>
-static void filter_t(const FilterParams& p, int g1, int g2, int g3, cudaStream_t s) {
+static void filter_t(const FilterParams& p, int g1, int g2, int g3, int g4, int g5,
+                     cudaStream_t s) {
   filter_classify_kernel<DT, B><<<g1, kThreads, 0, s>>>(p);
   filter_resolve_kernel<DT, B><<<g3, kThreads, 0, s>>>(p);
   if ((reinterpret_cast<uintptr_t>(p.keys) & 15u) == 0) {
@@ -1642,6 +1818,8 @@ static void filter_t(const FilterParams& p, int g1, int g2, int g3, cudaStream_t
     filter_count_kernel<DT, false><<<g2, kThreads, 0, s>>>(p);
     filter_scan_kernel<DT, false><<<g2, kThreads, 0, s>>>(p);
   }
+  filter_tfind_kernel<B><<<g5, kThreads, 0, s>>>(p);
+  filter_ties_kernel<DT, B><<<g4, kThreads, 0, s>>>(p);
 }
 
 cudaError_t launch_filter(const Work& w, const void* keys, bool kth_only, int sms,
@@ -1662,17 +1840,21 @@ cudaError_t launch_filter(const Work& w, const void* keys, bool kth_only, int sm
   p.no_filter = (w.ablate & kAblateNoFilter) ? 1 : 0;
   p.rq = w.rq;
   p.rq_cap = w.rq_cap;
+  p.w = w.w;
   const int g1 = grid_for(w.S, kThreads, sms, 8);
   // requests to resolve: at most rq_cap, one per thread per block step
   const int g3 = grid_for(w.rq_cap, kThreads, sms, 4);
   // scanned keys are bounded by the G capacity (or n when tau = 0)
   const int g2 = grid_for(w.g_cap, kScanStep, sms, 6);
+  // direct tie path: a warp per listed or scanned subrange
+  const int g4 = grid_for(int64_t(kTieSCap) + kTieScanMax, kThreads / 32, sms, 1);
+  const int g5 = grid_for(w.S, kThreads, sms, 4);
 #define DRTOPK_FILTER_CASE(DTV)                              \
   switch (w.beta) {                                          \
-    case 1: filter_t<DTV, 1>(p, g1, g2, g3, s); break;       \
-    case 2: filter_t<DTV, 2>(p, g1, g2, g3, s); break;       \
-    case 3: filter_t<DTV, 3>(p, g1, g2, g3, s); break;       \
-    default: filter_t<DTV, 4>(p, g1, g2, g3, s); break;      \
+    case 1: filter_t<DTV, 1>(p, g1, g2, g3, g4, g5, s); break;       \
+    case 2: filter_t<DTV, 2>(p, g1, g2, g3, g4, g5, s); break;       \
+    case 3: filter_t<DTV, 3>(p, g1, g2, g3, g4, g5, s); break;       \
+    default: filter_t<DTV, 4>(p, g1, g2, g3, g4, g5, s); break;      \
   }
   switch (w.dtype) {
     case DRTOPK_U32: DRTOPK_FILTER_CASE(DRTOPK_U32); break;
@@ -1684,7 +1866,7 @@ cudaError_t launch_filter(const Work& w, const void* keys, bool kth_only, int sm
     default: return cudaErrorInvalidValue;
   }
 #undef DRTOPK_FILTER_CASE
-  note_launch(4);
+  note_launch(6);
   return cudaGetLastError();
 }
 
