@@ -810,11 +810,13 @@ def main():
         stage = torch.empty(n, dtype=torch.int32, device=dev)
         stage.copy_(hosts[dists[0]], non_blocking=True)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for d in dists:
-            stage.copy_(hosts[d], non_blocking=True)
-        torch.cuda.synchronize()
-        link_gbs = 4.0 * n * len(dists) / (time.perf_counter() - t0) / 1e9
+        link_gbs = 0.0
+        for _ in range(2):  # best of two rounds
+            t0 = time.perf_counter()
+            for d in dists:
+                stage.copy_(hosts[d], non_blocking=True)
+            torch.cuda.synchronize()
+            link_gbs = max(link_gbs, 4.0 * n * len(dists) / (time.perf_counter() - t0) / 1e9)
         del stage
         torch.cuda.empty_cache()
 
@@ -823,7 +825,8 @@ def main():
                 for k in ks:
                     drtopk.drtopk_topk_host_ptr(hosts[d].data_ptr(), n, k, "u32",
                                                 hk[k][0].data_ptr(), hk[k][1].data_ptr())
-        estep()
+        for _ in range(2):  # warm-up rounds (the first calls after set-up are slower)
+            estep()
         esteps = max(2, min(args.steps, 5))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -834,9 +837,11 @@ def main():
         out["e2e"] = {"value": float(n) * queries * esteps / et / 1e9, "unit": "Gkeys/s",
                       "h2d_bytes_per_step": 4 * n * queries,
                       "d2h_bytes_per_step": 8 * sum(ks) * len(dists),
-                      "steps": esteps, "api": "drtopk_topk_host (pinned host keys)",
+                      "steps": esteps, "api": "drtopk_topk_host (pinned host keys; copies in "
+                      "~128 MB pieces overlapped with the delegate pass)",
                       "h2d_link_gbs": link_gbs,
-                      "link_bound_gkeys": link_gbs / 4.0}
+                      "link_bound_gkeys": link_gbs / 4.0,
+                      "frac_of_link_bound": (float(n) * queries * esteps / et / 1e9) / (link_gbs / 4.0)}
 
     print(json.dumps(out))
 

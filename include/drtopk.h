@@ -282,13 +282,17 @@ drtopk_status drtopk_kth_noalloc(const void* keys, drtopk_dtype dtype,
 
 /*
  * top-k of a HOST array: copies keys (host, pinned or pageable) to the
- * device, runs drtopk_topk and copies the results back to host out_keys /
- * out_idx. Synchronous: returns when the host outputs are written.
- * The device copy goes to a staging buffer the library keeps per device,
- * grown to the largest call so far (n * 4 + 2 k * 4 bytes, 256-byte
- * aligned parts) and held until the process exits; repeated calls reuse
- * it, and with it the cached graph of the query. Calls on one device are
- * serialised on that buffer.
+ * device, computes what drtopk_topk computes and copies the results back to
+ * host out_keys / out_idx. Synchronous: returns when the host outputs are
+ * written. The keys travel in pieces of whole subranges (about 128 MB) on a
+ * copy stream of the library; the delegate pass of each piece runs on
+ * `stream` as soon as that piece has landed, while the later pieces are
+ * still in flight, and the rest of the query follows the last piece. The
+ * device copy goes to a staging buffer the library keeps per device, grown
+ * to the largest call so far (n * 4 + 2 k * 4 bytes, 256-byte aligned
+ * parts) and held until the process exits. Calls on one device are
+ * serialised on that buffer. With pageable host memory the copies do not
+ * overlap the kernels.
  */
 drtopk_status drtopk_topk_host(const void* keys, drtopk_dtype dtype,
                                int64_t n, int64_t k, void* out_keys,

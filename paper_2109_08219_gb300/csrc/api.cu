@@ -129,11 +129,17 @@ namespace {
 // host-mapped word that the last kernel of every query ORs its error flags
 // into, read and cleared by the next call on the device or by
 // drtopk_sync_status.
+constexpr int kHostChunks = 64;  // copy pieces of one drtopk_topk_host call at most
 struct DevInfo {
   int sms = 0;
   cudaMemPool_t pool = nullptr;
   uint32_t* err_host = nullptr;  // mapped pinned host word
   uint32_t* err_dev = nullptr;   // its device address
+  // drtopk_topk_host: the copy stream and one event per piece (plus one
+  // ordering the copies after the caller's earlier work); created on first
+  // use, guarded by the device's staging lock
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t copy_ev[kHostChunks + 1] = {};
 };
 std::mutex g_dev_mu;
 DevInfo g_dev[64];
@@ -252,17 +258,11 @@ drtopk_status check_args(const void* keys, int dtype, int64_t n, int64_t k) {
     }                                            \
   } while (0)
 
-// Every launch of one query, in order, on stream s (no allocation, no sync).
-cudaError_t enqueue_query(const Work& w, const Plan& P, const void* keys, bool topk,
-                          void* out_keys, int32_t* out_idx, void* out_kth, int sms,
-                          cudaStream_t s, StageTimer& tm) {
-  cudaError_t e = cudaMemsetAsync(w.ctl, 0, sizeof(Ctl), s);
-  if (e != cudaSuccess) return e;
-  tm.begin(0);
-  e = launch_delegates(w, keys, P.fuse_hist, sms, s);
-  note_launch();
-  tm.end();
-  if (e != cudaSuccess) return e;
+// The launches of one query after its delegate pass, in order, on stream s.
+cudaError_t enqueue_after_delegates(const Work& w, const Plan& P, const void* keys, bool topk,
+                                    void* out_keys, int32_t* out_idx, void* out_kth, int sms,
+                                    cudaStream_t s, StageTimer& tm) {
+  cudaError_t e = cudaSuccess;
   if (P.fuse_hist) {
     tm.begin(1);
     e = launch_threshold(w, sms, s);
@@ -290,6 +290,19 @@ cudaError_t enqueue_query(const Work& w, const Plan& P, const void* keys, bool t
     tm.end();
   }
   return e;
+}
+
+// Every launch of one query, in order, on stream s (no allocation, no sync).
+cudaError_t enqueue_query(const Work& w, const Plan& P, const void* keys, bool topk,
+                          void* out_keys, int32_t* out_idx, void* out_kth, int sms,
+                          cudaStream_t s, StageTimer& tm) {
+  cudaError_t e = cudaMemsetAsync(w.ctl, 0, sizeof(Ctl), s);
+  if (e != cudaSuccess) return e;
+  tm.begin(0);
+  e = launch_delegates(w, keys, P.fuse_hist, sms, s);
+  tm.end();
+  if (e != cudaSuccess) return e;
+  return enqueue_after_delegates(w, P, keys, topk, out_keys, out_idx, out_kth, sms, s, tm);
 }
 
 // ---------------------------------------------------------- graph cache ---
@@ -726,7 +739,6 @@ drtopk_status drtopk_delegates(const void* keys, drtopk_dtype dtype, int64_t n, 
   e = cudaMemsetAsync(w.ctl, 0, sizeof(Ctl), s);
   if (e == cudaSuccess) {
     e = launch_delegates(w, keys, false, sms, s);
-    note_launch();
   }
   if (e == cudaSuccess) e = launch_resolve_delegates(w, keys, d_idx, s);
   cudaError_t e2 = cudaFreeAsync(ws, s);
@@ -741,11 +753,17 @@ drtopk_status drtopk_topk_host(const void* keys, drtopk_dtype dtype, int64_t n, 
   if (!out_keys || !out_idx) return DRTOPK_ERR_INVALID;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return DRTOPK_ERR_CUDA;
+  int sms = 0;
+  DevInfo* dv = nullptr;
+  st = dev_info(&sms, &dv);
+  if (st != DRTOPK_OK) return st;
+  if (const uint32_t prev = take_errors(dv)) return error_status(prev);
+  Plan P;
+  if (!make_plan(n, k, 0, 0, &P)) return DRTOPK_ERR_INVALID;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t kb = al(static_cast<size_t>(n) * 4);
   const size_t ob = al(static_cast<size_t>(k) * 4);
-  // the device's staging buffer, grown to the largest call and kept: the
-  // same addresses every call, so the query replays a cached graph
+  // the device's staging buffer, grown to the largest call and kept
   HostStage& hs = g_hstage[dev];
   std::lock_guard<std::mutex> lk(hs.mu);
   if (hs.cap < kb + 2 * ob) {
@@ -763,26 +781,60 @@ drtopk_status drtopk_topk_host(const void* keys, drtopk_dtype dtype, int64_t n, 
     }
     hs.cap = kb + 2 * ob;
   }
-  char* d = hs.d;
-  cudaError_t e = cudaMemcpyAsync(d, keys, static_cast<size_t>(n) * 4, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) {
-    st = run_query(d, dtype, n, k, 0, 0, d + kb, reinterpret_cast<int32_t*>(d + kb + ob), nullptr,
-                   nullptr, s, true);
-    if (st == DRTOPK_OK) {
-      e = cudaMemcpyAsync(out_keys, d + kb, static_cast<size_t>(k) * 4, cudaMemcpyDeviceToHost, s);
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync(out_idx, d + kb + ob, static_cast<size_t>(k) * 4,
-                            cudaMemcpyDeviceToHost, s);
-    }
+  if (!dv->copy_stream) {
+    if (cudaStreamCreateWithFlags(&dv->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return DRTOPK_ERR_CUDA;
+    for (auto& ev : dv->copy_ev)
+      if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return DRTOPK_ERR_CUDA;
   }
-  cudaError_t e3 = cudaStreamSynchronize(s);
-  if (st != DRTOPK_OK) return st;
+  char* d = hs.d;
+  const char* h = static_cast<const char*>(keys);
+  const Layout L = layout(P, k, true, false);
+  char* ws = nullptr;
+  cudaError_t e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&ws), L.total, dv->pool, s);
+  note_alloc();
+  if (e != cudaSuccess) return cuda_status(e);
+  Work w;
+  bind_work(w, ws, L, P, n, k, dtype);
+  w.err_out = dv->err_dev;
+  // The keys go over in pieces of whole subranges (about 128 MB) on the
+  // copy stream; the delegate pass of piece c runs on `stream` as soon as
+  // piece c has landed, while the next pieces are still in flight. The rest
+  // of the query follows the last piece.
+  int64_t spc = std::max<int64_t>(1, (int64_t(32) << 20) >> P.alpha);  // subranges per piece
+  while ((P.S + spc - 1) / spc > kHostChunks) spc *= 2;
+  const int nc = static_cast<int>((P.S + spc - 1) / spc);
+  cudaStream_t cs = dv->copy_stream;
+  StageTimer tm(s, false);
+  e = cudaEventRecord(dv->copy_ev[kHostChunks], s);  // after the caller's earlier work
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, dv->copy_ev[kHostChunks], 0);
+  for (int c = 0; c < nc && e == cudaSuccess; ++c) {
+    const int64_t k0 = (int64_t(c) * spc) << P.alpha;
+    const int64_t k1 = std::min<int64_t>(n, (int64_t(c + 1) * spc) << P.alpha);
+    e = cudaMemcpyAsync(d + k0 * 4, h + k0 * 4, static_cast<size_t>(k1 - k0) * 4,
+                        cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaEventRecord(dv->copy_ev[c], cs);
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(w.ctl, 0, sizeof(Ctl), s);
+  for (int c = 0; c < nc && e == cudaSuccess; ++c) {
+    e = cudaStreamWaitEvent(s, dv->copy_ev[c], 0);
+    if (e == cudaSuccess)
+      e = launch_delegates_range(w, d, int64_t(c) * spc, std::min<int64_t>(P.S, int64_t(c + 1) * spc),
+                                 P.fuse_hist, c == nc - 1, sms, s);
+  }
+  if (e == cudaSuccess)
+    e = enqueue_after_delegates(w, P, d, true, d + kb, reinterpret_cast<int32_t*>(d + kb + ob),
+                                nullptr, sms, s, tm);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out_keys, d + kb, static_cast<size_t>(k) * 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out_idx, d + kb + ob, static_cast<size_t>(k) * 4, cudaMemcpyDeviceToHost, s);
+  const cudaError_t e2 = cudaFreeAsync(ws, s);
+  const cudaError_t e3 = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = e2;
   if (e == cudaSuccess) e = e3;
   if (e != cudaSuccess) return cuda_status(e);
   // synchronous: the query's device-side errors are reported here
-  int sms = 0;
-  DevInfo* dv = nullptr;
-  if (dev_info(&sms, &dv) != DRTOPK_OK) return DRTOPK_ERR_CUDA;
   return error_status(take_errors(dv));
 }
 

@@ -46,6 +46,7 @@ struct DelegParams {
   uint16_t* dsegs;
   Ctl* ctl;
   int fuse_hist;
+  int select_last;  // the launch's last block resolves the first threshold digit
   uint32_t k;
 };
 
@@ -299,7 +300,7 @@ __global__ void __launch_bounds__(kThreads, 2) delegate_kernel(DelegParams p) {
       const uint32_t v = sh_hist[i];
       if (v) atomicAdd(&p.ctl->dsel.hist[0][i], v);
     }
-    if (last_block(&p.ctl->dsel.ticket[0])) {
+    if (p.select_last && last_block(&p.ctl->dsel.ticket[0])) {
       if (warp == 0) {
         if (lane == 0) p.ctl->dsel.k_rem = p.k;
         __syncwarp();
@@ -342,18 +343,30 @@ cudaError_t launch_deleg_b(const DelegParams& p, int beta, bool tma, int sms, cu
 
 cudaError_t launch_delegates(const Work& w, const void* keys, bool fuse_hist, int sms,
                              cudaStream_t s) {
+  return launch_delegates_range(w, keys, 0, w.S, fuse_hist, true, sms, s);
+}
+
+cudaError_t launch_delegates_range(const Work& w, const void* keys, int64_t sub0, int64_t sub1,
+                                   bool fuse_hist, bool select_last, int sms, cudaStream_t s) {
+  // subranges [sub0, sub1) as an array of their own: keys and delegate
+  // slots offset by whole subranges (positions inside a subrange and the
+  // segments stored with the delegates do not change)
   DelegParams p;
-  p.keys = static_cast<const uint32_t*>(keys);
-  p.n = w.n;
-  p.S = w.S;
+  const int64_t k0 = sub0 << w.alpha;
+  p.keys = static_cast<const uint32_t*>(keys) + k0;
+  p.n = imin64(w.n, sub1 << w.alpha) - k0;
+  p.S = sub1 - sub0;
   p.alpha = w.alpha;
-  p.nchunks = (w.n + kChunkKeys - 1) / kChunkKeys;
-  p.dkeys = w.dkeys;
-  p.dsegs = w.dsegs;
+  p.nchunks = (p.n + kChunkKeys - 1) / kChunkKeys;
+  p.dkeys = w.dkeys + sub0 * w.beta;
+  p.dsegs = w.dsegs + sub0 * w.beta;
   p.ctl = w.ctl;
   p.fuse_hist = fuse_hist ? 1 : 0;
+  p.select_last = select_last ? 1 : 0;
   p.k = static_cast<uint32_t>(w.k);
-  const bool tma = (reinterpret_cast<uintptr_t>(keys) & 15u) == 0;
+  if (p.n <= 0 || p.S <= 0) return cudaErrorInvalidValue;
+  const bool tma = (reinterpret_cast<uintptr_t>(p.keys) & 15u) == 0;
+  note_launch();
   switch (w.dtype) {
     case DRTOPK_U32: return launch_deleg_b<DRTOPK_U32>(p, w.beta, tma, sms, s);
     case DRTOPK_I32: return launch_deleg_b<DRTOPK_I32>(p, w.beta, tma, sms, s);

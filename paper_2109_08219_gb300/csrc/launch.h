@@ -48,6 +48,11 @@ cudaError_t enqueue_query_plain(const Work& w, const Plan& P, const void* keys, 
 // the threshold select and resolve it in the last block.
 cudaError_t launch_delegates(const Work& w, const void* keys, bool fuse_hist, int sms,
                              cudaStream_t s);
+// The delegate pass over subranges [sub0, sub1) only (keys is the whole
+// array). The fused first-digit histogram accumulates over calls; only the
+// call with select_last resolves the digit (it must come last).
+cudaError_t launch_delegates_range(const Work& w, const void* keys, int64_t sub0, int64_t sub1,
+                                   bool fuse_hist, bool select_last, int sms, cudaStream_t s);
 
 // Threshold select passes 1..3 over the delegate keys (select.cu).
 cudaError_t launch_threshold(const Work& w, int sms, cudaStream_t s);

@@ -385,3 +385,16 @@ def test_output_sort_clustered_winners():
         st = check_topk(bits, "u32", k)
         assert st["greater"] >= k, st  # select mode: the sort covers all k
         check_topk(bits, "u32", k, alpha=4, beta=1)
+
+
+def test_host_entry_point_in_pieces():
+    """Host keys longer than one copy piece (32M keys): the delegate pass
+    runs piece by piece as the copies land; ragged last piece, tie-heavy and
+    distinct inputs, small and large k."""
+    n = (1 << 26) + 3 * (1 << 20) + 12345
+    for kind, ks in (("few", (1000, 300000)), ("uniform", (1, 1 << 20)), ("asc", (4096,))):
+        bits = make(kind, n, 77, "u32")
+        for k in ks:
+            ok, oi = drtopk.drtopk_topk_host(bits, k, "u32")
+            rk, ri = oracle.topk(bits, oracle.U32, k)
+            assert np.array_equal(ok, rk) and np.array_equal(oi, ri), (kind, k)
