@@ -384,7 +384,9 @@ def batched_measure(drtopk, inputs, dev, peak, rows=4096, reps=10):
 
     ok0, oi0 = time_plan("rule4")
     t0 = time.perf_counter()
-    drtopk.autotune_batched("f32", 12, 22, rows_per_shape=152)
+    # two rows per SM: at least one per CTA of the batched launch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    drtopk.autotune_batched("f32", 12, 22, rows_per_shape=2 * sms)
     out["autotune_s"] = time.perf_counter() - t0
     ok1, oi1 = time_plan("autotuned")
     out["autotuned_equals_rule4"] = bool(torch.equal(ok0.view(torch.int32), ok1.view(torch.int32))
@@ -820,20 +822,26 @@ def main():
         del stage
         torch.cuda.empty_cache()
 
+        call_s = []
+
         def estep():
             for d in dists:
                 for k in ks:
+                    c0 = time.perf_counter()
                     drtopk.drtopk_topk_host_ptr(hosts[d].data_ptr(), n, k, "u32",
                                                 hk[k][0].data_ptr(), hk[k][1].data_ptr())
+                    call_s.append(time.perf_counter() - c0)
         for _ in range(2):  # warm-up rounds (the first calls after set-up are slower)
             estep()
         esteps = max(2, min(args.steps, 5))
         torch.cuda.synchronize()
+        call_s.clear()
         t0 = time.perf_counter()
         for _ in range(esteps):
             estep()
         torch.cuda.synchronize()
         et = time.perf_counter() - t0
+        cms = sorted(1e3 * c for c in call_s)
         out["e2e"] = {"value": float(n) * queries * esteps / et / 1e9, "unit": "Gkeys/s",
                       "h2d_bytes_per_step": 4 * n * queries,
                       "d2h_bytes_per_step": 8 * sum(ks) * len(dists),
@@ -841,7 +849,10 @@ def main():
                       "~128 MB pieces overlapped with the delegate pass)",
                       "h2d_link_gbs": link_gbs,
                       "link_bound_gkeys": link_gbs / 4.0,
-                      "frac_of_link_bound": (float(n) * queries * esteps / et / 1e9) / (link_gbs / 4.0)}
+                      "frac_of_link_bound": (float(n) * queries * esteps / et / 1e9) / (link_gbs / 4.0),
+                      "call_ms": {"min": cms[0], "median": cms[len(cms) // 2], "max": cms[-1],
+                                  "calls": len(cms),
+                                  "above_1.5x_median": sum(c > 1.5 * cms[len(cms) // 2] for c in cms)}}
 
     print(json.dumps(out))
 

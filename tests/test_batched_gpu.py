@@ -172,7 +172,7 @@ def expected_params(n, k, lim):
 
 def test_batched_parameters_follow_rule4_and_table():
     lim = drtopk.batch_limits()
-    lens = [100, 4096, 4097, 20000, 40000, 1 << 16, 1 << 20, (1 << 22) + 3, 16500]
+    lens = [100, 4096, 4097, 10000, 40000, 1 << 16, 1 << 20, (1 << 22) + 3, 16500]
     ks = [7, 4096, 5, 700, 4000, 1024, 1000, 1, 600]
     rng = np.random.default_rng(3)
     bits = rng.integers(0, 2**32, sum(lens), dtype=np.uint64).astype(np.uint32)
@@ -180,7 +180,7 @@ def test_batched_parameters_follow_rule4_and_table():
     a, b = run_and_check(bits, row_off, np.array(ks, np.int32), "u32")
     for n, k, ar, br in zip(lens, ks, a, b):
         assert (ar, br) == expected_params(n, k, lim), (n, k, ar, br)
-    assert a[3] == 0 and a[4] > 0   # 20000/700 is selected directly, 40000 is too long
+    assert a[3] == 0 and a[4] > 0   # 10000/700 is selected directly, 40000 is too long
     # table entries override the default for their shape bucket
     drtopk.tune_set(20, 9, 12, 3)   # n in [2^20, 2^21), k in [512, 1024)
     drtopk.tune_set(14, 9, 6, 4)    # n in [2^14, 2^15), k in [512, 1024): delegates
