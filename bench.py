@@ -64,8 +64,18 @@ PAPER_UD_MS = 6.4  # Dr. Top-k radix, |V| = 2^30 UD, k = 1024, V100S (Sec. 5.1)
 # launches at n = 2^30 (Zipf input, k = 1024 -> alpha 11, k = 2^20 ->
 # alpha 6; mean of two launches each). Must be re-measured (or set to None)
 # whenever the delegate kernel changes.
-DELEG_DRAM_BYTES_PER_KEY = {11: (4295.1e6 + 6.15e6) / (1 << 30),
-                            6: (4295.1e6 + 151.0e6) / (1 << 30)}
+# DRAM bytes (read + write) of a query's delegate stage per key at n = 2^30,
+# by (alpha, delegate path), from one ncu capture of this benchmark's
+# launches (dram__bytes_read.sum + dram__bytes_write.sum, one pass):
+#   path 0: the full delegate pass alone;
+#   path 1: sample (1/128 of the chunks) + records pass + idle fallback;
+#   path 2: sample + idle records pass + the fallback as the full pass;
+#   path 3: records, then the full pass again (the sample misled: rare).
+DELEG_DRAM_BYTES_PER_KEY = {(11, 0): 4301.0e6 / (1 << 30),
+                            (6, 0): 4446.1e6 / (1 << 30),
+                            (6, 1): 4335.8e6 / (1 << 30),
+                            (6, 2): 4480.8e6 / (1 << 30),
+                            (6, 3): (4335.8e6 + 4446.1e6) / (1 << 30)}
 
 
 def parse():
@@ -687,22 +697,30 @@ def main():
         peak = 6800.0
     dms, dl = prof["delegate"]
     achieved = (4.0 * n) / ((dms / max(dl, 1)) * 1e-3) / 1e9 if dl else None
-    # DRAM traffic of the timed delegate launches: each query's alpha (Rule 4
-    # at its k) picks the measured bytes per key; the launch-weighted mean
-    alphas = [drtopk.drtopk_plan(n, k)[0] for d in dists for k in ks]
-    by_alpha = {a: (DELEG_DRAM_BYTES_PER_KEY.get(a) or 0) * n or None for a in sorted(set(alphas))}
-    traffic = (sum(by_alpha[a] for a in alphas) / len(alphas)
-               if all(by_alpha[a] for a in alphas) else None)
+    # DRAM traffic of the timed delegate stages: each query's alpha and
+    # delegate path (from its statistics, read outside the timed region)
+    # pick the measured bytes per key; the mean over the timed queries
+    paths = {}
+    for d in dists:
+        for k in ks:
+            st = drtopk.drtopk_topk_ex(xs[d], k, want_kth=False, dtype="u32")[3]
+            paths[(d, k)] = (st["alpha"], st["delegate_path"])
+    per_q = {"%s/k=%d" % dk: {"alpha": ap[0], "path": ap[1],
+                              "bytes": (DELEG_DRAM_BYTES_PER_KEY.get(ap) or 0) * n or None}
+             for dk, ap in paths.items()}
+    traffic = (sum(q["bytes"] for q in per_q.values()) / len(per_q)
+               if all(q["bytes"] for q in per_q.values()) else None)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                "traffic_by_alpha": {str(a): v for a, v in by_alpha.items()},
-                "traffic_ratio_to_4n_by_alpha": {str(a): (v / (4.0 * n) if v else None)
-                                                 for a, v in by_alpha.items()},
+                "traffic_by_query": per_q,
+                "traffic_ratio_to_4n_by_alpha_path": {
+                    "%d/%d" % ap: v * n / (4.0 * n) for ap, v in DELEG_DRAM_BYTES_PER_KEY.items()},
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the "
-                                  "delegate kernel per alpha, captured in this benchmark's "
-                                  "launches at n=2^30; launch-weighted mean over the timed "
-                                  "queries",
-                "kernel": "delegate_kernel (TMA-streamed delegate pass)",
+                                  "delegate stage's kernels per (alpha, delegate path), "
+                                  "captured in this benchmark's launches at n=2^30; mean over "
+                                  "the timed queries",
+                "kernel": "delegate stage: delegate_kernel (TMA-streamed delegate pass; for "
+                          "alpha <= 10 on large arrays a sampled bound and a records pass)",
                 "algorithmic_bytes_per_launch": 4 * n, "launches": dl,
                 "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs, copy burst)" % peak_src,
                 "frac_vs_nominal_8TBps": (achieved / 8000.0) if achieved else None,
@@ -842,6 +860,11 @@ def main():
         torch.cuda.synchronize()
         et = time.perf_counter() - t0
         cms = sorted(1e3 * c for c in call_s)
+        med = cms[len(cms) // 2]
+        # the slow calls by (round, query in round): a pattern points at the
+        # library, scattered ones at the shared host
+        slow = [[j // queries, j % queries, round(1e3 * c, 2)] for j, c in enumerate(call_s)
+                if 1e3 * c > 1.5 * med][:16]
         out["e2e"] = {"value": float(n) * queries * esteps / et / 1e9, "unit": "Gkeys/s",
                       "h2d_bytes_per_step": 4 * n * queries,
                       "d2h_bytes_per_step": 8 * sum(ks) * len(dists),
@@ -850,9 +873,11 @@ def main():
                       "h2d_link_gbs": link_gbs,
                       "link_bound_gkeys": link_gbs / 4.0,
                       "frac_of_link_bound": (float(n) * queries * esteps / et / 1e9) / (link_gbs / 4.0),
-                      "call_ms": {"min": cms[0], "median": cms[len(cms) // 2], "max": cms[-1],
+                      "frac_of_link_bound_median_call": (4.0 * n / (med * 1e-3) / 1e9) / link_gbs,
+                      "call_ms": {"min": cms[0], "median": med, "max": cms[-1],
                                   "calls": len(cms),
-                                  "above_1.5x_median": sum(c > 1.5 * cms[len(cms) // 2] for c in cms)}}
+                                  "above_1.5x_median": sum(c > 1.5 * med for c in cms),
+                                  "slow_calls_round_query_ms": slow}}
 
     print(json.dumps(out))
 

@@ -207,7 +207,13 @@ typedef struct {
                               second top-k */
   int64_t emitted;         /* outputs written (equals k on success) */
   uint32_t error;          /* device error flags, 0 when none */
-  uint32_t reserved;
+  uint32_t delegate_path;  /* bit 0: the delegate pass stored only the records
+                              of subranges reaching a sampled bound (speculative
+                              compaction of the delegate vector, large arrays
+                              with alpha in [5, 10]); bit 1: a fallback pass then
+                              wrote the full delegate arrays (the bound was above
+                              tau, the records overflowed, or the query ended in
+                              tie mode). The result is exact either way. */
 } drtopk_stats;
 
 /*

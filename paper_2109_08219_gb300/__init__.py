@@ -44,10 +44,10 @@ class Stats(ctypes.Structure):
                 ("ties_needed", ctypes.c_int64), ("scanned", ctypes.c_int64),
                 ("tie_scanned", ctypes.c_int64), ("survivors", ctypes.c_int64),
                 ("emitted", ctypes.c_int64), ("error", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32)]
+                ("delegate_path", ctypes.c_uint32)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class ServerStats(ctypes.Structure):

@@ -69,6 +69,12 @@ bool make_plan(int64_t n, int64_t k, int alpha, int beta, Plan* p, int ablate) {
   return true;
 }
 
+void plan_spec(Plan* p, int64_t n) {
+  p->rec_cap = 0;
+  if (p->ablate == 0 && p->fuse_hist && p->alpha >= 5 && p->alpha <= 10 && n >= (int64_t(1) << 26))
+    p->rec_cap = std::max<int64_t>(1024, p->S / 4);
+}
+
 Layout layout(const Plan& p, int64_t k, bool need_topk, bool external_dkeys) {
   Layout L;
   const size_t D = static_cast<size_t>(p.S) * p.beta;
@@ -85,6 +91,10 @@ Layout layout(const Plan& p, int64_t k, bool need_topk, bool external_dkeys) {
   L.w2 = o; if (need_topk && k > 4096) o += al(static_cast<size_t>(k) * 8);
   L.tstat = o; if (need_topk) o += al(tie_bytes(p.S, p.alpha));
   L.sstat = o; if (need_topk) o += al(sort_status_words(k) * 8);
+  const size_t rc = static_cast<size_t>(p.rec_cap);
+  L.rk = o; o += al(rc * p.beta * 4);
+  L.rs = o; o += al(rc * p.beta * 2);
+  L.rsub = o; o += al(rc * 4);
   L.total = o;
   return L;
 }
@@ -113,6 +123,10 @@ void bind_work(Work& w, char* ws, const Layout& L, const Plan& P, int64_t n, int
   w.dtype = dtype;
   w.ablate = P.ablate;
   w.err_out = nullptr;
+  w.rec_cap = P.rec_cap;
+  w.rec_keys = P.rec_cap ? reinterpret_cast<uint32_t*>(ws + L.rk) : nullptr;
+  w.rec_segs = P.rec_cap ? reinterpret_cast<uint16_t*>(ws + L.rs) : nullptr;
+  w.rec_sub = P.rec_cap ? reinterpret_cast<uint32_t*>(ws + L.rsub) : nullptr;
 }
 
 drtopk_status error_status(uint32_t flags) {
@@ -299,7 +313,8 @@ cudaError_t enqueue_query(const Work& w, const Plan& P, const void* keys, bool t
   cudaError_t e = cudaMemsetAsync(w.ctl, 0, sizeof(Ctl), s);
   if (e != cudaSuccess) return e;
   tm.begin(0);
-  e = launch_delegates(w, keys, P.fuse_hist, sms, s);
+  e = spec_eligible(w, keys) ? launch_delegates_spec(w, keys, sms, s)
+                             : launch_delegates(w, keys, P.fuse_hist, sms, s);
   tm.end();
   if (e != cudaSuccess) return e;
   return enqueue_after_delegates(w, P, keys, topk, out_keys, out_idx, out_kth, sms, s, tm);
@@ -489,6 +504,7 @@ drtopk_status run_query(const void* keys, int dtype, int64_t n, int64_t k, int a
   if (beta > kMaxBeta) return DRTOPK_ERR_INVALID;
   Plan P;
   if (!make_plan(n, k, alpha, beta, &P, ablate)) return DRTOPK_ERR_INVALID;
+  plan_spec(&P, n);
   int sms = 0;
   DevInfo* dv = nullptr;
   st = dev_info(&sms, &dv);
@@ -547,6 +563,7 @@ drtopk_status run_query(const void* keys, int dtype, int64_t n, int64_t k, int a
     stats->survivors = c.stage_count[2];
     stats->emitted = c.w_count;
     stats->error = c.error;
+    stats->delegate_path = (c.spec_used ? 1u : 0u) | (c.full_written ? 2u : 0u);
     st = error_status(c.error);
   }
 done:
@@ -600,6 +617,7 @@ drtopk_status drtopk_plan(int64_t n, int64_t k, int* alpha, int* beta, size_t* w
   if (k < 1 || k > n) return DRTOPK_ERR_K;
   Plan P;
   if (!make_plan(n, k, 0, 0, &P)) return DRTOPK_ERR_INVALID;
+  plan_spec(&P, n);
   if (alpha) *alpha = P.alpha;
   if (beta) *beta = P.beta;
   if (workspace_bytes) *workspace_bytes = layout(P, k, true, false).total;

@@ -131,6 +131,27 @@ struct Ctl {
   uint32_t thr_lo_inv;       // ~(smallest delegate key in the first-digit bucket)
   uint32_t thr_hi;           // largest delegate key in the first-digit bucket
   uint32_t thr_done;         // tau found after digit 1 (the bucket holds one value)
+  // speculative compaction of the delegate vector (large arrays, alpha in
+  // [5, 10]): a sample of the chunks sets t_lo below the expected tau; the
+  // delegate pass then stores only the records of subranges whose largest
+  // delegate is >= t_lo, and the threshold and classification read those.
+  // Exact: when fewer than k delegates are >= t_lo (tau < t_lo), the
+  // records overflow, or the query ends in tie mode (the tie path reads
+  // every subrange's delegates), the full delegate arrays are written by
+  // another pass before they are needed.
+  uint32_t spec_on;          // the records stand in for the delegate arrays
+  uint32_t spec_used;        // the delegate pass stored records (statistics)
+  uint32_t t_lo;
+  uint32_t rec_count;        // records stored
+  uint32_t rec_over;         // more records than their capacity
+  uint32_t n_above;          // delegates >= t_lo
+  uint32_t need_full;        // the full delegate arrays must be written
+  uint32_t need_hist;        // ... and their first-digit histogram taken (the
+                             // sample declined: the records pass did nothing)
+  uint32_t full_written;     // a fallback pass wrote them (statistics)
+  uint32_t samp_n;           // delegates of the sampled chunks
+  uint32_t samp_ticket;
+  uint32_t samp_hist[2048];  // sampled delegates by their top 11 bits
   uint32_t tie_nlist;        // tiles listed for the tie emission
   uint32_t tie_dense;        // the listed tiles are read whole (bulk copies)
   uint32_t g_total;          // |G| = |{x > tau}| at the mode decision
@@ -205,7 +226,30 @@ struct Work {
   int ablate;         // kAblate* flags, 0 for the method as stated
   uint32_t* err_out;  // device-visible word the query's last kernel ORs its
                       // error flags into (nullptr: not reported there)
+  // speculative compaction (spec): records of subranges whose largest
+  // delegate reaches t_lo; rec_cap records at most (0: not planned)
+  uint32_t* rec_keys;  // [rec_cap * beta]
+  uint16_t* rec_segs;  // [rec_cap * beta]
+  uint32_t* rec_sub;   // [rec_cap] subrange of each record
+  int64_t rec_cap;
 };
+
+// Which delegate rows the threshold and the classification read: every
+// subrange (row r = subrange r), or the records of the speculative
+// compaction (row r = subrange sub[r]).
+struct DView {
+  const uint32_t* keys;  // [rows * beta]
+  const uint16_t* segs;
+  const uint32_t* sub;   // nullptr: rows are subranges
+  int64_t rows;
+  __device__ __forceinline__ int64_t subrange(int64_t r) const { return sub ? int64_t(__ldcg(sub + r)) : r; }
+};
+__device__ __forceinline__ DView delegate_view(const Ctl* ctl, const uint32_t* dkeys, const uint16_t* dsegs,
+                                               int64_t S, const uint32_t* rk, const uint16_t* rs,
+                                               const uint32_t* rsub) {
+  if (rk && __ldcg(&ctl->spec_on)) return DView{rk, rs, rsub, int64_t(__ldcg(&ctl->rec_count))};
+  return DView{dkeys, dsegs, nullptr, S};
+}
 
 // Called by one thread of the last kernel of a query, after every earlier
 // kernel of the query has finished: ORs the query's device error flags into

@@ -36,6 +36,17 @@ constexpr int kStages = 3;
 constexpr int kChunkBytes = kChunkKeys * 4;
 constexpr int kWarps = kThreads / 32;
 
+// Passes of the delegate kernel (the speculative compaction is described
+// with Ctl::spec_on).
+constexpr int kPassFull = 0;    // store every subrange's delegates
+constexpr int kPassSample = 1;  // histogram the delegates of every kSampStride-th chunk
+constexpr int kPassSpec = 2;    // store records of subranges reaching t_lo (or all, when off)
+constexpr int kPassFallback = 3;  // store every subrange's delegates when p.only_if holds
+constexpr int kSampStride = 128;
+constexpr int kSampBins = 2048;  // top 11 bits
+constexpr int kRecStage = 512;   // records staged per CTA
+constexpr int kRecFlush = kRecStage - (kChunkKeys >> 5);  // flush before a chunk can overflow
+
 struct DelegParams {
   const uint32_t* keys;
   int64_t n;
@@ -48,12 +59,19 @@ struct DelegParams {
   int fuse_hist;
   int select_last;  // the launch's last block resolves the first threshold digit
   uint32_t k;
+  int only_if;      // fallback pass: 1 when Ctl::need_full; 2 when the
+                    // records stand in and the query is in tie mode
+  int64_t d_total;  // delegate slots of the whole array (sample decision)
+  uint32_t* rec_keys;
+  uint16_t* rec_segs;
+  uint32_t* rec_sub;
+  int64_t rec_cap;
 };
 
 template <int B>
 __device__ __forceinline__ void write_delegates(const DelegParams& p, int64_t sub,
                                                 const uint64_t* c, uint32_t* sh_hist,
-                                                uint32_t& kmax) {
+                                                uint32_t& kmax, bool fuse) {
   // c: descending composites (B entries); kmax: running maximum key
   kmax = max(kmax, dc_key(c[0]));
 #pragma unroll
@@ -62,13 +80,134 @@ __device__ __forceinline__ void write_delegates(const DelegParams& p, int64_t su
     const uint32_t seg = (c[j] == 0) ? kNoSeg : dc_seg(c[j]);
     p.dkeys[sub * B + j] = key;
     p.dsegs[sub * B + j] = static_cast<uint16_t>(seg);
-    if (p.fuse_hist) atomicAdd(&sh_hist[key >> 24], 1u);
+    if (fuse) atomicAdd(&sh_hist[key >> 24], 1u);
   }
 }
 
-// Block-sequence of chunks: the j-th chunk this block processes, or -1.
-__device__ __forceinline__ int64_t chunk_of(const DelegParams& p, int64_t j, int cps_log) {
+// Histogram of a sampled subrange's delegates (top 11 bits).
+template <int B>
+__device__ __forceinline__ void sample_delegates(const uint64_t* c, uint32_t* sh_samp, uint32_t& cnt) {
+#pragma unroll
+  for (int j = 0; j < B; ++j) {
+    if (c[j] != 0) {
+      atomicAdd(&sh_samp[dc_key(c[j]) >> 21], 1u);
+      ++cnt;
+    }
+  }
+}
+
+// Records pass: the histogram and the running maximum for every subrange;
+// a record (subrange, delegates, segments) staged when its largest
+// delegate reaches t_lo; `above` counts the delegates >= t_lo.
+template <int B>
+__device__ __forceinline__ void record_delegates(int64_t sub, const uint64_t* c,
+                                                 uint32_t t_lo, uint32_t* sh_hist, uint32_t& kmax,
+                                                 uint32_t* rs_cnt, uint32_t* rs_sub, uint32_t* rs_keys,
+                                                 uint16_t* rs_segs, uint32_t& above) {
+  kmax = max(kmax, dc_key(c[0]));
+#pragma unroll
+  for (int j = 0; j < B; ++j) atomicAdd(&sh_hist[dc_key(c[j]) >> 24], 1u);
+  if (dc_key(c[0]) >= t_lo) {
+    const uint32_t slot = atomicAdd(rs_cnt, 1u);
+    rs_sub[slot] = static_cast<uint32_t>(sub);
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+      const uint32_t key = dc_key(c[j]);
+      rs_keys[slot * B + j] = key;
+      rs_segs[slot * B + j] = static_cast<uint16_t>((c[j] == 0) ? kNoSeg : dc_seg(c[j]));
+      above += (c[j] != 0 && key >= t_lo) ? 1u : 0u;
+    }
+  }
+}
+
+// Stores the `nst` staged records (all threads; nst read by every thread
+// after a block barrier, before this call) at one reserved range of the
+// record arrays; past their capacity the overflow is flagged instead.
+template <int B>
+__device__ __forceinline__ void flush_records(const DelegParams& p, uint32_t nst, uint32_t* rs_base,
+                                              uint32_t* rs_cnt, const uint32_t* rs_sub,
+                                              const uint32_t* rs_keys, const uint16_t* rs_segs) {
+  if (threadIdx.x == 0) *rs_base = atomicAdd(&p.ctl->rec_count, nst);
+  __syncthreads();
+  const uint64_t base = *rs_base;
+  for (uint32_t i = threadIdx.x; i < nst; i += kThreads) {
+    const uint64_t r = base + i;
+    if (r < static_cast<uint64_t>(p.rec_cap)) {
+      p.rec_sub[r] = rs_sub[i];
+#pragma unroll
+      for (int j = 0; j < B; ++j) {
+        p.rec_keys[r * B + j] = rs_keys[i * B + j];
+        p.rec_segs[r * B + j] = rs_segs[i * B + j];
+      }
+    }
+  }
+  if (threadIdx.x == 0) {
+    if (base + nst > static_cast<uint64_t>(p.rec_cap)) p.ctl->rec_over = 1;
+    *rs_cnt = 0;  // the next appends follow the next block barrier
+  }
+}
+
+// Last block of the sample pass: t_lo = the start of the highest 11-bit
+// bin whose count from the top reaches 1.5x the expected number of sampled
+// delegates above tau (k scaled by the sampled share of the delegates),
+// plus 8 standard deviations and 64; records are used when the delegates
+// >= t_lo, scaled up, stay within 80 % of the record capacity.
+__device__ void sample_decide(const DelegParams& p) {
+  constexpr int per = kSampBins / kThreads;  // bins per thread, from the top
+  __shared__ uint32_t s_acc;
+  if (threadIdx.x == 0) s_acc = 0;
+  uint32_t c[per];
+  uint32_t sum = 0;
+#pragma unroll
+  for (int j = 0; j < per; ++j) {
+    c[j] = __ldcg(&p.ctl->samp_hist[kSampBins - 1 - (threadIdx.x * per + j)]);
+    sum += c[j];
+  }
+  const uint32_t excl = block_scan_excl<kThreads>(sum, nullptr);  // (synchronizes)
+  const double sn = static_cast<double>(__ldcg(&p.ctl->samp_n));
+  const double scale = static_cast<double>(p.d_total) / (sn > 0.0 ? sn : 1.0);
+  const double target = static_cast<double>(p.k) / scale;
+  const double need = 1.5 * target + 8.0 * sqrt(target) + 64.0;
+  // too few sampled delegates: decline
+  if (sn >= 4096.0 && static_cast<double>(excl) < need && static_cast<double>(excl) + sum >= need) {
+    double acc = excl;
+    int j = 0;
+    for (; j < per - 1; ++j) {
+      acc += c[j];
+      if (acc >= need) break;
+    }
+    if (j == per - 1) acc = static_cast<double>(excl) + sum;
+    const uint32_t bin = static_cast<uint32_t>(kSampBins - 1 - (threadIdx.x * per + j));
+    const double est = acc * scale * 1.1;
+    if (bin > 0 && est <= 0.8 * static_cast<double>(p.rec_cap)) {
+      p.ctl->t_lo = bin << 21;
+      p.ctl->spec_on = 1;
+      s_acc = 1;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !s_acc) {
+    // declined: the fallback pass is the delegate pass of this query
+    p.ctl->need_full = 1;
+    p.ctl->need_hist = 1;
+  }
+}
+
+// Block-sequence of chunks: the j-th chunk this block processes, or -1
+// (always -1 for a fallback pass whose condition does not hold: the pass
+// then ends without an early return, which keeps its code as the full
+// pass's).
+template <int MODE = kPassFull>
+__device__ __forceinline__ int64_t chunk_of(const DelegParams& p, int64_t j, int cps_log,
+                                            bool skip = false) {
   const int64_t G = gridDim.x;
+  if constexpr (MODE == kPassFallback || MODE == kPassSpec) {
+    if (skip) return -1;
+  }
+  if constexpr (MODE == kPassSample) {
+    const int64_t c = (blockIdx.x + j * G) * kSampStride;
+    return c < p.nchunks ? c : -1;
+  }
   if (cps_log == 0) {
     const int64_t c = blockIdx.x + j * G;
     return c < p.nchunks ? c : -1;
@@ -102,14 +241,41 @@ __device__ __forceinline__ void issue_chunk(const DelegParams& p, int64_t c, uin
   }
 }
 
-template <int DT, int B, bool TMA>
+template <int DT, int B, bool TMA, int MODE = kPassFull>
 __global__ void __launch_bounds__(kThreads, 2) delegate_kernel(DelegParams p) {
   constexpr int P = Pow2<B>::v;
+  // a fallback pass runs only when its condition holds, a records pass
+  // only when the sample accepted (uniform over the grid)
+  bool skip = false;
+  bool fuse = p.fuse_hist != 0, sel = p.select_last != 0;
+  if constexpr (MODE == kPassFallback) {
+    skip = (p.only_if == 1) ? !__ldcg(&p.ctl->need_full)
+                            : !(__ldcg(&p.ctl->spec_on) && __ldcg(&p.ctl->mode) == kModeTies);
+    if (!skip && blockIdx.x == 0 && threadIdx.x == 0) p.ctl->full_written = 1;
+    // after a declined sample this is the query's delegate pass
+    fuse = sel = !skip && p.only_if == 1 && __ldcg(&p.ctl->need_hist) != 0;
+  }
   extern __shared__ __align__(128) uint32_t smem[];
   uint32_t* buf = smem;  // kStages * kChunkKeys
   __shared__ __align__(8) uint64_t full_bar[kStages];
   __shared__ uint32_t sh_hist[256];
   __shared__ uint64_t sh_lists[kWarps][P];
+  // sample pass: histogram; records pass: the staged records
+  __shared__ uint32_t sh_samp[MODE == kPassSample ? kSampBins : 1];
+  __shared__ uint32_t rs_sub[MODE == kPassSpec ? kRecStage : 1];
+  __shared__ uint32_t rs_keys[MODE == kPassSpec ? kRecStage * B : 1];
+  __shared__ uint16_t rs_segs[MODE == kPassSpec ? kRecStage * B : 1];
+  __shared__ uint32_t rs_cnt, rs_base;
+  uint32_t samp_cnt = 0, above = 0;
+  bool spec = false;
+  uint32_t t_lo = 0;
+  if constexpr (MODE == kPassSpec) {
+    spec = __ldcg(&p.ctl->spec_on) != 0;
+    t_lo = __ldcg(&p.ctl->t_lo);
+    skip = !spec;
+    fuse = fuse && spec;
+    sel = sel && spec;
+  }
 
   const int tid = threadIdx.x;
   const int lane = tid & 31;
@@ -118,6 +284,9 @@ __global__ void __launch_bounds__(kThreads, 2) delegate_kernel(DelegParams p) {
   const int cps_log = alpha > 13 ? alpha - 13 : 0;  // chunks per subrange (log2)
 
   for (int i = tid; i < 256; i += kThreads) sh_hist[i] = 0;
+  if constexpr (MODE == kPassSample)
+    for (int i = tid; i < kSampBins; i += kThreads) sh_samp[i] = 0;
+  if (MODE == kPassSpec && tid == 0) rs_cnt = 0;
   uint64_t pol = 0;
   if constexpr (TMA) {
     if (tid == 0) {
@@ -131,7 +300,7 @@ __global__ void __launch_bounds__(kThreads, 2) delegate_kernel(DelegParams p) {
   if constexpr (TMA) {
     if (tid == 0) {
       for (int s = 0; s < kStages; ++s) {
-        const int64_t c = chunk_of(p, s, cps_log);
+        const int64_t c = chunk_of<MODE>(p, s, cps_log, skip);
         if (c < 0) break;
         issue_chunk<true>(p, c, buf + s * kChunkKeys, &full_bar[s], pol);
       }
@@ -145,7 +314,7 @@ __global__ void __launch_bounds__(kThreads, 2) delegate_kernel(DelegParams p) {
   for (int i = 0; i < P; ++i) run[i] = 0;
 
   for (int64_t j = 0;; ++j) {
-    const int64_t c = chunk_of(p, j, cps_log);
+    const int64_t c = chunk_of<MODE>(p, j, cps_log, skip);
     if (c < 0) break;
     const int stage = static_cast<int>(j % kStages);
     uint32_t* cb = buf + stage * kChunkKeys;
@@ -161,7 +330,7 @@ __global__ void __launch_bounds__(kThreads, 2) delegate_kernel(DelegParams p) {
         if constexpr (TMA) {
           // copies still in flight land in this CTA's shared memory: let
           // them complete (bounded) before the CTA exits
-          for (int64_t jj = j; jj < j + kStages && chunk_of(p, jj, cps_log) >= 0; ++jj)
+          for (int64_t jj = j; jj < j + kStages && chunk_of<MODE>(p, jj, cps_log, skip) >= 0; ++jj)
             mbar_wait_bounded(&full_bar[jj % kStages], static_cast<uint32_t>((jj / kStages) & 1));
         }
       }
@@ -203,7 +372,7 @@ __global__ void __launch_bounds__(kThreads, 2) delegate_kernel(DelegParams p) {
         uint64_t cc[B];
 #pragma unroll
         for (int i = 0; i < B; ++i) cc[i] = (i < r) ? make_dc(m[i], 0) : 0;
-        write_delegates<B>(p, sub, cc, sh_hist, kmax);
+        write_delegates<B>(p, sub, cc, sh_hist, kmax, fuse);
       }
     } else {
       // value-only top-B of the thread's 32-key segment
@@ -236,7 +405,16 @@ __global__ void __launch_bounds__(kThreads, 2) delegate_kernel(DelegParams p) {
         const int wl = g_log < 5 ? g_log : 5;
         for (int l = 0; l < wl; ++l) shfl_merge<P>(a, 1 << l);
         if (g_log <= 5) {
-          if ((lane & ((1 << g_log) - 1)) == 0 && sub < p.S) write_delegates<B>(p, sub, a, sh_hist, kmax);
+          if ((lane & ((1 << g_log) - 1)) == 0 && sub < p.S) {
+            if constexpr (MODE == kPassSample) {
+              sample_delegates<B>(a, sh_samp, samp_cnt);
+            } else if constexpr (MODE == kPassSpec) {
+              record_delegates<B>(sub, a, t_lo, sh_hist, kmax, &rs_cnt, rs_sub, rs_keys, rs_segs,
+                                  above);
+            } else {
+              write_delegates<B>(p, sub, a, sh_hist, kmax, fuse);
+            }
+          }
         } else {
           // 2^(g_log-5) warps per subrange: merge their lists in shared memory
           if (lane == 0) {
@@ -253,7 +431,7 @@ __global__ void __launch_bounds__(kThreads, 2) delegate_kernel(DelegParams p) {
             for (int i = 0; i < P; ++i) b[i] = sh_lists[src][i];
             for (int l = 0; l < wps_log; ++l) shfl_merge<P>(b, 1 << l);
             const int64_t sub2 = (cstart >> alpha) + warp;
-            if (lane == 0 && sub2 < p.S) write_delegates<B>(p, sub2, b, sh_hist, kmax);
+            if (lane == 0 && sub2 < p.S) write_delegates<B>(p, sub2, b, sh_hist, kmax, fuse);
           }
         }
       } else {
@@ -273,7 +451,7 @@ __global__ void __launch_bounds__(kThreads, 2) delegate_kernel(DelegParams p) {
 #pragma unroll
             for (int i = 0; i < P; ++i) b[i] = sh_lists[lane & 7][i];
             for (int l = 0; l < 3; ++l) shfl_merge<P>(b, 1 << l);
-            if (lane == 0) write_delegates<B>(p, c >> cps_log, b, sh_hist, kmax);
+            if (lane == 0) write_delegates<B>(p, c >> cps_log, b, sh_hist, kmax, fuse);
           }
 #pragma unroll
           for (int i = 0; i < P; ++i) run[i] = 0;
@@ -283,10 +461,36 @@ __global__ void __launch_bounds__(kThreads, 2) delegate_kernel(DelegParams p) {
     __syncthreads();  // stage fully consumed
     if constexpr (TMA) {
       if (tid == 0) {
-        const int64_t cn = chunk_of(p, j + kStages, cps_log);
+        const int64_t cn = chunk_of<MODE>(p, j + kStages, cps_log, skip);
         if (cn >= 0) issue_chunk<true>(p, cn, cb, &full_bar[stage], pol);
       }
     }
+    if constexpr (MODE == kPassSpec) {
+      const uint32_t nst = rs_cnt;  // no append is in flight after the barrier
+      if (nst >= static_cast<uint32_t>(kRecFlush))
+        flush_records<B>(p, nst, &rs_base, &rs_cnt, rs_sub, rs_keys, rs_segs);
+    }
+  }
+  if constexpr (MODE == kPassSpec) {
+    if (spec) {  // else the sample declined: the fallback pass does it all
+      __syncthreads();
+      const uint32_t nst = rs_cnt;
+      if (nst) flush_records<B>(p, nst, &rs_base, &rs_cnt, rs_sub, rs_keys, rs_segs);
+      const uint32_t wa = __reduce_add_sync(0xFFFFFFFFu, above);
+      if (lane == 0 && wa) atomicAdd(&p.ctl->n_above, wa);
+      if (tid == 0) p.ctl->spec_used = 1;
+    }
+  }
+  if constexpr (MODE == kPassSample) {
+    __syncthreads();
+    for (int i = tid; i < kSampBins; i += kThreads) {
+      const uint32_t v = sh_samp[i];
+      if (v) atomicAdd(&p.ctl->samp_hist[i], v);
+    }
+    const uint32_t wc = __reduce_add_sync(0xFFFFFFFFu, samp_cnt);
+    if (lane == 0 && wc) atomicAdd(&p.ctl->samp_n, wc);
+    if (last_block(&p.ctl->samp_ticket)) sample_decide(p);
+    return;
   }
 
   {
@@ -294,63 +498,80 @@ __global__ void __launch_bounds__(kThreads, 2) delegate_kernel(DelegParams p) {
     const uint32_t wm = __reduce_max_sync(0xFFFFFFFFu, kmax);
     if (lane == 0 && wm) atomicMax(&p.ctl->key_max, wm);
   }
-  if (p.fuse_hist) {
+  if (fuse) {
     __syncthreads();
     for (int i = tid; i < 256; i += kThreads) {
       const uint32_t v = sh_hist[i];
       if (v) atomicAdd(&p.ctl->dsel.hist[0][i], v);
     }
-    if (p.select_last && last_block(&p.ctl->dsel.ticket[0])) {
+    if (sel && last_block(&p.ctl->dsel.ticket[0])) {
       if (warp == 0) {
         if (lane == 0) p.ctl->dsel.k_rem = p.k;
         __syncwarp();
         select_digit<4>(&p.ctl->dsel, 0, 32, false);
       }
+      if constexpr (MODE == kPassSpec) {
+        // tau >= t_lo iff at least k delegates are >= t_lo: else, or when
+        // the records overflowed, the full arrays are written next
+        if (tid == 0 && __ldcg(&p.ctl->spec_on) &&
+            (__ldcg(&p.ctl->n_above) < p.k || __ldcg(&p.ctl->rec_over))) {
+          p.ctl->need_full = 1;
+          p.ctl->spec_on = 0;
+        }
+      }
     }
   }
 }
 
-template <int DT, int B>
+template <int DT, int B, int MODE>
 cudaError_t launch_deleg_t(const DelegParams& p, bool tma, int sms, cudaStream_t s) {
   const size_t smem = static_cast<size_t>(kStages) * kChunkBytes;
   int64_t units = (p.alpha > 13) ? p.S : p.nchunks;
+  if (MODE == kPassSample) units = (p.nchunks + kSampStride - 1) / kSampStride;
   int64_t grid = std::min<int64_t>(units, static_cast<int64_t>(sms) * 2);
   if (grid < 1) grid = 1;
-  if (tma) {
-    auto k = delegate_kernel<DT, B, true>;
+  if (tma || MODE != kPassFull) {
+    auto k = delegate_kernel<DT, B, true, MODE>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     k<<<static_cast<unsigned>(grid), kThreads, smem, s>>>(p);
   } else {
-    auto k = delegate_kernel<DT, B, false>;
+    auto k = delegate_kernel<DT, B, false, kPassFull>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     k<<<static_cast<unsigned>(grid), kThreads, smem, s>>>(p);
   }
   return cudaGetLastError();
 }
 
-template <int DT>
+template <int DT, int MODE>
 cudaError_t launch_deleg_b(const DelegParams& p, int beta, bool tma, int sms, cudaStream_t s) {
   switch (beta) {
-    case 1: return launch_deleg_t<DT, 1>(p, tma, sms, s);
-    case 2: return launch_deleg_t<DT, 2>(p, tma, sms, s);
-    case 3: return launch_deleg_t<DT, 3>(p, tma, sms, s);
-    case 4: return launch_deleg_t<DT, 4>(p, tma, sms, s);
+    case 1: return launch_deleg_t<DT, 1, MODE>(p, tma, sms, s);
+    case 2: return launch_deleg_t<DT, 2, MODE>(p, tma, sms, s);
+    case 3: return launch_deleg_t<DT, 3, MODE>(p, tma, sms, s);
+    case 4: return launch_deleg_t<DT, 4, MODE>(p, tma, sms, s);
   }
   return cudaErrorInvalidValue;
 }
 
-}  // namespace
-
-cudaError_t launch_delegates(const Work& w, const void* keys, bool fuse_hist, int sms,
-                             cudaStream_t s) {
-  return launch_delegates_range(w, keys, 0, w.S, fuse_hist, true, sms, s);
+template <int MODE>
+cudaError_t launch_deleg_mode(const Work& w, const DelegParams& p, bool tma, int sms, cudaStream_t s) {
+  note_launch();
+  switch (w.dtype) {
+    case DRTOPK_U32: return launch_deleg_b<DRTOPK_U32, MODE>(p, w.beta, tma, sms, s);
+    case DRTOPK_I32: return launch_deleg_b<DRTOPK_I32, MODE>(p, w.beta, tma, sms, s);
+    case DRTOPK_F32: return launch_deleg_b<DRTOPK_F32, MODE>(p, w.beta, tma, sms, s);
+    case DRTOPK_U32 | kSmallest: return launch_deleg_b<DRTOPK_U32 | kSmallest, MODE>(p, w.beta, tma, sms, s);
+    case DRTOPK_I32 | kSmallest: return launch_deleg_b<DRTOPK_I32 | kSmallest, MODE>(p, w.beta, tma, sms, s);
+    case DRTOPK_F32 | kSmallest: return launch_deleg_b<DRTOPK_F32 | kSmallest, MODE>(p, w.beta, tma, sms, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_delegates_range(const Work& w, const void* keys, int64_t sub0, int64_t sub1,
-                                   bool fuse_hist, bool select_last, int sms, cudaStream_t s) {
-  // subranges [sub0, sub1) as an array of their own: keys and delegate
-  // slots offset by whole subranges (positions inside a subrange and the
-  // segments stored with the delegates do not change)
+// Parameters of the pass over subranges [sub0, sub1) as an array of their
+// own: keys and delegate slots offset by whole subranges (positions inside
+// a subrange and the segments stored with the delegates do not change).
+DelegParams deleg_params(const Work& w, const void* keys, int64_t sub0, int64_t sub1, bool fuse_hist,
+                         bool select_last) {
   DelegParams p;
   const int64_t k0 = sub0 << w.alpha;
   p.keys = static_cast<const uint32_t*>(keys) + k0;
@@ -364,18 +585,49 @@ cudaError_t launch_delegates_range(const Work& w, const void* keys, int64_t sub0
   p.fuse_hist = fuse_hist ? 1 : 0;
   p.select_last = select_last ? 1 : 0;
   p.k = static_cast<uint32_t>(w.k);
+  p.only_if = 0;
+  p.d_total = w.S * w.beta;
+  p.rec_keys = w.rec_keys;
+  p.rec_segs = w.rec_segs;
+  p.rec_sub = w.rec_sub;
+  p.rec_cap = w.rec_cap;
+  return p;
+}
+
+}  // namespace
+
+bool spec_eligible(const Work& w, const void* keys) {
+  return w.rec_cap > 0 && w.alpha >= 5 && w.alpha <= 10 && w.ablate == 0 &&
+         (reinterpret_cast<uintptr_t>(keys) & 15u) == 0;
+}
+
+cudaError_t launch_delegates(const Work& w, const void* keys, bool fuse_hist, int sms,
+                             cudaStream_t s) {
+  return launch_delegates_range(w, keys, 0, w.S, fuse_hist, true, sms, s);
+}
+
+cudaError_t launch_delegates_range(const Work& w, const void* keys, int64_t sub0, int64_t sub1,
+                                   bool fuse_hist, bool select_last, int sms, cudaStream_t s) {
+  const DelegParams p = deleg_params(w, keys, sub0, sub1, fuse_hist, select_last);
   if (p.n <= 0 || p.S <= 0) return cudaErrorInvalidValue;
   const bool tma = (reinterpret_cast<uintptr_t>(p.keys) & 15u) == 0;
-  note_launch();
-  switch (w.dtype) {
-    case DRTOPK_U32: return launch_deleg_b<DRTOPK_U32>(p, w.beta, tma, sms, s);
-    case DRTOPK_I32: return launch_deleg_b<DRTOPK_I32>(p, w.beta, tma, sms, s);
-    case DRTOPK_F32: return launch_deleg_b<DRTOPK_F32>(p, w.beta, tma, sms, s);
-    case DRTOPK_U32 | kSmallest: return launch_deleg_b<DRTOPK_U32 | kSmallest>(p, w.beta, tma, sms, s);
-    case DRTOPK_I32 | kSmallest: return launch_deleg_b<DRTOPK_I32 | kSmallest>(p, w.beta, tma, sms, s);
-    case DRTOPK_F32 | kSmallest: return launch_deleg_b<DRTOPK_F32 | kSmallest>(p, w.beta, tma, sms, s);
-  }
-  return cudaErrorInvalidValue;
+  return launch_deleg_mode<kPassFull>(w, p, tma, sms, s);
+}
+
+cudaError_t launch_delegates_spec(const Work& w, const void* keys, int sms, cudaStream_t s) {
+  if (!spec_eligible(w, keys)) return launch_delegates(w, keys, true, sms, s);
+  const DelegParams p = deleg_params(w, keys, 0, w.S, true, true);
+  cudaError_t e = launch_deleg_mode<kPassSample>(w, p, true, sms, s);
+  if (e == cudaSuccess) e = launch_deleg_mode<kPassSpec>(w, p, true, sms, s);
+  if (e == cudaSuccess) e = launch_delegates_fallback(w, keys, 1, sms, s);
+  return e;
+}
+
+cudaError_t launch_delegates_fallback(const Work& w, const void* keys, int cond, int sms,
+                                      cudaStream_t s) {
+  DelegParams p = deleg_params(w, keys, 0, w.S, false, false);
+  p.only_if = cond;
+  return launch_deleg_mode<kPassFallback>(w, p, true, sms, s);
 }
 
 }  // namespace drtopk

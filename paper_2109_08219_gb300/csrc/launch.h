@@ -23,14 +23,18 @@ struct Plan {
   int64_t g_cap;
   bool fuse_hist;  // beta * S >= k: tau from the delegates, else tau = 0
   int ablate = 0;
+  int64_t rec_cap = 0;  // records of the speculative compaction (0: not planned)
 };
 bool make_plan(int64_t n, int64_t k, int alpha, int beta, Plan* p, int ablate = 0);
+// Plans the speculative compaction of the delegate vector for a query that
+// runs whole on the device (large arrays with alpha in [5, 10]).
+void plan_spec(Plan* p, int64_t n);
 
 // Byte offsets of a query's workspace regions (256-byte aligned) and the
 // total. need_topk = false leaves out the regions only top-k uses;
 // external_dkeys leaves out the delegate keys (a caller's buffer).
 struct Layout {
-  size_t ctl, dkeys, dsegs, ds, scanq, rq, g, sv, w, w2, tstat, sstat, total;
+  size_t ctl, dkeys, dsegs, ds, scanq, rq, g, sv, w, w2, tstat, sstat, rk, rs, rsub, total;
 };
 Layout layout(const Plan& p, int64_t k, bool need_topk, bool external_dkeys);
 
@@ -53,6 +57,17 @@ cudaError_t launch_delegates(const Work& w, const void* keys, bool fuse_hist, in
 // call with select_last resolves the digit (it must come last).
 cudaError_t launch_delegates_range(const Work& w, const void* keys, int64_t sub0, int64_t sub1,
                                    bool fuse_hist, bool select_last, int sms, cudaStream_t s);
+
+// Speculative compaction of the delegate vector (Ctl::spec_on): whether a
+// query can use it (records planned, alpha in [5, 10], the method as stated,
+// 16-byte aligned keys); the sample pass, the records pass and the fallback
+// full pass when the speculation missed (the whole delegate step of such a
+// query); and the fallback full pass for a query that ends in tie mode
+// (cond 2; cond 1 = when Ctl::need_full).
+bool spec_eligible(const Work& w, const void* keys);
+cudaError_t launch_delegates_spec(const Work& w, const void* keys, int sms, cudaStream_t s);
+cudaError_t launch_delegates_fallback(const Work& w, const void* keys, int cond, int sms,
+                                      cudaStream_t s);
 
 // Threshold select passes 1..3 over the delegate keys (select.cu).
 cudaError_t launch_threshold(const Work& w, int sms, cudaStream_t s);

@@ -169,9 +169,15 @@ constexpr int kThrStageCap = kThreads * 16;
 // one (compacted into ds) and histogram their second digit. When the first
 // digit's bucket is large (ties, few distinct values) nothing is copied and
 // the later passes read the delegate keys in place.
-__global__ void __launch_bounds__(kThreads) thr_compact_kernel(const uint32_t* dkeys,
-                                                               int64_t count, uint32_t* ds,
-                                                               Ctl* ctl, int allow_done) {
+__global__ void __launch_bounds__(kThreads) thr_compact_kernel(const uint32_t* dkeys_all,
+                                                               int64_t count_all, uint32_t* ds,
+                                                               Ctl* ctl, int allow_done,
+                                                               const uint32_t* rec_keys, int beta) {
+  // every delegate key, or the records' keys (their rows hold every key
+  // >= t_lo, and tau >= t_lo: the same k-th largest)
+  const DView dv = delegate_view(ctl, dkeys_all, nullptr, count_all / beta, rec_keys, nullptr, nullptr);
+  const uint32_t* dkeys = dv.keys;
+  const int64_t count = dv.rows * beta;
   __shared__ uint32_t sh[256];
   constexpr int kWCap = kThrStageCap / (kThreads / 32);
   __shared__ uint32_t sbuf[kThrStageCap];
@@ -242,10 +248,14 @@ __global__ void __launch_bounds__(kThreads) thr_compact_kernel(const uint32_t* d
 
 // Digit 2 and 3 passes over the compacted survivors (or the delegate keys).
 __global__ void __launch_bounds__(kThreads) thr_pass_kernel(const uint32_t* dsv,
-                                                            const uint32_t* dkeys,
-                                                            int64_t dcount, Ctl* ctl,
-                                                            int pass, int last_pass) {
+                                                            const uint32_t* dkeys_all,
+                                                            int64_t dcount_all, Ctl* ctl,
+                                                            int pass, int last_pass,
+                                                            const uint32_t* rec_keys, int beta) {
   if (__ldcg(&ctl->thr_done)) return;  // tau already known
+  const DView dv = delegate_view(ctl, dkeys_all, nullptr, dcount_all / beta, rec_keys, nullptr, nullptr);
+  const uint32_t* dkeys = dv.keys;
+  const int64_t dcount = dv.rows * beta;
   __shared__ uint32_t sh[256];
   zero_hist(sh);
   __syncthreads();
@@ -292,6 +302,9 @@ struct FilterParams {
   int alpha;
   const uint32_t* dkeys;
   const uint16_t* dsegs;
+  const uint32_t* rec_keys;  // speculative compaction's records (nullptr: none)
+  const uint16_t* rec_segs;
+  const uint32_t* rec_sub;
   uint32_t* scanq;
   uint64_t* g;
   Ctl* ctl;
@@ -353,15 +366,19 @@ __global__ void __launch_bounds__(kThreads) filter_classify_kernel(FilterParams 
   const int alpha = p.alpha;
   uint32_t nscan = 0;
   const int64_t per_step = int64_t(kThreads) * kClsSub;
+  // rows: every subrange, or the records of the speculative compaction
+  // (subranges not recorded have m^0 < t_lo <= tau: skipped either way)
+  const DView dv = delegate_view(p.ctl, p.dkeys, p.dsegs, p.S, p.rec_keys, p.rec_segs, p.rec_sub);
+  const int64_t rows = dv.rows;
   // the next step's delegates are loaded before this step is classified
   // (double-buffered in registers)
   uint32_t dk[kClsSub][B], nk[kClsSub][B];
   auto load_step = [&](int64_t b) {
 #pragma unroll
     for (int u = 0; u < kClsSub; ++u) {
-      const int64_t i = b + int64_t(u) * kThreads + threadIdx.x;
-      if (i < p.S) {
-        load_dkeys<B>(p.dkeys, i, nk[u]);
+      const int64_t r = b + int64_t(u) * kThreads + threadIdx.x;
+      if (r < rows) {
+        load_dkeys<B>(dv.keys, r, nk[u]);
       } else {
 #pragma unroll
         for (int j = 0; j < B; ++j) nk[u][j] = 0u;
@@ -369,22 +386,23 @@ __global__ void __launch_bounds__(kThreads) filter_classify_kernel(FilterParams 
     }
   };
   load_step(int64_t(blockIdx.x) * per_step);
-  for (int64_t base = int64_t(blockIdx.x) * per_step; base < p.S;
+  for (int64_t base = int64_t(blockIdx.x) * per_step; base < rows;
        base += int64_t(gridDim.x) * per_step) {
 #pragma unroll
     for (int u = 0; u < kClsSub; ++u)
 #pragma unroll
       for (int j = 0; j < B; ++j) dk[u][j] = nk[u][j];
-    if (base + int64_t(gridDim.x) * per_step < p.S) load_step(base + int64_t(gridDim.x) * per_step);
+    if (base + int64_t(gridDim.x) * per_step < rows) load_step(base + int64_t(gridDim.x) * per_step);
     uint32_t scanm = 0;  // subranges to scan (bit u)
     uint32_t emitm = 0;  // delegate slots to place (bit u * B + j)
 #pragma unroll
     for (int u = 0; u < kClsSub; ++u) {
-      const int64_t i = base + int64_t(u) * kThreads + threadIdx.x;
+      const int64_t r = base + int64_t(u) * kThreads + threadIdx.x;
+      const int64_t i = r < rows ? dv.subrange(r) : 0;
       if (p.no_filter) {
         // Rule 1 alone: a subrange whose maximum delegate reaches tau is kept whole
-        if (i < p.S && dk[u][0] >= tau) scanm |= 1u << u;
-      } else if (i < p.S && dk[u][0] > tau) {
+        if (r < rows && dk[u][0] >= tau) scanm |= 1u << u;
+      } else if (r < rows && dk[u][0] > tau) {
         if (dk[u][B - 1] > tau && sub_len(i, alpha, p.n) > B) {
           scanm |= 1u << u;
         } else {
@@ -399,9 +417,12 @@ __global__ void __launch_bounds__(kThreads) filter_classify_kernel(FilterParams 
       uint32_t pos = sq.reserve(__popc(scanm), &p.ctl->scanq_count, p.scanq, ~uint64_t(0),
                                 &p.ctl->error, 0u);
 #pragma unroll
-      for (int u = 0; u < kClsSub; ++u)
-        if ((scanm >> u) & 1u)
-          sq.buf[pos++] = static_cast<uint32_t>(base + int64_t(u) * kThreads + threadIdx.x);
+      for (int u = 0; u < kClsSub; ++u) {
+        if ((scanm >> u) & 1u) {
+          const int64_t r = base + int64_t(u) * kThreads + threadIdx.x;
+          sq.buf[pos++] = static_cast<uint32_t>(dv.subrange(r));
+        }
+      }
       nscan += __popc(scanm);
     }
     if (__any_sync(0xFFFFFFFFu, emitm != 0)) {
@@ -411,7 +432,7 @@ __global__ void __launch_bounds__(kThreads) filter_classify_kernel(FilterParams 
       for (int u = 0; u < kClsSub; ++u)
 #pragma unroll
         for (int j = 0; j < B; ++j)
-          if ((emitm >> (u * B + j)) & 1u)
+          if ((emitm >> (u * B + j)) & 1u)  // row << 2 | slot
             sr.buf[pos++] = static_cast<uint32_t>((base + int64_t(u) * kThreads + threadIdx.x) << 2) |
                             static_cast<uint32_t>(j);
     }
@@ -446,7 +467,7 @@ __device__ __forceinline__ FineGeom fine_geom(const Ctl* ctl) {
 // k): then only the keys from the bucket holding the k-th key upwards are
 // written, not every key above tau.
 __device__ __forceinline__ bool two_pass_wanted(int no_filter, int64_t total, int64_t k) {
-  const int64_t lim = 4 * k > (int64_t(1) << 22) ? 4 * k : (int64_t(1) << 22);
+  const int64_t lim = 4 * k > (int64_t(1) << 17) ? 4 * k : (int64_t(1) << 17);
   return !no_filter && total > lim;
 }
 
@@ -503,6 +524,8 @@ __global__ void __launch_bounds__(kThreads) filter_resolve_kernel(FilterParams p
   const FineGeom fg = fine_geom(ctl);
   // the counting pass of a large scan set needs these keys in its histogram
   const bool fine = two_pass_wanted(p.no_filter, int64_t(__ldcg(&ctl->scanq_count)) << alpha, p.k);
+  // requests are (row << 2 | slot) of the classification's rows
+  const DView dv = delegate_view(ctl, p.dkeys, p.dsegs, p.S, p.rec_keys, p.rec_segs, p.rec_sub);
   for (int64_t b0 = int64_t(blockIdx.x) * kThreads; b0 < nq; b0 += int64_t(gridDim.x) * kThreads) {
     const int64_t q = b0 + threadIdx.x;  // this lane's request
     uint32_t key = 0;
@@ -510,14 +533,15 @@ __global__ void __launch_bounds__(kThreads) filter_resolve_kernel(FilterParams p
     int occ = 0;
     if (q < nq) {
       const uint32_t r = p.rq[q];
-      const int64_t i = r >> 2;
+      const int64_t row = r >> 2;
+      const int64_t i = dv.subrange(row);
       const int j = static_cast<int>(r & 3u);
       uint32_t dk[B];
       uint16_t ds[B];
 #pragma unroll
       for (int z = 0; z < B; ++z) {
-        dk[z] = p.dkeys[i * B + z];
-        ds[z] = p.dsegs[i * B + z];
+        dk[z] = dv.keys[row * B + z];
+        ds[z] = dv.segs[row * B + z];
       }
       // register selects (j is data-dependent): no local-memory arrays
       uint32_t sj = 0;
@@ -1794,21 +1818,27 @@ cudaError_t launch_threshold(const Work& w, int sms, cudaStream_t s) {
   // the one-value shortcut after digit 1 is off under the ablation that
   // stops the select one digit early (its tau must stay the truncated one)
   thr_compact_kernel<<<g1, kThreads, 0, s>>>(w.dkeys, count, w.ds, w.ctl,
-                                             (w.ablate & kAblateSkipLastDigit) ? 0 : 1);
+                                             (w.ablate & kAblateSkipLastDigit) ? 0 : 1,
+                                             w.rec_keys, w.beta);
   const int g2 = grid_for(count, kThreads * 8, sms, 4);
   // the shortcut stops after digit 2: tau = the k-th delegate's top 24 bits
   // (low byte 0), a lower threshold, still exact (the tie reading holds for
   // any tau with at least k keys >= tau)
   const bool skip_last = (w.ablate & kAblateSkipLastDigit) != 0;
-  thr_pass_kernel<<<g2, kThreads, 0, s>>>(w.ds, w.dkeys, count, w.ctl, 2, skip_last ? 2 : 3);
-  if (!skip_last) thr_pass_kernel<<<g2, kThreads, 0, s>>>(w.ds, w.dkeys, count, w.ctl, 3, 3);
+  thr_pass_kernel<<<g2, kThreads, 0, s>>>(w.ds, w.dkeys, count, w.ctl, 2, skip_last ? 2 : 3,
+                                          w.rec_keys, w.beta);
+  if (!skip_last)
+    thr_pass_kernel<<<g2, kThreads, 0, s>>>(w.ds, w.dkeys, count, w.ctl, 3, 3, w.rec_keys, w.beta);
   note_launch(skip_last ? 2 : 3);
   return cudaGetLastError();
 }
 
+// fb: the work of a query whose delegate pass may have stored records
+// only; in tie mode its full delegate arrays are written before the tie
+// path reads them (nullptr: not such a query)
 template <int DT, int B>
 static void filter_t(const FilterParams& p, int g1, int g2, int g3, int g4, int g5,
-                     cudaStream_t s) {
+                     cudaStream_t s, const Work* fb, int sms) {
   filter_classify_kernel<DT, B><<<g1, kThreads, 0, s>>>(p);
   filter_resolve_kernel<DT, B><<<g3, kThreads, 0, s>>>(p);
   if ((reinterpret_cast<uintptr_t>(p.keys) & 15u) == 0) {
@@ -1818,6 +1848,7 @@ static void filter_t(const FilterParams& p, int g1, int g2, int g3, int g4, int 
     filter_count_kernel<DT, false><<<g2, kThreads, 0, s>>>(p);
     filter_scan_kernel<DT, false><<<g2, kThreads, 0, s>>>(p);
   }
+  if (fb) launch_delegates_fallback(*fb, p.keys, 2, sms, s);
   filter_tfind_kernel<B><<<g5, kThreads, 0, s>>>(p);
   filter_ties_kernel<DT, B><<<g4, kThreads, 0, s>>>(p);
 }
@@ -1833,6 +1864,9 @@ cudaError_t launch_filter(const Work& w, const void* keys, bool kth_only, int sm
   p.alpha = w.alpha;
   p.dkeys = w.dkeys;
   p.dsegs = w.dsegs;
+  p.rec_keys = w.rec_keys;
+  p.rec_segs = w.rec_segs;
+  p.rec_sub = w.rec_sub;
   p.scanq = w.scanq;
   p.g = w.g;
   p.ctl = w.ctl;
@@ -1849,12 +1883,13 @@ cudaError_t launch_filter(const Work& w, const void* keys, bool kth_only, int sm
   // direct tie path: a warp per listed or scanned subrange
   const int g4 = grid_for(int64_t(kTieSCap) + kTieScanMax, kThreads / 32, sms, 1);
   const int g5 = grid_for(w.S, kThreads, sms, 4);
+  const Work* fb = (!kth_only && spec_eligible(w, keys)) ? &w : nullptr;
 #define DRTOPK_FILTER_CASE(DTV)                              \
   switch (w.beta) {                                          \
-    case 1: filter_t<DTV, 1>(p, g1, g2, g3, g4, g5, s); break;       \
-    case 2: filter_t<DTV, 2>(p, g1, g2, g3, g4, g5, s); break;       \
-    case 3: filter_t<DTV, 3>(p, g1, g2, g3, g4, g5, s); break;       \
-    default: filter_t<DTV, 4>(p, g1, g2, g3, g4, g5, s); break;      \
+    case 1: filter_t<DTV, 1>(p, g1, g2, g3, g4, g5, s, fb, sms); break;       \
+    case 2: filter_t<DTV, 2>(p, g1, g2, g3, g4, g5, s, fb, sms); break;       \
+    case 3: filter_t<DTV, 3>(p, g1, g2, g3, g4, g5, s, fb, sms); break;       \
+    default: filter_t<DTV, 4>(p, g1, g2, g3, g4, g5, s, fb, sms); break;      \
   }
   switch (w.dtype) {
     case DRTOPK_U32: DRTOPK_FILTER_CASE(DRTOPK_U32); break;
