@@ -11,9 +11,9 @@
 //
 // GB300 design (replaces the paper's warp-per-subrange shuffles and its
 // shared-memory transposition for small subranges):
-//   * persistent grid, 2 CTAs of 256 threads per SM;
+//   * persistent grid, 3 CTAs of 256 threads per SM;
 //   * each CTA streams 32 KB chunks (8192 keys) with cp.async.bulk (TMA,
-//     1-D) into a 3-stage shared-memory ring completed on mbarriers, with an
+//     1-D) into a 2-stage shared-memory ring completed on mbarriers, with an
 //     L2 evict-first hint (the keys are read once);
 //   * thread t owns keys [32t, 32t+32) of a chunk and reads them as eight
 //     16-byte words in a rotated order (conflict-free banks); its top-beta
@@ -32,7 +32,8 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kChunkKeys = 8192;
 constexpr int kKPT = 32;  // keys per thread per chunk
-constexpr int kStages = 3;
+constexpr int kStages = 2;
+constexpr int kCtasPerSm = 3;  // 3 x (2 x 32 KB ring + static) per SM
 constexpr int kChunkBytes = kChunkKeys * 4;
 constexpr int kWarps = kThreads / 32;
 
@@ -44,8 +45,7 @@ constexpr int kPassSpec = 2;    // store records of subranges reaching t_lo (or 
 constexpr int kPassFallback = 3;  // store every subrange's delegates when p.only_if holds
 constexpr int kSampStride = 128;
 constexpr int kSampBins = 2048;  // top 11 bits
-constexpr int kRecStage = 512;   // records staged per CTA
-constexpr int kRecFlush = kRecStage - (kChunkKeys >> 5);  // flush before a chunk can overflow
+constexpr int kRecStage = 320;   // records staged per CTA (three CTAs per SM must fit)
 
 struct DelegParams {
   const uint32_t* keys;
@@ -242,7 +242,7 @@ __device__ __forceinline__ void issue_chunk(const DelegParams& p, int64_t c, uin
 }
 
 template <int DT, int B, bool TMA, int MODE = kPassFull>
-__global__ void __launch_bounds__(kThreads, 2) delegate_kernel(DelegParams p) {
+__global__ void __launch_bounds__(kThreads, kCtasPerSm) delegate_kernel(DelegParams p) {
   constexpr int P = Pow2<B>::v;
   // a fallback pass runs only when its condition holds, a records pass
   // only when the sample accepted (uniform over the grid)
@@ -467,7 +467,8 @@ __global__ void __launch_bounds__(kThreads, 2) delegate_kernel(DelegParams p) {
     }
     if constexpr (MODE == kPassSpec) {
       const uint32_t nst = rs_cnt;  // no append is in flight after the barrier
-      if (nst >= static_cast<uint32_t>(kRecFlush))
+      // flush while the next chunk's subranges (8192 >> alpha) still fit
+      if (nst > static_cast<uint32_t>(kRecStage - (kChunkKeys >> alpha)))
         flush_records<B>(p, nst, &rs_base, &rs_cnt, rs_sub, rs_keys, rs_segs);
     }
   }
@@ -528,7 +529,7 @@ cudaError_t launch_deleg_t(const DelegParams& p, bool tma, int sms, cudaStream_t
   const size_t smem = static_cast<size_t>(kStages) * kChunkBytes;
   int64_t units = (p.alpha > 13) ? p.S : p.nchunks;
   if (MODE == kPassSample) units = (p.nchunks + kSampStride - 1) / kSampStride;
-  int64_t grid = std::min<int64_t>(units, static_cast<int64_t>(sms) * 2);
+  int64_t grid = std::min<int64_t>(units, static_cast<int64_t>(sms) * kCtasPerSm);
   if (grid < 1) grid = 1;
   if (tma || MODE != kPassFull) {
     auto k = delegate_kernel<DT, B, true, MODE>;
