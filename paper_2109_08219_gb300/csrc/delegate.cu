@@ -22,6 +22,12 @@
 //     bitonic merges over warp shuffles, then across warps in shared memory;
 //   * the histogram of the delegates' top 8 bits (first digit of the
 //     threshold select) is fused into the epilogue.
+// For alpha in [5, 10] on large arrays the same kernel also runs as the
+// passes of the speculative compaction (Ctl::spec_on): a sample pass over
+// every 128th chunk that sets a bound t_lo below the expected tau, a records
+// pass that stores only the subranges whose largest delegate reaches t_lo,
+// and a fallback pass (the full pass behind a device-side condition) that
+// writes the full arrays when the records cannot stand in for them.
 #include "common.cuh"
 #include "delegate_core.cuh"
 #include "launch.h"
@@ -41,7 +47,7 @@ constexpr int kWarps = kThreads / 32;
 // with Ctl::spec_on).
 constexpr int kPassFull = 0;    // store every subrange's delegates
 constexpr int kPassSample = 1;  // histogram the delegates of every kSampStride-th chunk
-constexpr int kPassSpec = 2;    // store records of subranges reaching t_lo (or all, when off)
+constexpr int kPassSpec = 2;    // store records of subranges reaching t_lo (nothing when declined)
 constexpr int kPassFallback = 3;  // store every subrange's delegates when p.only_if holds
 constexpr int kSampStride = 128;
 constexpr int kSampBins = 2048;  // top 11 bits
