@@ -209,11 +209,13 @@ typedef struct {
   uint32_t error;          /* device error flags, 0 when none */
   uint32_t delegate_path;  /* bit 0: the delegate pass stored only the records
                               of subranges reaching a sampled bound (speculative
-                              compaction of the delegate vector, large arrays
-                              with alpha in [5, 10]); bit 1: a fallback pass then
-                              wrote the full delegate arrays (the bound was above
-                              tau, the records overflowed, or the query ended in
-                              tie mode). The result is exact either way. */
+                              compaction of the delegate vector, 16-byte aligned
+                              arrays of 2^26 keys or more with alpha in [5, 10]);
+                              bit 1: a fallback pass wrote the full delegate
+                              arrays (alone: the sample declined; with bit 0: the
+                              bound was above tau, the records overflowed, or the
+                              query ended in tie mode). 0: the full pass alone.
+                              The result is exact either way. */
 } drtopk_stats;
 
 /*
