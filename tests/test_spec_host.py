@@ -98,3 +98,30 @@ def test_sampled_bound_is_conservative_on_uniform_input():
         t = (2047 - top) << 21
         tau = oracle.threshold(dk, di, k)
         assert int(np.sum(dk.ravel() >= t)) >= k and tau >= t, k
+
+
+def test_plan_reserves_records_only_for_eligible_shapes():
+    """drtopk_plan's workspace includes the records of the speculative
+    compaction (S/4 records of beta keys, beta segments and a subrange id)
+    exactly for arrays of 2^26 keys or more with alpha in [5, 10]."""
+    import paper_2109_08219_gb300 as drtopk
+    from paper_2109_08219_gb300 import build as libbuild
+    libbuild.build()
+
+    def al(b):
+        return (b + 255) // 256 * 256
+
+    for n, k in (((1 << 26), 1 << 16), ((1 << 30), 1 << 20), ((1 << 28), 1 << 14)):
+        a, b, ws = drtopk.drtopk_plan(n, k)
+        assert 5 <= a <= 10
+        a2, b2, ws_small = drtopk.drtopk_plan(n - 1, k)   # one key short of eligible at 2^26
+        S = (n + (1 << a) - 1) >> a
+        rec = max(1024, S // 4)
+        extra = al(rec * b * 4) + al(rec * b * 2) + al(rec * 4)
+        if n == 1 << 26:
+            assert (a2, b2) == (a, b) and ws - ws_small >= extra - 4096
+    # alpha above 10 (small k): no records
+    a, b, ws = drtopk.drtopk_plan(1 << 30, 1024)
+    assert a == 11
+    a3, b3, ws3 = drtopk.drtopk_plan((1 << 30) - 1, 1024)
+    assert abs(ws - ws3) < 1 << 20
