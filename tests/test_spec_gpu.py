@@ -159,3 +159,30 @@ def test_graph_replay_with_records():
         torch.cuda.synchronize()
         assert np.array_equal(host_bits(outs[0]), rk) and np.array_equal(outs[1].cpu().numpy(), ri)
     drtopk.sync_status()
+
+
+@pytest.mark.parametrize("beta", [1, 3, 4])
+def test_records_with_forced_beta(beta):
+    # the records hold beta delegates each; results stay exact on uniform
+    # keys whatever the path (records; records then the tie-mode fallback,
+    # since 2^26 random u32 keys repeat and the k-th may be tied; or a
+    # declined sample) and on the misleading sample, which must never end
+    # with the records alone (declined when the sampled bins are crowded,
+    # else the records pass finds fewer than k delegates above the bound)
+    bits = inputs.uniform_u32(N, 20 + beta).numpy().view(np.uint32)
+    x = to_dev(bits, "u32")
+    ok, oi, ot, st = drtopk.drtopk_topk_ex(x, K, alpha=6, beta=beta, dtype="u32")
+    rk, ri = oracle.topk(bits, oracle.U32, K)
+    assert np.array_equal(host_bits(ok), rk) and np.array_equal(oi.cpu().numpy(), ri)
+    assert int(host_bits(ot)[0]) == oracle.kth(bits, oracle.U32, K)
+    assert st["error"] == 0 and st["beta"] == beta and st["delegate_path"] in (1, 2, 3)
+    if beta == 3:
+        rng = np.random.default_rng(21)
+        m = rng.integers(0, 1 << 20, N, dtype=np.uint64).astype(np.uint32)
+        for c in range(0, N // CHUNK, SAMPLE_STRIDE):
+            m[c * CHUNK:(c + 1) * CHUNK] = rng.integers(1 << 31, 1 << 32, CHUNK,
+                                                        dtype=np.uint64).astype(np.uint32)
+        ok, oi, _, st = drtopk.drtopk_topk_ex(to_dev(m, "u32"), K, alpha=6, beta=3, dtype="u32")
+        rk, ri = oracle.topk(m, oracle.U32, K)
+        assert np.array_equal(host_bits(ok), rk) and np.array_equal(oi.cpu().numpy(), ri)
+        assert st["error"] == 0 and st["delegate_path"] in (2, 3)
