@@ -109,3 +109,42 @@ def test_ablation_argument_checks(L):
     assert L.drtopk_topk_ablate(p, 0, 100, 1, -1, 0, 1, out, out, None, None) == 1  # alpha
     assert L.drtopk_topk_ablate(p, 0, 100, 0, 0, 0, 1, out, out, None, None) == 2   # k = 0
     assert L.drtopk_topk_ablate(p, 0, 100, 1, 0, 0, 1, None, out, None, None) == 1  # outputs
+
+
+def test_select_merge_and_selftest_check_arguments_before_cuda(L):
+    """drtopk_select, drtopk_topk_merge and drtopk_wait_selftest reject bad
+    arguments with a status before any CUDA call (no GPU here)."""
+    p = ctypes.c_void_p(0x1000)  # never dereferenced
+    out = ctypes.c_void_p(0x2000)
+    # drtopk_select(keys, dtype, n, k, flags, out_keys, out_idx, out_kth, stream)
+    assert L.drtopk_select(p, 0, 100, 5, 2, out, out, None, None) == 1     # unknown flag
+    assert L.drtopk_select(p, 0, 100, 5, 0, out, None, None, None) == 1    # keys without idx
+    assert L.drtopk_select(p, 0, 100, 5, 0, None, None, None, None) == 1   # no output
+    assert L.drtopk_select(p, 9, 100, 5, 1, out, out, None, None) == 3     # dtype
+    assert L.drtopk_select(p, 0, 100, 0, 1, out, out, None, None) == 2     # k = 0
+    assert L.drtopk_select(p, 0, 100, 101, 1, None, None, out, None) == 2  # k > n
+
+    def arr(v):
+        a = (ctypes.c_int64 * len(v))(*v)
+        return ctypes.cast(a, ctypes.POINTER(ctypes.c_int64)), a
+
+    def merge(off, base, k, parts=None, flags=0, dtype=0, keys=p):
+        po, _ka = arr(off)
+        pb, _kb = arr(base)
+        n = len(off) - 1 if parts is None else parts
+        return L.drtopk_topk_merge(keys, p, dtype, po, pb, n, k, flags, out, out, None)
+
+    assert merge([0, 5, 10], [0, 100], 3, keys=None) == 1       # null keys
+    assert merge([0, 5, 10], [0, 100], 3, parts=0) == 1         # no parts
+    assert merge([0] * 258, [0] * 257, 1, parts=257) == 1       # more than 256 parts
+    assert merge([0, 5, 10], [0, 100], 3, flags=4) == 1         # unknown flag
+    assert merge([0, 5, 10], [0, 100], 3, dtype=9) == 3         # dtype
+    assert merge([0, 6, 5], [0, 100], 3) == 1                   # offsets decrease
+    assert merge([0, 5, 10], [0, -1], 3) == 1                   # negative base
+    assert merge([4, 4, 4], [0, 100], 1) == 1                   # empty lists
+    assert merge([0, 5, 10], [0, 100], 11) == 2                 # k > listed entries
+    assert merge([0, 5, 10], [0, 100], 0) == 2                  # k = 0
+    # the selftest's wait limit: 1 us to 10 s
+    assert L.drtopk_wait_selftest(0, None) == 1
+    assert L.drtopk_wait_selftest(10000001, None) == 1
+    assert drtopk.alloc_count() >= 0
